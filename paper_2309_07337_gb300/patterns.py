@@ -1,0 +1,386 @@
+"""Seeded synthetic communication patterns for the neighbourhood exchange.
+
+This module only builds inputs: distributed-graph adjacency, per-edge counts and
+displacements, send index lists, global indices and payload buffers, for the workloads
+the exchange is measured on (halo exchanges of structured stencils and of a
+row-partitioned sparse matrix-vector product, the applications that motivate
+locality-aware neighbourhood collectives in section 1 of the MPI Advance paper).
+It holds none of the exchange's own arithmetic: no edge matching, no data movement,
+no aggregation.  Both the GPU path and the CPU oracle consume what it returns.
+
+Conventions shared by every generator:
+  * ranks are numbered row-major with x fastest; node(r) = r // ppn;
+  * out- and in-neighbour lists are in ascending rank order;
+  * each rank's send slots are its send lists concatenated in out-list order
+    (sdispls packed), its receive slots the received blocks concatenated in in-list
+    order (rdispls packed);
+  * all ranks' regions live in one send buffer and one receive buffer, located by
+    per-rank byte offsets;
+  * numpy PCG64 streams seeded by the caller.
+"""
+from __future__ import annotations
+
+import dataclasses
+import itertools
+from typing import Optional
+
+import numpy as np
+
+
+@dataclasses.dataclass
+class Pattern:
+    """One neighbourhood all-to-all-v problem over P emulated ranks."""
+
+    name: str
+    P: int
+    ppn: int
+    in_ptr: np.ndarray          # int32 [P+1], CSR of in-lists
+    sources: np.ndarray         # int32 [E]
+    out_ptr: np.ndarray         # int32 [P+1], CSR of out-lists
+    dests: np.ndarray           # int32 [E]
+    sendcounts: np.ndarray      # int32 [E], aligned with dests
+    sdispls: np.ndarray         # int32 [E]
+    recvcounts: np.ndarray      # int32 [E], aligned with sources
+    rdispls: np.ndarray         # int32 [E]
+    elem_size: int              # bytes per element
+    dtype: str                  # 'f64', 'f32' or 'bytes'
+    send_base: np.ndarray       # int64 [P], byte offset of rank r's send region
+    recv_base: np.ndarray       # int64 [P], byte offset of rank r's receive region
+    sendbuf_bytes: int
+    recvbuf_bytes: int
+    send_slot_ptr: Optional[np.ndarray] = None   # int64 [P+1]
+    send_idx: Optional[np.ndarray] = None        # int32 [send slots]
+    recv_slot_ptr: Optional[np.ndarray] = None   # int64 [P+1]
+    global_sidx: Optional[np.ndarray] = None     # int64 [send slots]
+    global_ridx: Optional[np.ndarray] = None     # int64 [receive slots]
+    meta: dict = dataclasses.field(default_factory=dict)
+
+    @property
+    def n_edges(self) -> int:
+        return int(self.out_ptr[-1])
+
+    @property
+    def volume(self) -> int:
+        """Elements moved by one exchange (V)."""
+        return int(self.sendcounts.astype(np.int64).sum())
+
+    def user_bytes(self) -> int:
+        """Bytes a user sees moved: V elements read and V elements written."""
+        return 2 * self.volume * self.elem_size
+
+
+def _ptr_from_counts(counts: np.ndarray) -> np.ndarray:
+    ptr = np.zeros(len(counts) + 1, dtype=np.int64)
+    np.cumsum(counts, out=ptr[1:])
+    return ptr
+
+
+def _segmented_exclusive(counts: np.ndarray, owner: np.ndarray, P: int) -> np.ndarray:
+    """Exclusive running sum of counts restarting at every owner (edges sorted by owner)."""
+    c = counts.astype(np.int64)
+    run = np.cumsum(c) - c
+    first = np.searchsorted(owner, np.arange(P), side="left")
+    start_of = np.concatenate([run, [0]])[first]  # running sum at each owner's first edge
+    return run - start_of[owner]
+
+
+def _ragged_arange(counts: np.ndarray) -> np.ndarray:
+    """concatenate([arange(c) for c in counts]) without a Python loop."""
+    counts = counts.astype(np.int64)
+    total = int(counts.sum())
+    if total == 0:
+        return np.zeros(0, dtype=np.int64)
+    starts = np.cumsum(counts) - counts
+    return np.arange(total, dtype=np.int64) - np.repeat(starts, counts)
+
+
+def _assemble(name, P, ppn, out_src, out_dst, out_cnt, send_elem, send_gidx,
+              in_dst, in_src, in_cnt, recv_gidx, elem_size, dtype, region_elems, meta):
+    """Builds a Pattern from edge lists already sorted by (owner rank, list order).
+
+    out_*: one entry per out-edge; send_elem/send_gidx: one per send slot, in out-edge
+    order.  in_*: one per in-edge; recv_gidx: one per receive slot in in-edge order.
+    region_elems[r]: number of elements in rank r's send region."""
+    out_src = np.asarray(out_src, dtype=np.int64)
+    in_dst = np.asarray(in_dst, dtype=np.int64)
+    out_ptr = _ptr_from_counts(np.bincount(out_src, minlength=P)).astype(np.int32)
+    in_ptr = _ptr_from_counts(np.bincount(in_dst, minlength=P)).astype(np.int32)
+    sdispls = _segmented_exclusive(out_cnt, out_src, P)
+    rdispls = _segmented_exclusive(in_cnt, in_dst, P)
+    send_tot = np.bincount(out_src, weights=out_cnt, minlength=P).astype(np.int64)
+    recv_tot = np.bincount(in_dst, weights=in_cnt, minlength=P).astype(np.int64)
+    send_slot_ptr = _ptr_from_counts(send_tot)
+    recv_slot_ptr = _ptr_from_counts(recv_tot)
+    region_elems = np.asarray(region_elems, dtype=np.int64)
+    send_base = (_ptr_from_counts(region_elems)[:-1] * elem_size).astype(np.int64)
+    recv_base = (recv_slot_ptr[:-1] * elem_size).astype(np.int64)
+    return Pattern(
+        name=name, P=P, ppn=ppn,
+        in_ptr=in_ptr, sources=np.asarray(in_src, dtype=np.int32),
+        out_ptr=out_ptr, dests=np.asarray(out_dst, dtype=np.int32),
+        sendcounts=np.asarray(out_cnt, dtype=np.int32), sdispls=sdispls.astype(np.int32),
+        recvcounts=np.asarray(in_cnt, dtype=np.int32), rdispls=rdispls.astype(np.int32),
+        elem_size=int(elem_size), dtype=dtype,
+        send_base=send_base, recv_base=recv_base,
+        sendbuf_bytes=int(region_elems.sum() * elem_size),
+        recvbuf_bytes=int(recv_slot_ptr[-1] * elem_size),
+        send_slot_ptr=send_slot_ptr, send_idx=np.asarray(send_elem, dtype=np.int32),
+        recv_slot_ptr=recv_slot_ptr,
+        global_sidx=np.asarray(send_gidx, dtype=np.int64),
+        global_ridx=np.asarray(recv_gidx, dtype=np.int64),
+        meta=meta)
+
+
+# ------------------------------------------------------------------ stencils ---
+
+def stencil(grid, ranks, ppn, comps=1, dtype="f64", neighbors="all", name=None) -> Pattern:
+    """Halo exchange of a structured grid split into equal rank blocks (no periodicity).
+
+    grid, ranks: per-axis point and rank counts (x first), 2 or 3 axes.
+    neighbors: 'faces' (5-point in 2D, 7-point in 3D) or 'all' (9- / 27-point).
+    Each point carries `comps` values stored together (one element of comps*8 or
+    comps*4 bytes).  The send list towards direction delta is the boundary layer facing
+    it (coordinate 0 where delta=-1, n-1 where delta=+1, all where delta=0), in
+    ascending local point index; the global index of a point is its row-major index in
+    the whole grid."""
+    grid = tuple(int(g) for g in grid)
+    ranks = tuple(int(r) for r in ranks)
+    D = len(grid)
+    assert D in (2, 3) and len(ranks) == D
+    blk = tuple(g // r for g, r in zip(grid, ranks))
+    assert all(b * r == g for b, r, g in zip(blk, ranks, grid))
+    P = int(np.prod(ranks))
+    esz = comps * (8 if dtype == "f64" else 4)
+    npts = int(np.prod(blk))
+
+    # directions in ascending neighbour-rank order: lexicographic in (dz, dy, dx)
+    dirs = []
+    for d in itertools.product((-1, 0, 1), repeat=D):
+        dd = tuple(reversed(d))  # dd[0] = dx
+        if any(dd) and (neighbors == "all" or sum(map(abs, dd)) == 1):
+            dirs.append(dd)
+
+    # local coordinates of each local point (x fastest)
+    loc = np.indices(tuple(reversed(blk))).reshape(D, -1)[::-1]  # loc[axis][point]
+    templates = []
+    for dd in dirs:
+        m = np.ones(npts, dtype=bool)
+        for ax in range(D):
+            if dd[ax] == -1:
+                m &= loc[ax] == 0
+            elif dd[ax] == 1:
+                m &= loc[ax] == blk[ax] - 1
+        templates.append(np.nonzero(m)[0].astype(np.int64))
+    tsize = np.array([len(t) for t in templates], dtype=np.int64)
+    tpool = np.concatenate(templates)
+    toff = _ptr_from_counts(tsize)[:-1]
+
+    rc = np.indices(tuple(reversed(ranks))).reshape(D, -1)[::-1]  # rank coords[axis][rank]
+    stride = [1, ranks[0], ranks[0] * ranks[1]][:D]
+    dirs_a = np.array(dirs, dtype=np.int64)                         # [ndir, D]
+    valid = np.ones((P, len(dirs)), dtype=bool)
+    for ax in range(D):
+        c = rc[ax][:, None] + dirs_a[None, :, ax]
+        valid &= (c >= 0) & (c < ranks[ax])
+    nbr = np.arange(P)[:, None] + (dirs_a * np.array(stride)).sum(1)[None, :]
+    er, ed = np.nonzero(valid)                 # edges sorted by (rank, direction order)
+    edst = nbr[er, ed]
+    ecnt = tsize[ed]
+
+    gstride = [1, grid[0], grid[0] * grid[1]][:D]
+
+    def gidx_of(rank, local):
+        g = np.zeros(len(local), dtype=np.int64)
+        for ax in range(D):
+            g += (rc[ax][rank] * blk[ax] + loc[ax][local]) * gstride[ax]
+        return g
+
+    k = _ragged_arange(ecnt)
+    send_elem = tpool[np.repeat(toff[ed], ecnt) + k]
+    send_rank = np.repeat(er, ecnt)
+    send_gidx = gidx_of(send_rank, send_elem)
+
+    # receive side: rank d hears from d+delta' (ascending order = same direction order);
+    # the block from q = d + delta' is q's send list towards -delta'.
+    opp = np.array([dirs.index(tuple(-x for x in dd)) for dd in dirs], dtype=np.int64)
+    ir, idd = np.nonzero(valid)
+    isrc = nbr[ir, idd]
+    icnt = tsize[opp[idd]]
+    k2 = _ragged_arange(icnt)
+    recv_elem = tpool[np.repeat(toff[opp[idd]], icnt) + k2]
+    recv_gidx = gidx_of(np.repeat(isrc, icnt), recv_elem)
+
+    meta = dict(kind="stencil", grid=grid, ranks=ranks, blk=blk, comps=comps,
+                neighbors=neighbors, dirs=dirs)
+    return _assemble(name or f"stencil{D}d_{'x'.join(map(str, grid))}_P{P}_c{comps}",
+                     P, ppn, er, edst, ecnt, send_elem, send_gidx,
+                     ir, isrc, icnt, recv_gidx, esz, dtype, np.full(P, npts), meta)
+
+
+def stencil_field(p: Pattern, seed: int) -> np.ndarray:
+    """Send buffer of a stencil pattern: every rank's block, values U(-1, 1)."""
+    rng = np.random.default_rng(seed)
+    n = p.sendbuf_bytes // (8 if p.dtype == "f64" else 4)
+    if p.dtype == "f64":
+        return rng.uniform(-1.0, 1.0, size=n)
+    return rng.uniform(-1.0, 1.0, size=n).astype(np.float32)
+
+
+# -------------------------------------------------------------- SpMV halos ---
+
+def row_starts(n: int, P: int) -> np.ndarray:
+    """Contiguous row partition; the first n mod P ranks get one extra row."""
+    base, extra = divmod(n, P)
+    r = np.arange(P + 1, dtype=np.int64)
+    return r * base + np.minimum(r, extra)
+
+
+def spmv_columns(n: int, nnz: int, seed: int, band: int = 4096, band_frac: float = 0.8):
+    """Column indices of a random sparse matrix: per row, round(band_frac*nnz) columns
+    uniform in [i-band, i+band] (clipped to the matrix) and the rest uniform in [0, n);
+    duplicates inside a row are redrawn from the same distribution."""
+    rng = np.random.default_rng(seed)
+    nb = int(round(band_frac * nnz))
+    rows = np.arange(n, dtype=np.int64)
+    lo = np.maximum(rows - band, 0)
+    hi = np.minimum(rows + band, n - 1)
+    assert int((hi - lo + 1).min()) >= nb and n >= nnz, "band too narrow for nnz"
+    cols = np.empty((n, nnz), dtype=np.int64)
+    cols[:, :nb] = rng.integers(lo[:, None], hi[:, None] + 1, size=(n, nb))
+    cols[:, nb:] = rng.integers(0, n, size=(n, nnz - nb))
+    while True:
+        order = np.argsort(cols, axis=1, kind="stable")
+        srt = np.take_along_axis(cols, order, axis=1)
+        dup_sorted = np.zeros_like(srt, dtype=bool)
+        dup_sorted[:, 1:] = srt[:, 1:] == srt[:, :-1]
+        if not dup_sorted.any():
+            break
+        dup = np.zeros_like(dup_sorted)
+        np.put_along_axis(dup, order, dup_sorted, axis=1)
+        ri, ci = np.nonzero(dup)
+        is_band = ci < nb
+        cols[ri[is_band], ci[is_band]] = rng.integers(lo[ri[is_band]], hi[ri[is_band]] + 1)
+        cols[ri[~is_band], ci[~is_band]] = rng.integers(0, n, size=int((~is_band).sum()))
+    return cols
+
+
+def spmv_halo(n: int, P: int, ppn: int, nnz: int, seed: int, dtype: str = "f64",
+              band: int = 4096, band_frac: float = 0.8, name=None, keep_matrix=False) -> Pattern:
+    """Halo exchange of y = A x with A row-partitioned over P ranks.
+
+    Rank d receives the x entries of every column its rows touch outside its own row
+    range (the off-rank columns, ascending global index = ascending owner); the owner
+    sends them, in the same order, from its slice of x.  Global index = matrix column."""
+    cols = spmv_columns(n, nnz, seed, band, band_frac)
+    rs = row_starts(n, P)
+    row_owner = np.repeat(np.arange(P, dtype=np.int64), np.diff(rs))
+    col_owner = np.searchsorted(rs, cols, side="right") - 1
+    off = col_owner != row_owner[:, None]
+    d_of = np.broadcast_to(row_owner[:, None], cols.shape)[off]
+    keys = np.sort(d_of * n + cols[off])             # sorted by (receiver, column)
+    keys = keys[np.r_[True, keys[1:] != keys[:-1]]]
+    rd = keys // n
+    rcol = keys % n
+    rq = np.searchsorted(rs, rcol, side="right") - 1  # owner of each received column
+    # in-edges: runs of (d, q)
+    ek = rd * P + rq
+    starts = np.flatnonzero(np.r_[True, ek[1:] != ek[:-1]])
+    in_dst = rd[starts]
+    in_src = rq[starts]
+    in_cnt = np.diff(np.r_[starts, len(ek)])
+    # out-edges: the same (q -> d) blocks sorted by (q, d, column)
+    o = np.lexsort((rcol, rd, rq))
+    sq, sd, sc = rq[o], rd[o], rcol[o]
+    ok = sq * P + sd
+    ostarts = np.flatnonzero(np.r_[True, ok[1:] != ok[:-1]])
+    out_src = sq[ostarts]
+    out_dst = sd[ostarts]
+    out_cnt = np.diff(np.r_[ostarts, len(ok)])
+    send_elem = sc - rs[sq]
+    esz = 8 if dtype == "f64" else 4
+    meta = dict(kind="spmv", n=n, nnz=nnz, band=band, row_starts=rs, seed=seed)
+    if keep_matrix:
+        meta["cols"] = cols
+    return _assemble(name or f"spmv_n{n}_P{P}_nnz{nnz}_{dtype}", P, ppn,
+                     out_src, out_dst, out_cnt, send_elem, sc,
+                     in_dst, in_src, in_cnt, rcol, esz, dtype, np.diff(rs), meta)
+
+
+def spmv_x(p: Pattern, seed: int) -> np.ndarray:
+    """Send buffer of an SpMV halo pattern: x ~ N(0, 1) in the pattern's precision."""
+    rng = np.random.default_rng(seed)
+    x = rng.standard_normal(p.meta["n"])
+    return x if p.dtype == "f64" else x.astype(np.float32)
+
+
+def batched_specs(count: int, seed: int):
+    """Sizes of the uneven batch: rows 2^k (k uniform in 14..20), P uniform in 64..1024,
+    nnz/row uniform in 8..32, fp32 or fp64 with probability 1/2 each, 32 ranks per node."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for j in range(count):
+        k = int(rng.integers(14, 21))
+        P = int(rng.integers(64, 1025))
+        nnz = int(rng.integers(8, 33))
+        dt = "f32" if rng.random() < 0.5 else "f64"
+        out.append(dict(n=1 << k, P=P, ppn=32, nnz=nnz, dtype=dt, seed=seed * 1000 + j))
+    return out
+
+
+# ------------------------------------------------------------ the workloads ---
+
+SEED = 2309
+
+
+def config1():
+    """2D 5-point Laplacian halo: 256x256 grid, 4x4 ranks of 64x64, 4 ranks per node, fp64."""
+    return stencil((256, 256), (4, 4), ppn=4, comps=1, dtype="f64", neighbors="faces",
+                   name="cfg1_stencil2d_5pt_256sq_P16")
+
+
+def config2(n=1 << 20, P=1024):
+    """SpMV halo: 2^20 rows over 1024 ranks (32 per node), 20 nnz/row, fp64 x."""
+    return spmv_halo(n, P, 32, 20, SEED + 2, "f64", name=f"cfg2_spmv_n{n}_P{P}")
+
+
+def config3(count=64):
+    """64 uneven SpMV halo patterns, mixed fp32 / fp64."""
+    return [spmv_halo(s["n"], s["P"], s["ppn"], s["nnz"], s["seed"], s["dtype"],
+                      name=f"cfg3_{j}_n{s['n']}_P{s['P']}_{s['dtype']}")
+            for j, s in enumerate(batched_specs(count, SEED + 3))]
+
+
+def config4(n=1 << 20, P=1024, ppn=32):
+    """Differentiable halo: the config-2 matrix with fp32 values and fp32 x."""
+    return spmv_halo(n, P, ppn, 20, SEED + 2, "f32", name=f"cfg4_spmv_n{n}_P{P}_f32",
+                     keep_matrix=True)
+
+
+def config5(edge=32, comps=8, R=16, ppn=64):
+    """3D 27-point stencil: (R*edge)^3 grid over R^3 ranks, `comps` fp64 per point."""
+    g = R * edge
+    return stencil((g, g, g), (R, R, R), ppn=ppn, comps=comps, dtype="f64", neighbors="all",
+                   name=f"cfg5_stencil3d_27pt_{g}cube_P{R ** 3}_c{comps}")
+
+
+def restrict_to_receivers(p: Pattern, keep) -> Pattern:
+    """Sub-problem of `p` in which only ranks in `keep` receive (a bounded sample of the
+    same workload).  Buffers and displacements are unchanged; edges into other ranks
+    are dropped from both lists."""
+    keep_mask = np.zeros(p.P, dtype=bool)
+    keep_mask[np.asarray(keep)] = True
+    in_owner = np.repeat(np.arange(p.P), np.diff(p.in_ptr))
+    out_owner = np.repeat(np.arange(p.P), np.diff(p.out_ptr))
+    ki = keep_mask[in_owner]
+    ko = keep_mask[p.dests]
+    q = dataclasses.replace(p)
+    q.name = p.name + f"_recv{int(keep_mask.sum())}"
+    q.in_ptr = _ptr_from_counts(np.bincount(in_owner[ki], minlength=p.P)).astype(np.int32)
+    q.sources = p.sources[ki]
+    q.recvcounts = p.recvcounts[ki]
+    q.rdispls = p.rdispls[ki]
+    q.out_ptr = _ptr_from_counts(np.bincount(out_owner[ko], minlength=p.P)).astype(np.int32)
+    q.dests = p.dests[ko]
+    q.sendcounts = p.sendcounts[ko]
+    q.sdispls = p.sdispls[ko]
+    return q

@@ -1,0 +1,451 @@
+"""Checks that pin the CPU oracle to facts outside itself.
+
+Each check takes an oracle library handle (the real one, or a build with a planted
+mistake in the mutation test) and raises AssertionError when the oracle disagrees with:
+  * hand-worked golden cases (tests/golden/*.json, each with its citation);
+  * brute force: a stencil halo equals the global grid read at the ghost coordinates,
+    an SpMV halo equals x[off-rank columns of the rank's rows];
+  * invariants: list-order permutation, locality form == standard form, idempotence;
+  * closed-form counts from the stencil geometry;
+  * the adjoint: backward == dense transpose of the forward's 0/1 map, exactly for
+    integer data, and finite differences.
+"""
+from __future__ import annotations
+
+import itertools
+import json
+import os
+import types
+
+import numpy as np
+
+import oracle
+from paper_2309_07337_gb300 import patterns as pt
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+_ARR = {"in_ptr": np.int32, "sources": np.int32, "out_ptr": np.int32, "dests": np.int32,
+        "sendcounts": np.int32, "sdispls": np.int32, "recvcounts": np.int32,
+        "rdispls": np.int32, "send_base": np.int64, "recv_base": np.int64,
+        "send_slot_ptr": np.int64, "send_idx": np.int32, "recv_slot_ptr": np.int64,
+        "global_sidx": np.int64, "global_ridx": np.int64}
+
+
+def load_golden(name):
+    with open(os.path.join(GOLDEN, name)) as f:
+        g = json.load(f)
+    ns = types.SimpleNamespace()
+    for k, v in g.items():
+        setattr(ns, k, np.array(v, dtype=_ARR[k]) if k in _ARR else v)
+    for k in _ARR:
+        if not hasattr(ns, k):
+            setattr(ns, k, None)
+    vt = np.int32 if g["values"] == "i4" else np.float64
+    ns.vt = vt
+    ns.sendbuf = np.array(g["send_values"], dtype=vt)
+    ns.recv_init = np.array(g["recv_init"], dtype=vt)
+    ns.dtype = "f64" if vt == np.float64 else "bytes"
+    return ns
+
+
+def as_values(b, vt):
+    return np.frombuffer(np.ascontiguousarray(b).tobytes(), dtype=vt)
+
+
+# ------------------------------------------------------------------ golden ----
+
+def check_golden_forward(lib):
+    for name in ("ring3.json", "multigraph.json", "locality_dedup.json", "backward_order.json"):
+        g = load_golden(name)
+        got = as_values(oracle.standard(g, g.sendbuf, g.recv_init, lib=lib), g.vt)
+        assert np.array_equal(got, np.array(g.expected_recv, dtype=g.vt)), name
+        if g.global_sidx is not None:
+            got2, _ = oracle.locality(g, g.sendbuf, g.recv_init, lib=lib)
+            assert np.array_equal(as_values(got2, g.vt), np.array(g.expected_recv, dtype=g.vt)), name
+
+
+def check_golden_multigraph_truncate(lib):
+    g = load_golden("multigraph.json")
+    g.recvcounts = g.recvcounts[::-1].copy()   # first listing now expects 2 elements
+    assert oracle.validate(g, lib=lib) == g.swapped_recvcounts_error
+
+
+def check_golden_locality(lib):
+    g = load_golden("locality_dedup.json")
+    st = oracle.locality_stats(g, lib=lib)
+    assert st == g.expected_stats, st
+    a, b, gi, rep = oracle.locality_layout(g, lib=lib)
+    lay = g.expected_layout
+    assert a.tolist() == lay["a"] and b.tolist() == lay["b"]
+    assert gi.tolist() == lay["gidx"] and rep.tolist() == lay["rep"]
+    gr = np.array(g.grad_recv, dtype=np.float64)
+    for form in (0, 1):
+        got = as_values(oracle.backward(g, gr, form=form, lib=lib), np.float64)
+        assert np.array_equal(got, np.array(g.expected_grad_send)), (form, got)
+
+
+def check_golden_backward_order(lib):
+    for name in ("backward_order.json", "backward_order2.json"):
+        g = load_golden(name)
+        got = as_values(oracle.standard(g, g.sendbuf, g.recv_init, lib=lib), np.float64)
+        assert got.tolist() == g.expected_recv, name
+        gr = np.array(g.grad_recv, dtype=np.float64)
+        old = np.array(g.grad_send_init, dtype=np.float64)
+        for form, key in ((0, "standard"), (1, "node_blocked")):
+            got = as_values(oracle.backward(g, gr, form=form, lib=lib), np.float64)
+            assert got.tolist() == g.__dict__[f"expected_grad_{key}"], (name, key, got)
+            got = as_values(oracle.backward(g, gr, old, form=form, accumulate=True, lib=lib),
+                            np.float64)
+            assert got.tolist() == g.__dict__[f"expected_grad_{key}_accumulate"], (name, key, got)
+
+
+# ------------------------------------------------------------- brute force ----
+
+def ghost_expected(p, field):
+    """Receive region of every rank, read straight from the assembled global grid at
+    the ghost-layer coordinates (neighbour directions in ascending rank order)."""
+    grid, ranks, blk, comps = p.meta["grid"], p.meta["ranks"], p.meta["blk"], p.meta["comps"]
+    D = len(grid)
+    npts = int(np.prod(blk))
+    f = field.reshape(p.P, npts, comps)
+    G = np.zeros(tuple(reversed(grid)) + (comps,), dtype=field.dtype)
+    rc_all = []
+    for r in range(p.P):
+        rc = []
+        q = r
+        for ax in range(D):
+            rc.append(q % ranks[ax])
+            q //= ranks[ax]
+        rc_all.append(rc)
+        sl = tuple(slice(rc[ax] * blk[ax], (rc[ax] + 1) * blk[ax]) for ax in reversed(range(D)))
+        G[sl] = f[r].reshape(tuple(reversed(blk)) + (comps,))
+    out = []
+    for r in range(p.P):
+        rc = rc_all[r]
+        parts = []
+        for dd in itertools.product((-1, 0, 1), repeat=D):
+            dd = tuple(reversed(dd))
+            if not any(dd):
+                continue
+            if p.meta["neighbors"] == "faces" and sum(map(abs, dd)) != 1:
+                continue
+            if any(not (0 <= rc[ax] + dd[ax] < ranks[ax]) for ax in range(D)):
+                continue
+            rngs = []
+            for ax in range(D):
+                o = rc[ax] * blk[ax]
+                if dd[ax] == -1:
+                    rngs.append(np.array([o - 1]))
+                elif dd[ax] == 1:
+                    rngs.append(np.array([o + blk[ax]]))
+                else:
+                    rngs.append(np.arange(o, o + blk[ax]))
+            idx = np.meshgrid(*[rngs[ax] for ax in reversed(range(D))], indexing="ij")
+            parts.append(G[tuple(i.reshape(-1) for i in idx)])
+        out.append(np.concatenate(parts) if parts else np.zeros((0, comps), field.dtype))
+    return out
+
+
+def check_bruteforce_stencil(lib):
+    for grid, ranks, ppn, comps, nb in (((24, 16), (3, 2), 4, 1, "all"),
+                                        ((16, 16), (4, 4), 4, 1, "faces"),
+                                        ((12, 8, 8), (3, 2, 2), 5, 2, "all")):
+        p = pt.stencil(grid, ranks, ppn=ppn, comps=comps, dtype="f64", neighbors=nb)
+        x = pt.stencil_field(p, 11)
+        exp = ghost_expected(p, x)
+        for fn in (oracle.standard, lambda *a, **k: oracle.locality(*a, **k)[0]):
+            got = as_values(fn(p, x, lib=lib), np.float64).reshape(-1, comps)
+            for r in range(p.P):
+                lo = p.recv_base[r] // p.elem_size
+                assert np.array_equal(got[lo: lo + len(exp[r])], exp[r]), (grid, r)
+
+
+def check_bruteforce_spmv(lib):
+    for n, P, ppn, nnz, band, dt in ((4096, 16, 4, 12, 300, "f64"), (3000, 7, 3, 9, 200, "f32")):
+        p = pt.spmv_halo(n, P, ppn, nnz, seed=5, dtype=dt, band=band, keep_matrix=True)
+        x = pt.spmv_x(p, 6)
+        rs = pt.row_starts(n, P)
+        cols = p.meta["cols"]
+        for fn in (oracle.standard, lambda *a, **k: oracle.locality(*a, **k)[0]):
+            got = as_values(fn(p, x, lib=lib), x.dtype)
+            for r in range(P):
+                c = np.unique(cols[rs[r]:rs[r + 1]])
+                off = c[(c < rs[r]) | (c >= rs[r + 1])]
+                lo = p.recv_base[r] // p.elem_size
+                assert np.array_equal(got[lo: lo + len(off)], x[off]), (n, r)
+
+
+def check_permutation_invariance(lib):
+    p = pt.spmv_halo(2048, 9, 4, 10, seed=8, dtype="f64", band=200)
+    x = pt.spmv_x(p, 9)
+    ref = oracle.standard(p, x, lib=lib)
+    rng = np.random.default_rng(3)
+    q = types.SimpleNamespace(**{k: getattr(p, k) for k in p.__dataclass_fields__})
+    for side, ptr, cols in (("out", "out_ptr", ("dests", "sendcounts", "sdispls")),
+                            ("in", "in_ptr", ("sources", "recvcounts", "rdispls"))):
+        perm = np.concatenate([lo + rng.permutation(hi - lo) for lo, hi in
+                               zip(getattr(p, ptr)[:-1], getattr(p, ptr)[1:])])
+        for c in cols:
+            setattr(q, c, getattr(p, c)[perm])
+    got = oracle.standard(q, x, lib=lib)
+    assert np.array_equal(got, ref)
+    got2, st2 = oracle.locality(q, x, lib=lib)
+    assert np.array_equal(got2, ref)
+    # list order is not part of the problem: every count is invariant too
+    assert st2 == oracle.locality_stats(p, lib=lib)
+
+
+def check_idempotent_and_untouched(lib):
+    p = pt.spmv_halo(1024, 5, 2, 8, seed=4, dtype="f64", band=150)
+    x = pt.spmv_x(p, 2)
+    # widen the receive buffer with a sentinel tail no block covers
+    q = types.SimpleNamespace(**{k: getattr(p, k) for k in p.__dataclass_fields__})
+    q.recvbuf_bytes = p.recvbuf_bytes + 64
+    init = np.full(q.recvbuf_bytes, 0xAB, dtype=np.uint8)
+    a = oracle.standard(q, x, init, lib=lib)
+    b = oracle.standard(q, x, a, lib=lib)
+    assert np.array_equal(a, b)
+    assert (a[p.recvbuf_bytes:] == 0xAB).all()
+    assert int(np.sum(p.sendcounts)) == int(np.sum(p.recvcounts))
+
+
+# ------------------------------------------------------------ closed forms ----
+
+def stencil_counts(ranks, blk, ppn, neighbors="all"):
+    """Edge and element counts of a box-stencil halo from its geometry alone."""
+    D = len(ranks)
+    P = int(np.prod(ranks))
+    rc = np.indices(tuple(reversed(ranks))).reshape(D, -1)[::-1]
+    node = np.arange(P) // ppn
+    stride = np.array([1, ranks[0], ranks[0] * (ranks[1] if D > 1 else 1)][:D])
+    E = V = Vx = Mx = 0
+    pairs = set()
+    per_rb = {}
+    dirs = [tuple(reversed(d)) for d in itertools.product((-1, 0, 1), repeat=D)
+            if any(d) and (neighbors == "all" or sum(map(abs, d)) == 1)]
+    for dd in dirs:
+        ok = np.ones(P, dtype=bool)
+        for ax in range(D):
+            ok &= (rc[ax] + dd[ax] >= 0) & (rc[ax] + dd[ax] < ranks[ax])
+        src = np.nonzero(ok)[0]
+        dst = src + int((np.array(dd) * stride).sum())
+        tsz = int(np.prod([blk[ax] if dd[ax] == 0 else 1 for ax in range(D)]))
+        inter = node[src] != node[dst]
+        E += len(src)
+        V += len(src) * tsz
+        Vx += int(inter.sum()) * tsz
+        Mx += int(inter.sum())
+        for a, b in set(zip(node[src[inter]].tolist(), node[dst[inter]].tolist())):
+            pairs.add((a, b))
+        for r, b in zip(src[inter].tolist(), node[dst[inter]].tolist()):
+            per_rb.setdefault((r, b), []).append(dd)
+    # distinct points per (source rank, destination node): a point of boundary type t
+    # (per axis -1 at 0, +1 at n-1, 0 inside) lies in the send list of delta iff every
+    # axis has delta = 0 or delta = t.
+    types_ = list(itertools.product((-1, 0, 1), repeat=D))
+    tcount = {t: int(np.prod([1 if t[ax] else blk[ax] - 2 for ax in range(D)])) for t in types_}
+    U = 0
+    for dl in per_rb.values():
+        for t in types_:
+            if any(all(d[ax] == 0 or d[ax] == t[ax] for ax in range(D)) for d in dl):
+                U += tcount[t]
+    # leaders (the reading adopted for the aggregation): node pair (a, b) gathers at rank
+    # a*ppn + (b mod size(a)) and scatters from rank b*ppn + (a mod size(b)); every
+    # stencil point has one owner, so the representative of a value is its sender.
+    def size(a):
+        return min(ppn, P - a * ppn)
+    m1 = sum(1 for (r, b) in per_rb if r != (r // ppn) * ppn + b % size(r // ppn))
+    seen3 = set()
+    for (r, b), dl in per_rb.items():
+        for dd in dl:
+            d = r + int((np.array(dd) * stride).sum())
+            seen3.add((r // ppn, d))
+    m3 = sum(1 for (a, d) in seen3 if d != (d // ppn) * ppn + a % size(d // ppn))
+    return dict(E=E, V=V, V_inter=Vx, V_direct=V - Vx, msgs_inter=Mx, msgs_intra=E - Mx,
+                node_pairs=len(pairs), U=U, msgs_step1=m1, msgs_step3=m3)
+
+
+def check_closed_forms_small(lib):
+    for grid, ranks, ppn, nb in (((256, 256), (4, 4), 4, "faces"),
+                                 ((40, 24, 16), (5, 3, 2), 6, "all"),
+                                 ((32, 32, 32), (4, 4, 4), 8, "all")):
+        p = pt.stencil(grid, ranks, ppn=ppn, comps=1, dtype="f64", neighbors=nb)
+        blk = tuple(g // r for g, r in zip(grid, ranks))
+        want = stencil_counts(ranks, blk, ppn, nb)
+        got = oracle.locality_stats(p, lib=lib)
+        for k, v in want.items():
+            assert got[k] == v, (grid, k, got[k], v)
+
+
+def bytes1(p):
+    """The same pattern with one-byte elements (counts are independent of the size)."""
+    q = types.SimpleNamespace(**{k: getattr(p, k) for k in p.__dataclass_fields__})
+    s = p.elem_size
+    q.elem_size = 1
+    q.send_base = p.send_base // s
+    q.recv_base = p.recv_base // s
+    q.sendbuf_bytes = p.sendbuf_bytes // s
+    q.recvbuf_bytes = p.recvbuf_bytes // s
+    return q
+
+
+# ------------------------------------------------------------------ adjoint ----
+
+def forward_map(p, lib, form=0):
+    """Source element read by each receive element (-1 where no block writes):
+    the forward run on element ids, which fp64 carries exactly."""
+    comps = p.elem_size // (8 if p.dtype == "f64" else 4)
+    q = types.SimpleNamespace(**{k: getattr(p, k) for k in p.__dataclass_fields__})
+    q.elem_size = comps * 8
+    q.send_base = p.send_base // p.elem_size * q.elem_size
+    q.recv_base = p.recv_base // p.elem_size * q.elem_size
+    q.sendbuf_bytes = p.sendbuf_bytes // p.elem_size * q.elem_size
+    q.recvbuf_bytes = p.recvbuf_bytes // p.elem_size * q.elem_size
+    ids = np.arange(q.sendbuf_bytes // 8, dtype=np.float64)
+    init = np.full(q.recvbuf_bytes // 8, -1.0)
+    if form == 0:
+        r = oracle.standard(q, ids, init, lib=lib)
+    else:
+        r, _ = oracle.locality(q, ids, init, lib=lib)
+    return as_values(r, np.float64).astype(np.int64)
+
+
+def dense_transpose(p, src_of, g):
+    """E^T g with E the 0/1 matrix [receive component, send component]."""
+    n_send = p.sendbuf_bytes // (8 if p.dtype == "f64" else 4)
+    E = np.zeros((len(src_of), n_send))
+    cov = src_of >= 0
+    E[np.nonzero(cov)[0], src_of[cov]] = 1.0
+    return E.T @ g.astype(np.float64), cov
+
+
+def adjoint_cases():
+    yield pt.stencil((12, 8), (3, 2), ppn=4, comps=2, dtype="f64", neighbors="all")
+    yield pt.stencil((8, 8, 4), (2, 2, 2), ppn=3, comps=1, dtype="f32", neighbors="all")
+    yield pt.spmv_halo(1500, 6, 4, 9, seed=21, dtype="f32", band=120)
+    yield pt.spmv_halo(1200, 5, 2, 7, seed=22, dtype="f64", band=100)
+
+
+def check_adjoint_dense(lib):
+    rng = np.random.default_rng(17)
+    for p in adjoint_cases():
+        vt = np.float64 if p.dtype == "f64" else np.float32
+        src_of = forward_map(p, lib)
+        assert np.array_equal(src_of, forward_map(p, lib, form=1))
+        # integer-valued gradients: every order sums exactly
+        gi = rng.integers(-8, 9, size=len(src_of)).astype(vt)
+        want, cov = dense_transpose(p, src_of, np.where(src_of >= 0, gi, 0))
+        touched = np.zeros(len(want), dtype=bool)
+        touched[src_of[cov]] = True
+        for form in (0, 1):
+            got = as_values(oracle.backward(p, gi, form=form, lib=lib), vt)
+            assert np.array_equal(got[touched], want[touched].astype(vt)), (p.name, form)
+            assert (got[~touched] == 0).all()
+        # random positive data: within the rounding of a short sum
+        gr = rng.uniform(0.5, 1.5, size=len(src_of)).astype(vt)
+        want, _ = dense_transpose(p, src_of, np.where(src_of >= 0, gr, 0))
+        tol = 1e-12 if vt == np.float64 else 1e-5
+        for form in (0, 1):
+            got = as_values(oracle.backward(p, gr, form=form, lib=lib), vt).astype(np.float64)
+            assert np.allclose(got[touched], want[touched], rtol=tol, atol=0), (p.name, form)
+
+
+def check_accumulate_and_untouched(lib):
+    rng = np.random.default_rng(5)
+    for p in adjoint_cases():
+        vt = np.float64 if p.dtype == "f64" else np.float32
+        n_recv = p.recvbuf_bytes // np.dtype(vt).itemsize
+        n_send = p.sendbuf_bytes // np.dtype(vt).itemsize
+        g = rng.standard_normal(n_recv).astype(vt)
+        old = rng.standard_normal(n_send).astype(vt)
+        src_of = forward_map(p, lib)
+        touched = np.zeros(n_send, dtype=bool)
+        touched[src_of[src_of >= 0]] = True
+        for form in (0, 1):
+            plain = as_values(oracle.backward(p, g, old, form=form, lib=lib), vt)
+            acc = as_values(oracle.backward(p, g, old, form=form, accumulate=True, lib=lib), vt)
+            assert np.array_equal(plain[~touched], old[~touched])
+            assert np.array_equal(acc[~touched], old[~touched])
+            assert np.array_equal(acc[touched], (old[touched] + plain[touched]).astype(vt))
+
+
+def check_finite_difference(lib):
+    """Linear map: the central difference of L(x) = <w, forward(x)> along v equals
+    <backward(w), v>; checked in fp32 within 1e-3 relative."""
+    rng = np.random.default_rng(9)
+    p = pt.spmv_halo(2000, 8, 4, 10, seed=31, dtype="f32", band=150)
+    x = pt.spmv_x(p, 3)
+    nrecv = p.recvbuf_bytes // 4
+    w = rng.standard_normal(nrecv).astype(np.float32)
+    cov = forward_map(p, lib) >= 0
+    w[~cov] = 0
+    for form in (0, 1):
+        g = as_values(oracle.backward(p, w, form=form, lib=lib), np.float32).astype(np.float64)
+        for _ in range(3):
+            v = rng.standard_normal(len(x)).astype(np.float32)
+            h = np.float32(1e-2 * np.abs(x).max())
+
+            def L(z):
+                return float(np.dot(w.astype(np.float64),
+                                    as_values(oracle.standard(p, z, lib=lib), np.float32)))
+            fd = (L((x + h * v).astype(np.float32)) - L((x - h * v).astype(np.float32))) / (2 * h)
+            an = float(np.dot(g, v.astype(np.float64)))
+            assert abs(fd - an) <= 1e-3 * max(abs(an), 1e-6), (form, fd, an)
+
+
+# ------------------------------------------------------------------ errors ----
+
+def check_error_codes(lib):
+    def ring():
+        return load_golden("ring3.json")
+
+    g = ring()
+    assert oracle.validate(g, lib=lib) == 0
+    g = ring(); g.dests = g.dests.copy(); g.dests[0] = 5
+    assert oracle.validate(g, lib=lib) == oracle.ERR_RANK
+    g = ring(); g.dests = g.dests.copy(); g.dests[0] = 2          # r0 lists 2 twice
+    assert oracle.validate(g, lib=lib) == oracle.ERR_TRUNCATE
+    g = ring(); g.recvcounts = g.recvcounts.copy(); g.recvcounts[0] = 3
+    assert oracle.validate(g, lib=lib) == oracle.ERR_TRUNCATE
+    g = ring(); g.rdispls = g.rdispls.copy(); g.rdispls[3] = 9     # rank 2 block past the end
+    assert oracle.validate(g, lib=lib) == oracle.ERR_INDEX
+    g = ring(); g.sdispls = g.sdispls.copy(); g.sdispls[1] = -1
+    assert oracle.validate(g, lib=lib) == oracle.ERR_INDEX
+    g = ring(); g.rdispls = g.rdispls.copy(); g.rdispls[1] = 1     # rank 0 blocks overlap
+    assert oracle.validate(g, lib=lib) == oracle.ERR_OVERLAP
+    g = ring(); g.in_ptr = g.in_ptr.copy(); g.in_ptr[1] = 4        # not a CSR
+    assert oracle.validate(g, lib=lib) == oracle.ERR_ARG
+    # send index lists: out-of-range element
+    p = pt.spmv_halo(600, 4, 2, 6, seed=1, dtype="f64", band=80)
+    q = types.SimpleNamespace(**{k: getattr(p, k) for k in p.__dataclass_fields__})
+    q.send_idx = p.send_idx.copy()
+    q.send_idx[3] = 10 ** 6
+    assert oracle.validate(q, lib=lib) == oracle.ERR_INDEX
+    # receive global index that disagrees with the matched send index
+    q = types.SimpleNamespace(**{k: getattr(p, k) for k in p.__dataclass_fields__})
+    q.global_ridx = p.global_ridx.copy()
+    q.global_ridx[5] += 1
+    assert oracle.validate(q, lib=lib) == oracle.ERR_GIDX
+    # one global index carried by different bytes from two ranks of one node
+    g = load_golden("locality_dedup.json")
+    g.global_sidx = g.global_sidx.copy()
+    g.global_sidx[2] = 100        # rank 1's value now claims index 100, with other bytes
+    g.global_ridx = g.global_ridx.copy()
+    g.global_ridx[g.global_ridx == 102] = 100
+    assert oracle.validate(g, lib=lib) == 0
+    try:
+        oracle.locality(g, g.sendbuf, lib=lib)
+        raise AssertionError("duplicate index with different bytes accepted")
+    except oracle.OracleError as e:
+        assert e.code == oracle.ERR_DUP
+    sb = g.sendbuf.copy()
+    sb[2] = sb[0]                  # same bytes: legal, sent once
+    r, st = oracle.locality(g, sb, lib=lib)
+    assert st["U"] == 4
+
+
+ALL_CHECKS = [check_golden_forward, check_golden_multigraph_truncate, check_golden_locality,
+              check_golden_backward_order, check_bruteforce_stencil, check_bruteforce_spmv,
+              check_permutation_invariance, check_idempotent_and_untouched,
+              check_closed_forms_small, check_adjoint_dense, check_accumulate_and_untouched,
+              check_finite_difference, check_error_codes]
