@@ -1,0 +1,258 @@
+/*
+ * gbx.h -- C ABI of a GB300-native persistent neighbourhood all-to-all-v over an
+ * emulated distributed-graph communicator whose P ranks keep all their buffers in
+ * one GPU's memory.
+ *
+ * The operation is the one optimised by MPI Advance ("MPI Advance: Open-Source
+ * Message Passing Optimizations", arXiv 2309.07337):
+ *   - section 2.2, Listing 4: MPIX_Dist_graph_create_adjacent, then
+ *     MPIX_Neighbor_alltoallv_init, MPIX_Start, MPIX_Wait; all setup is paid once at
+ *     init (section 2.2, first paragraph);
+ *   - section 2.2, last paragraph: an optional unique global index per value sent and
+ *     received lets the locality-aware form send each value once per pair of nodes;
+ *   - section 1: locality-aware aggregation (one message per node pair).
+ * The meaning of the exchange is the MPI standard's MPI_Neighbor_alltoallv, which the
+ * paper calls (section 2.2, Listing 3) but does not restate.
+ *
+ * Conventions for every call
+ *   - Every function returns GBX_SUCCESS (0) or one of the GBX_ERR_* codes below;
+ *     gbx_error_string() gives its text.  On error no handle is returned and no
+ *     library memory is left allocated.
+ *   - The P emulated ranks live in one process.  Each per-rank MPI argument becomes a
+ *     CSR over ranks: in-edge arrays are indexed by the in-list CSR (in_ptr), out-edge
+ *     arrays by the out-list CSR (out_ptr).
+ *   - Unless stated otherwise, array arguments are DEVICE pointers (setup runs on the
+ *     GPU) and are only read during the call; the library keeps its own copies of
+ *     whatever it needs, so the caller may free them when the call returns.
+ *   - Data buffers (send, receive, gradients) are device memory owned by the caller,
+ *     bound to the request at init and used by every start; they must stay valid
+ *     until the request is freed (MPI persistent semantics) or re-bound.
+ *   - Handles are opaque and owned by the library; *_free releases them and sets the
+ *     handle to NULL.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = the legacy default stream).
+ *   - Nothing here allocates host-pinned memory or changes device settings.
+ */
+#ifndef GBX_H
+#define GBX_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- error codes (the CPU oracle uses the same numbers) ---- */
+#define GBX_SUCCESS          0
+#define GBX_ERR_ARG          1   /* NULL / negative / inconsistent argument, not a CSR  */
+#define GBX_ERR_RANK         2   /* neighbour rank outside [0, P)                        */
+#define GBX_ERR_TRUNCATE     3   /* unmatched edge, or paired counts differ (MPI_ERR_TRUNCATE) */
+#define GBX_ERR_INDEX        4   /* displacement, slot or element index out of range     */
+#define GBX_ERR_DUP          5   /* reserved: one global index with different bytes; the
+                                    library never reads payload at init, so only the CPU
+                                    oracle reports it                                     */
+#define GBX_ERR_GIDX         6   /* a receive global index differs from the matched send index */
+#define GBX_ERR_ACTIVE       7   /* start on a request already started                  */
+#define GBX_ERR_TIMEOUT      8   /* wait gave up after the request's timeout; the request
+                                    stays active and may be waited on again               */
+#define GBX_ERR_CUDA         9   /* a CUDA call failed                                   */
+#define GBX_ERR_NOMEM       10   /* device allocation failed                             */
+#define GBX_ERR_UNSUPPORTED 11   /* valid request the library does not implement         */
+#define GBX_ERR_OVERLAP     13   /* two receive blocks write the same bytes              */
+
+/* payload types: only the backward (which adds) needs to know them */
+#define GBX_BYTES 0
+#define GBX_F32   1
+#define GBX_F64   2
+
+/* algorithms */
+#define GBX_ALG_STANDARD 0   /* pack by send index list, block copy, unpack          */
+#define GBX_ALG_LOCALITY 1   /* direct intra-node copy + three-step aggregation      */
+
+typedef struct gbx_comm_s *gbx_comm_t;
+typedef struct gbx_graph_s *gbx_graph_t;
+typedef struct gbx_request_s *gbx_request_t;
+
+/* What a request does per start; filled by gbx_request_get_info. */
+typedef struct {
+    int kind;               /* 0 forward exchange, 1 backward (reverse) exchange       */
+    int algorithm;          /* GBX_ALG_*                                              */
+    int levels;             /* dependent kernel phases per start (1 or 3)             */
+    int launches;           /* kernels per start                                      */
+    int use_graph;          /* 1 if start replays a captured CUDA graph               */
+    int vec_bytes;          /* vector width of the dominant move kernel               */
+    int block;              /* threads per block of the dominant move kernel          */
+    int unroll;             /* chunks per thread per tile of the dominant kernel      */
+    int64_t elem_size;
+    int64_t V;              /* elements moved by the standard form                    */
+    int64_t E;              /* matched edges (messages), zero-count ones included     */
+    int64_t E_nonzero;      /* edges that carry data                                  */
+    int64_t V_direct;       /* locality form: elements moved inside a node            */
+    int64_t V_inter;        /* elements whose sender and receiver are on different nodes */
+    int64_t U;              /* locality form: distinct inter-node values (step 1 = step 2 volume) */
+    int64_t node_pairs;     /* locality form: node pairs with traffic (= step 2 messages) */
+    int64_t msgs_inter;     /* standard form: inter-node messages                     */
+    int64_t msgs_intra;     /* standard form: intra-node messages                     */
+    int64_t msgs_step1;     /* locality form: ranks sending to a different send leader */
+    int64_t msgs_step3;     /* locality form: receive leaders sending to another rank  */
+    int64_t rows;           /* backward: distinct source elements written             */
+    int64_t terms;          /* backward: additive terms read                          */
+    int64_t user_bytes;     /* 2*V*elem_size: bytes a user sees moved                 */
+    int64_t algo_bytes;     /* bytes the method must read and write per start,
+                               index and descriptor reads included                    */
+    int64_t device_bytes;   /* device memory the request owns                         */
+} gbx_request_info_t;
+
+const char *gbx_error_string(int code);
+int gbx_version(void);
+
+/* Emulated communicator of P ranks, ranks_per_node consecutive ranks per node
+ * (node(r) = r / ranks_per_node; the last node may be smaller).  Stands in for
+ * MPIX_Comm_init (section 2.1, Listing 2).  Host-only; no device memory. */
+int gbx_comm_create(int P, int ranks_per_node, gbx_comm_t *comm);
+int gbx_comm_free(gbx_comm_t *comm);
+
+/* Distributed graph (MPI_Dist_graph_create_adjacent, section 2.2 Listings 3-4) over
+ * all P ranks at once.
+ *   in_ptr[P+1], sources[n_in_edges]:   rank d's in-neighbours are
+ *                                       sources[in_ptr[d] .. in_ptr[d+1]-1];
+ *   out_ptr[P+1], destinations[n_out_edges]: likewise for out-neighbours.
+ *   sourceweights / destweights: accepted (may be NULL) and ignored, as is `reorder`
+ *                                (no rank reordering).
+ *   info: reserved, may be NULL.
+ * Device kernels validate the CSRs (GBX_ERR_ARG), the ranks (GBX_ERR_RANK) and match
+ * every out-edge r->d with an in-edge of d under the MPI multigraph rule (the t-th
+ * listing of d by r pairs with the t-th listing of r by d); an edge without a partner
+ * gives GBX_ERR_TRUNCATE.  Blocks on `stream` once to read the result.
+ * The graph keeps a pointer to `comm`, which must outlive it. */
+int gbx_dist_graph_create_adjacent(gbx_comm_t comm,
+                                   int64_t n_in_edges, const int *in_ptr, const int *sources,
+                                   const int *sourceweights,
+                                   int64_t n_out_edges, const int *out_ptr,
+                                   const int *destinations, const int *destweights,
+                                   const char *info, int reorder, void *stream,
+                                   gbx_graph_t *graph);
+int gbx_graph_free(gbx_graph_t *graph);
+
+/* Persistent neighbourhood all-to-all-v (MPIX_Neighbor_alltoallv_init, section 2.2
+ * Listing 4).  For every out-edge e of rank r to d, paired with in-edge i of d:
+ *     recv[d][rdispls[i] + k] = send[r][elem_r(sdispls[e] + k)],  0 <= k < sendcounts[e]
+ * where element j of rank r's send region starts at byte send_base[r] + j*elem_size of
+ * sendbuf, element j of d's receive region at byte recv_base[d] + j*elem_size of
+ * recvbuf, and elem_r(q) = send_idx[send_slot_ptr[r] + q] when send_idx is given (the
+ * pack-by-send-index-list step), else q (a user-packed send buffer).
+ *
+ *   sendbuf, sendbuf_bytes     device send buffer of all ranks and its size in bytes
+ *   send_base[P]               byte offset of each rank's send region (int64)
+ *   sendcounts, sdispls        per out-edge, in elements (int32, >= 0)
+ *   send_slot_ptr[P+1]         CSR of send slots; required with send_idx or global_sidx,
+ *                              then sdispls[e] + sendcounts[e] <= slots of r; else NULL
+ *   send_idx                   per send slot, element index in the rank's region; or NULL
+ *   recvbuf, recvbuf_bytes     device receive buffer of all ranks and its size
+ *   recv_base[P]               byte offset of each rank's receive region
+ *   recvcounts, rdispls        per in-edge, in elements; recvcounts must equal the paired
+ *                              sendcounts (else GBX_ERR_TRUNCATE)
+ *   recv_slot_ptr[P+1]         CSR of receive slots (bounds rdispls); required with
+ *                              global_ridx; else NULL
+ *   elem_size                  bytes per element (any positive size)
+ *   dtype                      GBX_BYTES, GBX_F32 or GBX_F64; only the backward uses it
+ *   global_sidx, global_ridx   unique global index of every send / receive slot (int64;
+ *                              section 2.2, last paragraph).  global_sidx is required by
+ *                              the locality form; global_ridx is optional and, when
+ *                              given, must equal the paired send index (GBX_ERR_GIDX).
+ *                              The same global index sent by two ranks of one node to
+ *                              the same remote node must carry identical bytes: it is
+ *                              sent once, from the first such sender in out-edge order.
+ *   graph, info, stream, request
+ *   info: "key=value;..." with
+ *       algorithm=standard|locality|auto   (default standard; auto times both and keeps
+ *                                          the faster; needs global_sidx)
+ *       graph=0|1          capture the start sequence in a CUDA graph (default 1)
+ *       autotune=0|1       time candidate kernel shapes at init (default 1)
+ *       vec=V block=B      force the move kernel's vector width / block size
+ *       timeout_ms=T       limit of gbx_wait (default 60000)
+ * Errors: GBX_ERR_ARG, _TRUNCATE, _INDEX, _GIDX, _OVERLAP (receive blocks must not
+ * overlap), _NOMEM, _CUDA.  Validation and map building run as device kernels; the
+ * call blocks on `stream` to read their status.  The autotuner's trial launches write
+ * the bound receive buffer (with the correct result for the send data present then).
+ * Element bytes are copied exactly; no value is converted. */
+int gbx_neighbor_alltoallv_init(const void *sendbuf, int64_t sendbuf_bytes,
+                                const int64_t *send_base, const int *sendcounts,
+                                const int *sdispls, const int64_t *send_slot_ptr,
+                                const int *send_idx,
+                                void *recvbuf, int64_t recvbuf_bytes,
+                                const int64_t *recv_base, const int *recvcounts,
+                                const int *rdispls, const int64_t *recv_slot_ptr,
+                                int64_t elem_size, int dtype,
+                                const int64_t *global_sidx, const int64_t *global_ridx,
+                                gbx_graph_t graph, const char *info, void *stream,
+                                gbx_request_t *request);
+
+/* Reverse exchange of a forward request: the transpose of its 0/1 map (the exchange is
+ * linear), so that a halo exchange can be differentiated.  grad_recv has the forward
+ * receive buffer's layout, grad_send the forward send buffer's.  Every source element
+ * read by at least one receive slot gets the sum of those slots' gradients:
+ *   standard forward: one left-to-right sum over the slots ordered by (destination rank,
+ *     receive position);
+ *   locality forward: the reverse of the three steps -- per distinct inter-node value
+ *     the sum over its slots in (rank, position) order, carried back across the node
+ *     pair, then per source element its groups folded in ascending destination node
+ *     (its own node's group = its direct slots in (rank, position) order).
+ * accumulate=0 stores the sum, accumulate=1 adds it to the existing value; elements no
+ * slot reads are never written.  Adds are IEEE round-to-nearest in the payload type
+ * (dtype of the forward must be GBX_F32 or GBX_F64, elem_size a multiple of it); the
+ * order is fixed, so results are bitwise reproducible.  The forward request must
+ * outlive the backward one.  info: graph=, autotune=, timeout_ms= as above. */
+int gbx_backward_init(gbx_request_t forward, const void *grad_recv, void *grad_send,
+                      int accumulate, const char *info, void *stream,
+                      gbx_request_t *request);
+
+/* MPIX_Start (section 2.2, Listing 4): enqueues one exchange on the request's stream
+ * (one CUDA graph launch, or eager kernel launches when graph=0).  GBX_ERR_ACTIVE if
+ * the request was started and not yet completed by wait/test. */
+int gbx_start(gbx_request_t request);
+
+/* MPIX_Wait (section 2.2, Listing 4): blocks the host until the started exchange has
+ * finished on the GPU, polling with a limit of timeout_ms; returns GBX_ERR_TIMEOUT
+ * (request still active) when the limit passes.  An inactive request returns at once. */
+int gbx_wait(gbx_request_t request);
+
+/* Non-blocking completion check: *flag = 1 and the request becomes inactive if done. */
+int gbx_test(gbx_request_t request, int *flag);
+
+/* Completes a started request without blocking the host: `stream` waits for it on the
+ * GPU and the request becomes inactive (stream-ordered use, e.g. autograd). */
+int gbx_wait_stream(gbx_request_t request, void *stream);
+
+/* Starts `count` inactive requests as one batch: all their move phases run as fused
+ * multi-pattern kernels (one launch per dependent phase, every pattern's tiles in the
+ * same grid), replayed from one CUDA graph built and cached on the first call for this
+ * exact request list (that first call allocates and blocks once).  The batch runs on
+ * requests[0]'s stream; each request completes through gbx_wait/gbx_waitall.  The
+ * requests must write disjoint memory. */
+int gbx_startall(int count, gbx_request_t *requests);
+int gbx_waitall(int count, gbx_request_t *requests);
+
+/* Re-binds the data buffers of an inactive request without redoing setup: `src` is the
+ * new send buffer (grad_recv for a backward request), `dst` the new receive buffer
+ * (grad_send); NULL keeps the old one.  The new buffers must have the sizes and at
+ * least the alignment of the old ones.  Stream-ordered on the request's stream. */
+int gbx_request_bind(gbx_request_t request, const void *src, void *dst);
+
+/* One exchange on HOST buffers: copies host_src (the whole bound source buffer, pinned
+ * host memory recommended) to the bound device source buffer, starts the exchange, and
+ * copies the bound destination buffer back to host_dst, all on the request's stream;
+ * then waits as gbx_wait does. */
+int gbx_start_host(gbx_request_t request, const void *host_src, void *host_dst);
+
+int gbx_request_get_info(gbx_request_t request, gbx_request_info_t *info);
+
+/* MPI_Request_free: waits for an active request, then releases its device memory and
+ * any cached batch that contains it. */
+int gbx_request_free(gbx_request_t *request);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GBX_H */

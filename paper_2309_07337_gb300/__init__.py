@@ -1,1 +1,291 @@
-"""GB300-native persistent neighbourhood all-to-all-v (placeholder; binding follows)."""
+"""GB300-native persistent neighbourhood all-to-all-v over emulated ranks in one GPU.
+
+Thin Python binding of the C ABI in include/gbx.h (libgbx.so, built in-tree by
+build.py): argument marshalling only, every step of the exchange runs in the library's
+CUDA kernels.  PyTorch supplies device memory and streams.  There is no CPU fallback:
+using the binding without the built library raises.
+
+Names follow MPI Advance (arXiv 2309.07337) section 2.2, Listing 4:
+dist_graph_create_adjacent, neighbor_alltoallv_init, start, wait.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Sequence
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libgbx.so")
+
+SUCCESS, ERR_ARG, ERR_RANK, ERR_TRUNCATE, ERR_INDEX, ERR_DUP, ERR_GIDX = 0, 1, 2, 3, 4, 5, 6
+ERR_ACTIVE, ERR_TIMEOUT, ERR_CUDA, ERR_NOMEM, ERR_UNSUPPORTED, ERR_OVERLAP = 7, 8, 9, 10, 11, 13
+BYTES, F32, F64 = 0, 1, 2
+ALG_STANDARD, ALG_LOCALITY = 0, 1
+DTYPE_CODES = {"bytes": BYTES, "f32": F32, "f64": F64}
+
+_vp = ctypes.c_void_p
+_i64 = ctypes.c_int64
+_pvp = ctypes.POINTER(ctypes.c_void_p)
+
+
+class RequestInfo(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int) for n in
+                ("kind", "algorithm", "levels", "launches", "use_graph", "vec_bytes", "block", "unroll")] + \
+               [(n, ctypes.c_int64) for n in
+                ("elem_size", "V", "E", "E_nonzero", "V_direct", "V_inter", "U", "node_pairs",
+                 "msgs_inter", "msgs_intra", "msgs_step1", "msgs_step3", "rows", "terms",
+                 "user_bytes", "algo_bytes", "device_bytes")]
+
+    def as_dict(self):
+        return {n: getattr(self, n) for n, _ in self._fields_}
+
+
+_lib = None
+
+
+def lib():
+    """The loaded libgbx.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: build it with __graft_entry__.build() "
+                           "(or python -m paper_2309_07337_gb300.build); there is no CPU fallback")
+    L = ctypes.CDLL(LIB_PATH)
+    sig = {
+        "gbx_comm_create": [ctypes.c_int, ctypes.c_int, _pvp],
+        "gbx_comm_free": [_pvp],
+        "gbx_dist_graph_create_adjacent": [_vp, _i64, _vp, _vp, _vp, _i64, _vp, _vp, _vp,
+                                           ctypes.c_char_p, ctypes.c_int, _vp, _pvp],
+        "gbx_graph_free": [_pvp],
+        "gbx_neighbor_alltoallv_init": [_vp, _i64, _vp, _vp, _vp, _vp, _vp, _vp, _i64, _vp, _vp,
+                                        _vp, _vp, _i64, ctypes.c_int, _vp, _vp, _vp,
+                                        ctypes.c_char_p, _vp, _pvp],
+        "gbx_backward_init": [_vp, _vp, _vp, ctypes.c_int, ctypes.c_char_p, _vp, _pvp],
+        "gbx_start": [_vp],
+        "gbx_wait": [_vp],
+        "gbx_test": [_vp, ctypes.POINTER(ctypes.c_int)],
+        "gbx_wait_stream": [_vp, _vp],
+        "gbx_startall": [ctypes.c_int, _pvp],
+        "gbx_waitall": [ctypes.c_int, _pvp],
+        "gbx_request_bind": [_vp, _vp, _vp],
+        "gbx_start_host": [_vp, _vp, _vp],
+        "gbx_request_get_info": [_vp, ctypes.POINTER(RequestInfo)],
+        "gbx_request_free": [_pvp],
+    }
+    for name, args in sig.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = ctypes.c_int
+    L.gbx_error_string.argtypes = [ctypes.c_int]
+    L.gbx_error_string.restype = ctypes.c_char_p
+    L.gbx_version.argtypes = []
+    L.gbx_version.restype = ctypes.c_int
+    _lib = L
+    return L
+
+
+class GbxError(RuntimeError):
+    def __init__(self, code: int, where: str = ""):
+        msg = lib().gbx_error_string(code).decode()
+        super().__init__(f"{where}: gbx error {code} ({msg})" if where else f"gbx error {code} ({msg})")
+        self.code = code
+
+
+def _check(rc: int, where: str):
+    if rc != SUCCESS:
+        raise GbxError(rc, where)
+
+
+def _ptr(t) -> Optional[int]:
+    if t is None:
+        return None
+    assert t.is_cuda and t.is_contiguous(), "device arrays must be contiguous CUDA tensors"
+    return t.data_ptr()
+
+
+def _nbytes(t) -> int:
+    return 0 if t is None else t.numel() * t.element_size()
+
+
+def _stream_handle(stream) -> Optional[int]:
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return stream.cuda_stream
+
+
+class Comm:
+    """Emulated communicator: P ranks, ranks_per_node consecutive ranks per node."""
+
+    def __init__(self, P: int, ranks_per_node: int):
+        h = ctypes.c_void_p()
+        _check(lib().gbx_comm_create(int(P), int(ranks_per_node), ctypes.byref(h)), "comm_create")
+        self.handle, self.P, self.ppn = h, int(P), int(ranks_per_node)
+
+    def free(self):
+        if self.handle:
+            lib().gbx_comm_free(ctypes.byref(self.handle))
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+class DistGraph:
+    """MPI_Dist_graph_create_adjacent over all ranks (CSR in/out lists, int32 CUDA tensors)."""
+
+    def __init__(self, comm: Comm, in_ptr, sources, out_ptr, dests, stream=None):
+        h = ctypes.c_void_p()
+        _check(lib().gbx_dist_graph_create_adjacent(
+            comm.handle, sources.numel(), _ptr(in_ptr), _ptr(sources), None,
+            dests.numel(), _ptr(out_ptr), _ptr(dests), None, None, 0, _stream_handle(stream),
+            ctypes.byref(h)), "dist_graph_create_adjacent")
+        self.handle, self.comm = h, comm
+
+    def free(self):
+        if self.handle:
+            lib().gbx_graph_free(ctypes.byref(self.handle))
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+class Request:
+    """Persistent request: start() / wait() (MPIX_Start / MPIX_Wait)."""
+
+    def __init__(self, handle, keep=()):
+        self.handle = handle
+        self._keep = list(keep)   # bound buffers stay alive as long as the request
+
+    def start(self):
+        _check(lib().gbx_start(self.handle), "start")
+
+    def wait(self):
+        _check(lib().gbx_wait(self.handle), "wait")
+
+    def test(self) -> bool:
+        f = ctypes.c_int(0)
+        _check(lib().gbx_test(self.handle, ctypes.byref(f)), "test")
+        return bool(f.value)
+
+    def wait_stream(self, stream=None):
+        _check(lib().gbx_wait_stream(self.handle, _stream_handle(stream)), "wait_stream")
+
+    def bind(self, src=None, dst=None):
+        _check(lib().gbx_request_bind(self.handle, _ptr(src), _ptr(dst)), "bind")
+        self._keep += [t for t in (src, dst) if t is not None]
+
+    def start_host(self, host_src, host_dst):
+        """One exchange on host tensors (copied in, exchanged, copied out)."""
+        _check(lib().gbx_start_host(self.handle, host_src.data_ptr(), host_dst.data_ptr()), "start_host")
+
+    def info(self) -> dict:
+        i = RequestInfo()
+        _check(lib().gbx_request_get_info(self.handle, ctypes.byref(i)), "get_info")
+        return i.as_dict()
+
+    def free(self):
+        if self.handle:
+            lib().gbx_request_free(ctypes.byref(self.handle))
+            self._keep = []
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def neighbor_alltoallv_init(sendbuf, send_base, sendcounts, sdispls, recvbuf, recv_base,
+                            recvcounts, rdispls, graph: DistGraph, elem_size: int, dtype: int = BYTES,
+                            send_slot_ptr=None, send_idx=None, recv_slot_ptr=None,
+                            global_sidx=None, global_ridx=None, info: str = "",
+                            stream=None) -> Request:
+    """MPIX_Neighbor_alltoallv_init over the emulated communicator (see include/gbx.h)."""
+    h = ctypes.c_void_p()
+    _check(lib().gbx_neighbor_alltoallv_init(
+        _ptr(sendbuf), _nbytes(sendbuf), _ptr(send_base), _ptr(sendcounts), _ptr(sdispls),
+        _ptr(send_slot_ptr), _ptr(send_idx), _ptr(recvbuf), _nbytes(recvbuf), _ptr(recv_base),
+        _ptr(recvcounts), _ptr(rdispls), _ptr(recv_slot_ptr), int(elem_size), int(dtype),
+        _ptr(global_sidx), _ptr(global_ridx), graph.handle, info.encode() if info else None,
+        _stream_handle(stream), ctypes.byref(h)), "neighbor_alltoallv_init")
+    return Request(h, keep=(sendbuf, recvbuf, graph))
+
+
+def backward_init(forward: Request, grad_recv, grad_send, accumulate: bool = False,
+                  info: str = "", stream=None) -> Request:
+    """Reverse exchange of a forward request (see include/gbx.h)."""
+    h = ctypes.c_void_p()
+    _check(lib().gbx_backward_init(forward.handle, _ptr(grad_recv), _ptr(grad_send),
+                                   int(bool(accumulate)), info.encode() if info else None,
+                                   _stream_handle(stream), ctypes.byref(h)), "backward_init")
+    return Request(h, keep=(grad_recv, grad_send, forward))
+
+
+def _handles(reqs: Sequence[Request]):
+    arr = (ctypes.c_void_p * len(reqs))(*[r.handle.value for r in reqs])
+    return arr
+
+
+def startall(reqs: Sequence[Request]):
+    _check(lib().gbx_startall(len(reqs), _handles(reqs)), "startall")
+
+
+def waitall(reqs: Sequence[Request]):
+    _check(lib().gbx_waitall(len(reqs), _handles(reqs)), "waitall")
+
+
+# --------------------------------------------------------------- conveniences
+
+class DevicePattern:
+    """A patterns.Pattern's integer arrays uploaded to the GPU (inputs only)."""
+
+    FIELDS = (("in_ptr", "int32"), ("sources", "int32"), ("out_ptr", "int32"), ("dests", "int32"),
+              ("sendcounts", "int32"), ("sdispls", "int32"), ("recvcounts", "int32"),
+              ("rdispls", "int32"), ("send_base", "int64"), ("recv_base", "int64"),
+              ("send_slot_ptr", "int64"), ("send_idx", "int32"), ("recv_slot_ptr", "int64"),
+              ("global_sidx", "int64"), ("global_ridx", "int64"))
+
+    def __init__(self, p, device="cuda"):
+        import numpy as np
+        import torch
+        self.p = p
+        for name, dt in self.FIELDS:
+            a = getattr(p, name, None)
+            setattr(self, name, None if a is None else
+                    torch.from_numpy(np.ascontiguousarray(a, dtype=dt)).to(device))
+
+
+class Exchange:
+    """Communicator + graph + persistent request for one pattern and its buffers.
+    Every array the pattern has is passed to the library (send lists, global indices)."""
+
+    def __init__(self, p, sendbuf, recvbuf, algorithm="standard", info="", dp: DevicePattern = None,
+                 stream=None, graph: DistGraph = None):
+        self.p = p
+        self.dp = dp or DevicePattern(p)
+        self.comm = graph.comm if graph is not None else Comm(p.P, p.ppn)
+        self.graph = graph or DistGraph(self.comm, self.dp.in_ptr, self.dp.sources, self.dp.out_ptr,
+                                        self.dp.dests, stream)
+        full = f"algorithm={algorithm}" + (";" + info if info else "")
+        dp = self.dp
+        self.request = neighbor_alltoallv_init(
+            sendbuf, dp.send_base, dp.sendcounts, dp.sdispls, recvbuf, dp.recv_base, dp.recvcounts,
+            dp.rdispls, self.graph, p.elem_size, DTYPE_CODES[p.dtype],
+            send_slot_ptr=dp.send_slot_ptr, send_idx=dp.send_idx, recv_slot_ptr=dp.recv_slot_ptr,
+            global_sidx=dp.global_sidx, global_ridx=dp.global_ridx, info=full, stream=stream)
+
+    def start(self):
+        self.request.start()
+
+    def wait(self):
+        self.request.wait()
+
+    def info(self):
+        return self.request.info()

@@ -1,0 +1,782 @@
+// gbx_api.cu -- the C ABI (include/gbx.h): communicator, distributed graph, persistent
+// requests (init / start / wait, MPI Advance section 2.2 Listing 4), batched start,
+// re-binding, the autotuner and CUDA-graph capture.
+#include <algorithm>
+#include <chrono>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <thread>
+
+#include "gbx_internal.cuh"
+
+struct Batch {
+    std::vector<gbx_request_s *> members;
+    DevPool mem;
+    std::vector<LevelLaunch> launches;
+    cudaGraphExec_t exec = nullptr;
+    cudaEvent_t done = nullptr;
+};
+
+extern "C" const char *gbx_error_string(int code) {
+    switch (code) {
+        case GBX_SUCCESS: return "success";
+        case GBX_ERR_ARG: return "invalid argument";
+        case GBX_ERR_RANK: return "neighbour rank out of range";
+        case GBX_ERR_TRUNCATE: return "unmatched edge or count mismatch between paired edges";
+        case GBX_ERR_INDEX: return "displacement or index out of range";
+        case GBX_ERR_DUP: return "one global index carried by different bytes";
+        case GBX_ERR_GIDX: return "receive global index differs from the paired send index";
+        case GBX_ERR_ACTIVE: return "request already active";
+        case GBX_ERR_TIMEOUT: return "wait timed out";
+        case GBX_ERR_CUDA: return "CUDA error";
+        case GBX_ERR_NOMEM: return "out of device memory";
+        case GBX_ERR_UNSUPPORTED: return "unsupported request";
+        case GBX_ERR_OVERLAP: return "receive blocks overlap";
+        default: return "unknown error";
+    }
+}
+
+extern "C" int gbx_version(void) { return 100; }
+
+// ------------------------------------------------------------------------ info
+struct Opts {
+    int algorithm = GBX_ALG_STANDARD;
+    int algorithm_auto = 0;
+    int graph = 1, autotune = 1, vec = 0, block = 0, timeout_ms = 60000;
+    bool ok = true;
+};
+
+static Opts parse_info(const char *info) {
+    Opts o;
+    if (!info) return o;
+    std::string s(info);
+    size_t pos = 0;
+    while (pos < s.size()) {
+        size_t end = s.find(';', pos);
+        if (end == std::string::npos) end = s.size();
+        std::string kv = s.substr(pos, end - pos);
+        pos = end + 1;
+        if (kv.empty()) continue;
+        size_t eq = kv.find('=');
+        if (eq == std::string::npos) { o.ok = false; continue; }
+        std::string k = kv.substr(0, eq), v = kv.substr(eq + 1);
+        if (k == "algorithm") {
+            if (v == "standard") o.algorithm = GBX_ALG_STANDARD;
+            else if (v == "locality") o.algorithm = GBX_ALG_LOCALITY;
+            else if (v == "auto") o.algorithm_auto = 1;
+            else o.ok = false;
+        } else if (k == "graph") o.graph = atoi(v.c_str()) != 0;
+        else if (k == "autotune") o.autotune = atoi(v.c_str()) != 0;
+        else if (k == "vec") o.vec = atoi(v.c_str());
+        else if (k == "block") o.block = atoi(v.c_str());
+        else if (k == "timeout_ms") o.timeout_ms = atoi(v.c_str());
+        else o.ok = false;
+    }
+    if (o.vec && !(o.vec == 1 || o.vec == 2 || o.vec == 4 || o.vec == 8 || o.vec == 16)) o.ok = false;
+    if (o.block && !(o.block == 128 || o.block == 256 || o.block == 512 || o.block == 1024)) o.ok = false;
+    if (o.timeout_ms <= 0) o.ok = false;
+    return o;
+}
+
+// ----------------------------------------------------------------- comm, graph
+extern "C" int gbx_comm_create(int P, int ranks_per_node, gbx_comm_t *comm) {
+    if (!comm) return GBX_ERR_ARG;
+    *comm = nullptr;
+    if (P <= 0 || ranks_per_node <= 0) return GBX_ERR_ARG;
+    gbx_comm_s *c = new gbx_comm_s;
+    c->P = P;
+    c->ppn = ranks_per_node;
+    c->nnodes = (P + ranks_per_node - 1) / ranks_per_node;
+    *comm = c;
+    return GBX_SUCCESS;
+}
+
+extern "C" int gbx_comm_free(gbx_comm_t *comm) {
+    if (!comm) return GBX_ERR_ARG;
+    delete *comm;
+    *comm = nullptr;
+    return GBX_SUCCESS;
+}
+
+extern "C" int gbx_dist_graph_create_adjacent(gbx_comm_t comm, int64_t n_in_edges, const int *in_ptr,
+                                              const int *sources, const int *sourceweights, int64_t n_out_edges,
+                                              const int *out_ptr, const int *destinations, const int *destweights,
+                                              const char *info, int reorder, void *stream, gbx_graph_t *graph) {
+    (void)sourceweights; (void)destweights; (void)info; (void)reorder;
+    if (!graph) return GBX_ERR_ARG;
+    *graph = nullptr;
+    if (!comm || n_in_edges < 0 || n_out_edges < 0 || !in_ptr || !out_ptr) return GBX_ERR_ARG;
+    if ((n_in_edges > 0 && !sources) || (n_out_edges > 0 && !destinations)) return GBX_ERR_ARG;
+    gbx_graph_s *g = new gbx_graph_s();
+    g->comm = comm;
+    g->P = comm->P;
+    g->ppn = comm->ppn;
+    g->nnodes = comm->nnodes;
+    cudaGetDevice(&g->device);
+    int rc = gbx_graph_setup(g, n_in_edges, in_ptr, sources, n_out_edges, out_ptr, destinations,
+                             (cudaStream_t)stream);
+    if (rc != GBX_SUCCESS) {
+        delete g;
+        return rc;
+    }
+    *graph = g;
+    return GBX_SUCCESS;
+}
+
+extern "C" int gbx_graph_free(gbx_graph_t *graph) {
+    if (!graph) return GBX_ERR_ARG;
+    delete *graph;
+    *graph = nullptr;
+    return GBX_SUCCESS;
+}
+
+// ------------------------------------------------------------------------- ops
+static int vec_of_align(uint64_t align) {
+    int v = 16;
+    while (v > 1 && (align & (uint64_t)(v - 1))) v >>= 1;
+    return v;
+}
+
+int gbx_make_copy_op(gbx_request_s *req, int level, const char *src, int src_role, char *dst, int dst_role,
+                     const Seg *segs, int64_t nseg, const int32_t *idx, int64_t nelem, int64_t algo_bytes) {
+    if (nelem <= 0) return GBX_SUCCESS;
+    HostOp op;
+    memset(&op, 0, sizeof(op));
+    op.kind = 0;
+    op.level = level;
+    op.units = nelem;
+    op.max_vec = vec_of_align(req->align);
+    op.min_vec = req->forced_vec ? std::min(req->forced_vec, op.max_vec) : std::max(1, op.max_vec / 2);
+    if (req->forced_vec) op.max_vec = op.min_vec;
+    op.block = 256;
+    op.persistent = 1;
+    op.algo_bytes = algo_bytes;
+    CopyDesc &d = op.cd;
+    d.src = src; d.dst = dst; d.segs = segs; d.idx = idx; d.nseg = nseg; d.nelem = nelem;
+    d.elem_size = req->elem_size; d.src_role = src_role; d.dst_role = dst_role;
+    const int64_t max_tiles = ceil_div(nelem * (req->elem_size / op.min_vec), GBX_TILE);
+    GBX_TRY(req->mem.get(&op.d_tile_seg, max_tiles + 1));
+    GBX_TRY(req->mem.get(&op.d_tile_e0, max_tiles + 1));
+    GBX_TRY(req->mem.alloc(&op.d_desc, sizeof(CopyDesc)));
+    GBX_TRY(req->mem.get(&op.d_self, 1));
+    GBX_TRY(req->mem.get(&op.d_self_prefix, 2));
+    d.tile_seg = op.d_tile_seg;
+    d.tile_e0 = op.d_tile_e0;
+    req->ops.push_back(op);
+    return GBX_SUCCESS;
+}
+
+int gbx_make_fold_op(gbx_request_s *req, int level, char *out, int out_role, const char *bufA, int a_role,
+                     const char *bufB, int b_role, const int64_t *row_ptr, const int64_t *row_out,
+                     const int64_t *terms, int64_t nrows, int64_t nterms, int accumulate) {
+    if (nrows <= 0) return GBX_SUCCESS;
+    HostOp op;
+    memset(&op, 0, sizeof(op));
+    op.kind = 1;
+    op.level = level;
+    op.units = nrows;
+    const int dsz = req->dtype == GBX_F64 ? 8 : 4;
+    op.max_vec = vec_of_align(req->align);
+    if (op.max_vec < dsz) return GBX_ERR_UNSUPPORTED;
+    op.min_vec = req->forced_vec ? std::max(dsz, std::min(req->forced_vec, op.max_vec)) : std::max(dsz, op.max_vec / 2);
+    if (req->forced_vec) op.max_vec = op.min_vec;
+    op.block = 256;
+    op.persistent = 1;
+    const int64_t s = req->elem_size;
+    op.algo_bytes = nterms * s + nrows * s * (accumulate ? 2 : 1) + nterms * 8 + nrows * 16;
+    FoldDesc &d = op.fd;
+    d.out = out; d.bufA = bufA; d.bufB = bufB; d.row_ptr = row_ptr; d.row_out = row_out; d.terms = terms;
+    d.nrows = nrows; d.elem_size = s; d.dtype = req->dtype; d.accumulate = accumulate;
+    d.out_role = out_role; d.a_role = a_role; d.b_role = b_role;
+    const int64_t max_tiles = ceil_div(nrows * (s / op.min_vec), GBX_TILE);
+    GBX_TRY(req->mem.get(&op.d_tile_e0, max_tiles + 1));
+    d.tile_e0 = op.d_tile_e0;
+    GBX_TRY(req->mem.alloc(&op.d_desc, sizeof(FoldDesc)));
+    GBX_TRY(req->mem.get(&op.d_self, 1));
+    GBX_TRY(req->mem.get(&op.d_self_prefix, 2));
+    req->ops.push_back(op);
+    return GBX_SUCCESS;
+}
+
+static int64_t op_tiles(const HostOp &op) { return op.kind == 0 ? op.cd.ntiles : op.fd.ntiles; }
+
+static int upload_desc(gbx_request_s *req, HostOp &op) {
+    if (op.kind == 0)
+        GBX_CUDA_TRY(cudaMemcpyAsync(op.d_desc, &op.cd, sizeof(CopyDesc), cudaMemcpyHostToDevice, req->stream));
+    else
+        GBX_CUDA_TRY(cudaMemcpyAsync(op.d_desc, &op.fd, sizeof(FoldDesc), cudaMemcpyHostToDevice, req->stream));
+    return GBX_SUCCESS;
+}
+
+// Sets the op's vector width: chunk geometry, tiles, tile->segment table, descriptor.
+static int set_vec(gbx_request_s *req, HostOp &op, int vec) {
+    const int64_t s = req->elem_size;
+    const int cpe = (int)(s / vec);
+    int shift = -1;
+    if ((cpe & (cpe - 1)) == 0) { shift = 0; while ((1 << shift) < cpe) shift++; }
+    const uint32_t magic = shift >= 0 ? 0u : (uint32_t)(((1ull << 32) + (uint64_t)cpe - 1) / (uint64_t)cpe);
+    if (op.kind == 0) {
+        CopyDesc &d = op.cd;
+        d.vec = vec; d.cpe = cpe; d.cpe_shift = shift; d.cpe_magic = magic;
+        d.nchunks = d.nelem * cpe;
+        d.ntiles = ceil_div(d.nchunks, GBX_TILE);
+        GBX_TRY(gbx_build_tile_meta(d.segs, d.nseg, cpe, d.ntiles, op.d_tile_seg, op.d_tile_e0, req->stream));
+    } else {
+        FoldDesc &d = op.fd;
+        d.vec = vec; d.cpe = cpe; d.cpe_shift = shift; d.cpe_magic = magic;
+        d.nchunks = d.nrows * cpe;
+        d.ntiles = ceil_div(d.nchunks, GBX_TILE);
+        GBX_TRY(gbx_build_tile_meta(nullptr, 0, cpe, d.ntiles, nullptr, op.d_tile_e0, req->stream));
+    }
+    GBX_TRY(upload_desc(req, op));
+    void *self = op.d_desc;
+    int64_t pre[2] = {0, op_tiles(op)};
+    GBX_CUDA_TRY(cudaMemcpyAsync(op.d_self, &self, sizeof(void *), cudaMemcpyHostToDevice, req->stream));
+    GBX_CUDA_TRY(cudaMemcpyAsync(op.d_self_prefix, pre, sizeof(pre), cudaMemcpyHostToDevice, req->stream));
+    GBX_CUDA_TRY(cudaStreamSynchronize(req->stream));
+    return GBX_SUCCESS;
+}
+
+static int op_vec(const HostOp &op) { return op.kind == 0 ? op.cd.vec : op.fd.vec; }
+
+static int grid_for(int kind, int dtype, int vec, int block, int persistent, int64_t tiles) {
+    if (!persistent) return (int)std::min<int64_t>(tiles, 1ll << 30);
+    int64_t g = (int64_t)gbx_num_sms() * gbx_occupancy(kind, dtype, vec, block);
+    return (int)std::max<int64_t>(1, std::min<int64_t>(g, tiles));
+}
+
+static cudaError_t launch_list(int kind, int dtype, int vec, void **d_ops, int64_t *d_prefix, int nops,
+                               int64_t tiles, int block, int grid, cudaStream_t st) {
+    if (kind == 0)
+        return gbx_launch_copy((const CopyDesc *const *)d_ops, d_prefix, nops, tiles, vec, block, grid, st);
+    return gbx_launch_fold((const FoldDesc *const *)d_ops, d_prefix, nops, tiles, dtype, vec, block, grid, st);
+}
+
+static cudaError_t launch_op_alone(gbx_request_s *req, HostOp &op, int block, int persistent) {
+    int64_t tiles = op_tiles(op);
+    const int vec = op_vec(op);
+    return launch_list(op.kind, req->dtype, vec, op.d_self, op.d_self_prefix, 1, tiles, block,
+                       grid_for(op.kind, req->dtype, vec, block, persistent, tiles), req->stream);
+}
+
+// ------------------------------------------------------------------ autotuner
+// Times every candidate shape of an op (vector width, block size, grid mode) with
+// CUDA events on the request's stream and keeps the fastest.  Results never depend on
+// the shape: every candidate moves the same bytes to the same places.  Chosen shapes are
+// cached by a signature of the op, so identical patterns are tuned once per process.
+struct TuneKey {
+    int kind, max_vec, min_vec, dtype;
+    int64_t units, nseg, elem_size, nterms;
+    bool operator<(const TuneKey &o) const {
+        return memcmp(this, &o, sizeof(TuneKey)) < 0;
+    }
+};
+struct TuneVal { int vec, block, persistent; float ms; };
+static std::map<TuneKey, TuneVal> g_tune_cache;
+static std::mutex g_tune_mu;
+
+static int time_op(gbx_request_s *req, HostOp &op, int block, int persistent, int reps, float *ms) {
+    cudaEvent_t a, b;
+    GBX_CUDA_TRY(cudaEventCreate(&a));
+    GBX_CUDA_TRY(cudaEventCreate(&b));
+    cudaError_t e = launch_op_alone(req, op, block, persistent);  // warm-up
+    float best = 1e30f;
+    for (int r = 0; r < reps && e == cudaSuccess; r++) {
+        cudaEventRecord(a, req->stream);
+        e = launch_op_alone(req, op, block, persistent);
+        cudaEventRecord(b, req->stream);
+        if (e == cudaSuccess) e = cudaEventSynchronize(b);
+        float t = 0;
+        if (e == cudaSuccess) cudaEventElapsedTime(&t, a, b);
+        best = std::min(best, t);
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    if (e != cudaSuccess) {
+        gbx_note_cuda_error(e, "tuning launch", __FILE__, __LINE__);
+        return GBX_ERR_CUDA;
+    }
+    *ms = best;
+    return GBX_SUCCESS;
+}
+
+static int tune_op(gbx_request_s *req, HostOp &op) {
+    TuneKey key;
+    memset(&key, 0, sizeof(key));
+    key.kind = op.kind; key.max_vec = op.max_vec; key.min_vec = op.min_vec; key.dtype = req->dtype;
+    key.units = op.units; key.elem_size = req->elem_size;
+    key.nseg = op.kind == 0 ? op.cd.nseg : 0;
+    key.nterms = op.kind == 1 ? op.fd.nchunks : 0;
+    int blocks[4] = {128, 256, 512, 1024};
+    if (!req->autotune || req->forced_block) {
+        op.block = req->forced_block ? req->forced_block : 256;
+        op.persistent = 1;
+        return set_vec(req, op, op.max_vec);
+    }
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end()) {
+            op.block = it->second.block;
+            op.persistent = it->second.persistent;
+            op.tuned_ms = it->second.ms;
+            return set_vec(req, op, it->second.vec);
+        }
+    }
+    TuneVal best = {op.max_vec, 256, 1, 1e30f};
+    for (int vec = op.max_vec; vec >= op.min_vec; vec >>= 1) {
+        GBX_TRY(set_vec(req, op, vec));
+        for (int bi = 0; bi < 4; bi++)
+            for (int pers = 1; pers >= 0; pers--) {
+                float ms = 0;
+                GBX_TRY(time_op(req, op, blocks[bi], pers, 3, &ms));
+                if (ms < best.ms) best = {vec, blocks[bi], pers, ms};
+            }
+        if (vec == 1) break;
+    }
+    op.block = best.block;
+    op.persistent = best.persistent;
+    op.tuned_ms = best.ms;
+    GBX_TRY(set_vec(req, op, best.vec));
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune_cache[key] = best;
+    return GBX_SUCCESS;
+}
+
+// ------------------------------------------------------- levels and the graph
+// One launch per (level, kind, vector class).  Single requests keep every vector class
+// in its own specialised launch; a batch (fixed_block != 0) puts all of a level's copy
+// ops into one launch (the generic kernel when their widths differ).
+static int build_levels(DevPool &mem, const std::vector<HostOp *> &ops, const std::vector<int> &dtypes,
+                        std::vector<LevelLaunch> &out, int fixed_block, cudaStream_t st) {
+    int nlev = 0;
+    for (HostOp *op : ops) nlev = std::max(nlev, op->level + 1);
+    for (int lv = 0; lv < nlev; lv++)
+        for (int kind = 0; kind < 2; kind++) {
+            std::vector<std::vector<size_t>> groups;
+            std::vector<std::pair<int, int>> keys;   // (dtype, vec) of each group
+            for (size_t i = 0; i < ops.size(); i++) {
+                HostOp *op = ops[i];
+                if (op->level != lv || op->kind != kind || op_tiles(*op) <= 0) continue;
+                // batches fuse copy ops of every width into one launch; fold ops stay grouped
+                // by payload class (the generic fold kernel needs far more registers)
+                std::pair<int, int> k = (fixed_block && kind == 0) ? std::make_pair(0, 0)
+                                                                   : std::make_pair(kind ? dtypes[i] : 0, op_vec(*op));
+                size_t g = 0;
+                while (g < keys.size() && keys[g] != k) g++;
+                if (g == keys.size()) { keys.push_back(k); groups.emplace_back(); }
+                groups[g].push_back(i);
+            }
+            for (size_t g = 0; g < groups.size(); g++) {
+                LevelLaunch L;
+                L.kind = kind;
+                L.nops = (int)groups[g].size();
+                // common payload type and vector width, or 0 (= mixed)
+                int dt = dtypes[groups[g][0]], vec = op_vec(*ops[groups[g][0]]);
+                for (size_t i : groups[g]) {
+                    if (dtypes[i] != dt) dt = -1;
+                    if (op_vec(*ops[i]) != vec) vec = 0;
+                }
+                if (dt < 0) vec = 0;
+                L.dtype = dt < 0 ? GBX_F32 : dt;
+                L.vec = vec;
+                std::vector<void *> ptrs;
+                std::vector<int64_t> pre(1, 0);
+                const HostOp *big = ops[groups[g][0]];
+                for (size_t i : groups[g]) {
+                    ptrs.push_back(ops[i]->d_desc);
+                    pre.push_back(pre.back() + op_tiles(*ops[i]));
+                    if (op_tiles(*ops[i]) > op_tiles(*big)) big = ops[i];
+                }
+                L.total_tiles = pre.back();
+                L.block = gbx_effective_block(L.vec, fixed_block ? fixed_block : big->block);
+                const int persistent = fixed_block ? 1 : big->persistent;
+                L.grid = grid_for(kind, L.dtype, L.vec, L.block, persistent, L.total_tiles);
+                GBX_TRY(mem.get(&L.d_ops, L.nops));
+                GBX_TRY(mem.get(&L.d_prefix, L.nops + 1));
+                GBX_CUDA_TRY(cudaMemcpyAsync(L.d_ops, ptrs.data(), sizeof(void *) * ptrs.size(),
+                                             cudaMemcpyHostToDevice, st));
+                GBX_CUDA_TRY(cudaMemcpyAsync(L.d_prefix, pre.data(), sizeof(int64_t) * pre.size(),
+                                             cudaMemcpyHostToDevice, st));
+                out.push_back(L);
+            }
+        }
+    GBX_CUDA_TRY(cudaStreamSynchronize(st));
+    return GBX_SUCCESS;
+}
+
+static cudaError_t enqueue_levels(const std::vector<LevelLaunch> &levels, cudaStream_t st) {
+    for (const LevelLaunch &L : levels) {
+        cudaError_t e = launch_list(L.kind, L.dtype, L.vec, L.d_ops, L.d_prefix, L.nops, L.total_tiles, L.block,
+                                    L.grid, st);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+static int capture(const std::vector<LevelLaunch> &levels, cudaGraphExec_t *exec) {
+    cudaStream_t cs;
+    GBX_CUDA_TRY(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        cudaError_t e2 = enqueue_levels(levels, cs);
+        e = cudaStreamEndCapture(cs, &graph);
+        if (e == cudaSuccess) e = e2;
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(exec, graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    cudaStreamDestroy(cs);
+    if (e != cudaSuccess) {
+        gbx_note_cuda_error(e, "graph capture", __FILE__, __LINE__);
+        return GBX_ERR_CUDA;
+    }
+    return GBX_SUCCESS;
+}
+
+static void fill_info(gbx_request_s *req) {
+    gbx_request_info_t &I = req->info;
+    I.kind = req->kind;
+    I.algorithm = req->algorithm;
+    int nlev = 0;
+    int64_t algo = 0;
+    const HostOp *big = nullptr;
+    for (const HostOp &op : req->ops) {
+        nlev = std::max(nlev, op.level + 1);
+        algo += op.algo_bytes;
+        if (!big || op.algo_bytes > big->algo_bytes) big = &op;
+    }
+    I.levels = nlev;
+    I.launches = (int)req->launches.size();
+    I.use_graph = req->use_graph;
+    I.algo_bytes = algo;
+    if (big) {
+        I.vec_bytes = big->kind == 0 ? big->cd.vec : big->fd.vec;
+        I.block = big->block;
+        I.unroll = GBX_TILE / big->block;
+    }
+    I.device_bytes = req->mem.bytes;
+}
+
+static int finalize(gbx_request_s *req) {
+    for (HostOp &op : req->ops) GBX_TRY(tune_op(req, op));
+    std::vector<HostOp *> ptrs;
+    std::vector<int> dts;
+    for (HostOp &op : req->ops) { ptrs.push_back(&op); dts.push_back(req->dtype); }
+    GBX_TRY(build_levels(req->mem, ptrs, dts, req->launches, 0, req->stream));
+    if (req->use_graph && !req->launches.empty()) GBX_TRY(capture(req->launches, &req->exec));
+    fill_info(req);
+    return GBX_SUCCESS;
+}
+
+static void destroy_batch(Batch *b) {
+    for (gbx_request_s *m : b->members) {
+        auto &v = m->batches;
+        v.erase(std::remove(v.begin(), v.end(), b), v.end());
+        if (m->pending == &b->done) {
+            cudaEventSynchronize(b->done);
+            m->pending = nullptr;
+            m->active = 0;
+        }
+    }
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->done) cudaEventDestroy(b->done);
+    delete b;
+}
+
+static void destroy_request(gbx_request_s *req) {
+    if (!req) return;
+    if (req->active) {
+        cudaEvent_t ev = req->pending ? *req->pending : req->done;
+        cudaEventSynchronize(ev);
+    }
+    while (!req->batches.empty()) destroy_batch(req->batches.back());
+    if (req->exec) cudaGraphExecDestroy(req->exec);
+    if (req->done) cudaEventDestroy(req->done);
+    delete req;
+}
+
+static gbx_request_s *new_request(const Opts &o, void *stream) {
+    gbx_request_s *req = new gbx_request_s();
+    cudaGetDevice(&req->device);
+    req->stream = (cudaStream_t)stream;
+    req->use_graph = o.graph;
+    req->autotune = o.autotune;
+    req->forced_vec = o.vec;
+    req->forced_block = o.block;
+    req->timeout_ms = o.timeout_ms;
+    if (cudaEventCreateWithFlags(&req->done, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        req->done = nullptr;
+    }
+    return req;
+}
+
+static float program_ms(gbx_request_s *req) {
+    // time of one eager pass over the levels (used by algorithm=auto)
+    cudaEvent_t a, b;
+    if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) return 1e30f;
+    enqueue_levels(req->launches, req->stream);
+    float best = 1e30f;
+    for (int r = 0; r < 3; r++) {
+        cudaEventRecord(a, req->stream);
+        enqueue_levels(req->launches, req->stream);
+        cudaEventRecord(b, req->stream);
+        cudaEventSynchronize(b);
+        float t = 0;
+        cudaEventElapsedTime(&t, a, b);
+        best = std::min(best, t);
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    return best;
+}
+
+extern "C" int gbx_neighbor_alltoallv_init(const void *sendbuf, int64_t sendbuf_bytes, const int64_t *send_base,
+                                           const int *sendcounts, const int *sdispls, const int64_t *send_slot_ptr,
+                                           const int *send_idx, void *recvbuf, int64_t recvbuf_bytes,
+                                           const int64_t *recv_base, const int *recvcounts, const int *rdispls,
+                                           const int64_t *recv_slot_ptr, int64_t elem_size, int dtype,
+                                           const int64_t *global_sidx, const int64_t *global_ridx, gbx_graph_t graph,
+                                           const char *info, void *stream, gbx_request_t *request) {
+    if (!request) return GBX_ERR_ARG;
+    *request = nullptr;
+    if (!graph || elem_size <= 0 || sendbuf_bytes < 0 || recvbuf_bytes < 0) return GBX_ERR_ARG;
+    if (dtype != GBX_BYTES && dtype != GBX_F32 && dtype != GBX_F64) return GBX_ERR_ARG;
+    if ((sendbuf_bytes > 0 && !sendbuf) || (recvbuf_bytes > 0 && !recvbuf)) return GBX_ERR_ARG;
+    if (!send_base || !recv_base) return GBX_ERR_ARG;
+    if (graph->E > 0 && (!sendcounts || !sdispls || !recvcounts || !rdispls)) return GBX_ERR_ARG;
+    if ((send_idx || global_sidx) && !send_slot_ptr) return GBX_ERR_ARG;
+    if (global_ridx && (!recv_slot_ptr || !global_sidx)) return GBX_ERR_ARG;
+    Opts o = parse_info(info);
+    if (!o.ok) return GBX_ERR_ARG;
+    if ((o.algorithm == GBX_ALG_LOCALITY || o.algorithm_auto) && !global_sidx) return GBX_ERR_ARG;
+
+    auto build = [&](int locality, gbx_request_s **out) -> int {
+        gbx_request_s *req = new_request(o, stream);
+        if (!req->done) { destroy_request(req); return GBX_ERR_CUDA; }
+        req->kind = 0;
+        req->graph = graph;
+        req->src = (const char *)sendbuf;
+        req->dst = (char *)recvbuf;
+        req->src_bytes = sendbuf_bytes;
+        req->dst_bytes = recvbuf_bytes;
+        req->elem_size = elem_size;
+        req->dtype = dtype;
+        int rc = gbx_setup_forward(req, send_base, sendcounts, sdispls, send_slot_ptr, send_idx, recv_base,
+                                   recvcounts, rdispls, recv_slot_ptr, global_sidx, global_ridx, locality);
+        if (rc == GBX_SUCCESS) rc = finalize(req);
+        if (rc != GBX_SUCCESS) { destroy_request(req); return rc; }
+        *out = req;
+        return GBX_SUCCESS;
+    };
+
+    gbx_request_s *req = nullptr;
+    if (o.algorithm_auto) {
+        gbx_request_s *a = nullptr, *b = nullptr;
+        GBX_TRY(build(0, &a));
+        int rc = build(1, &b);
+        if (rc != GBX_SUCCESS) { destroy_request(a); return rc; }
+        float ta = program_ms(a), tb = program_ms(b);
+        if (tb < ta) { destroy_request(a); req = b; }
+        else { destroy_request(b); req = a; }
+    } else {
+        GBX_TRY(build(o.algorithm == GBX_ALG_LOCALITY, &req));
+    }
+    *request = req;
+    return GBX_SUCCESS;
+}
+
+extern "C" int gbx_backward_init(gbx_request_t forward, const void *grad_recv, void *grad_send, int accumulate,
+                                 const char *info, void *stream, gbx_request_t *request) {
+    if (!request) return GBX_ERR_ARG;
+    *request = nullptr;
+    if (!forward || forward->kind != 0) return GBX_ERR_ARG;
+    if (forward->dtype != GBX_F32 && forward->dtype != GBX_F64) return GBX_ERR_ARG;
+    const int dsz = forward->dtype == GBX_F64 ? 8 : 4;
+    if (forward->elem_size % dsz) return GBX_ERR_ARG;
+    if ((forward->dst_bytes > 0 && !grad_recv) || (forward->src_bytes > 0 && !grad_send)) return GBX_ERR_ARG;
+    Opts o = parse_info(info);
+    if (!o.ok) return GBX_ERR_ARG;
+    gbx_request_s *req = new_request(o, stream);
+    if (!req->done) { destroy_request(req); return GBX_ERR_CUDA; }
+    req->kind = 1;
+    req->forward = forward;
+    req->graph = forward->graph;
+    req->src = (const char *)grad_recv;
+    req->dst = (char *)grad_send;
+    req->src_bytes = forward->dst_bytes;
+    req->dst_bytes = forward->src_bytes;
+    req->elem_size = forward->elem_size;
+    req->dtype = forward->dtype;
+    req->algorithm = forward->algorithm;
+    req->align = forward->align | (uint64_t)(uintptr_t)grad_recv | (uint64_t)(uintptr_t)grad_send;
+    int rc = gbx_setup_backward(req, accumulate ? 1 : 0);
+    if (rc == GBX_SUCCESS) rc = finalize(req);
+    if (rc != GBX_SUCCESS) { destroy_request(req); return rc; }
+    *request = req;
+    return GBX_SUCCESS;
+}
+
+// ------------------------------------------------------------- start / wait
+static int enqueue_start(gbx_request_s *req) {
+    if (req->use_graph && req->exec) {
+        GBX_CUDA_TRY(cudaGraphLaunch(req->exec, req->stream));
+    } else {
+        GBX_CUDA_TRY(enqueue_levels(req->launches, req->stream));
+    }
+    GBX_CUDA_TRY(cudaEventRecord(req->done, req->stream));
+    req->pending = nullptr;
+    req->active = 1;
+    return GBX_SUCCESS;
+}
+
+extern "C" int gbx_start(gbx_request_t req) {
+    if (!req) return GBX_ERR_ARG;
+    if (req->active) return GBX_ERR_ACTIVE;
+    return enqueue_start(req);
+}
+
+static cudaEvent_t pending_event(gbx_request_s *req) { return req->pending ? *req->pending : req->done; }
+
+extern "C" int gbx_test(gbx_request_t req, int *flag) {
+    if (!req || !flag) return GBX_ERR_ARG;
+    *flag = 1;
+    if (!req->active) return GBX_SUCCESS;
+    cudaError_t e = cudaEventQuery(pending_event(req));
+    if (e == cudaErrorNotReady) { *flag = 0; return GBX_SUCCESS; }
+    if (e != cudaSuccess) {
+        gbx_note_cuda_error(e, "event query", __FILE__, __LINE__);
+        return GBX_ERR_CUDA;
+    }
+    req->active = 0;
+    req->pending = nullptr;
+    return GBX_SUCCESS;
+}
+
+extern "C" int gbx_wait(gbx_request_t req) {
+    if (!req) return GBX_ERR_ARG;
+    if (!req->active) return GBX_SUCCESS;
+    const auto t0 = std::chrono::steady_clock::now();
+    int spins = 0;
+    for (;;) {
+        int flag = 0;
+        GBX_TRY(gbx_test(req, &flag));
+        if (flag) return GBX_SUCCESS;
+        const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+        if (ms > req->timeout_ms) return GBX_ERR_TIMEOUT;
+        if (++spins > 64) std::this_thread::sleep_for(std::chrono::microseconds(20));
+        else std::this_thread::yield();
+    }
+}
+
+extern "C" int gbx_wait_stream(gbx_request_t req, void *stream) {
+    if (!req) return GBX_ERR_ARG;
+    if (!req->active) return GBX_SUCCESS;
+    GBX_CUDA_TRY(cudaStreamWaitEvent((cudaStream_t)stream, pending_event(req), 0));
+    req->active = 0;
+    req->pending = nullptr;
+    return GBX_SUCCESS;
+}
+
+extern "C" int gbx_waitall(int count, gbx_request_t *reqs) {
+    if (count < 0 || (count > 0 && !reqs)) return GBX_ERR_ARG;
+    for (int i = 0; i < count; i++) GBX_TRY(gbx_wait(reqs[i]));
+    return GBX_SUCCESS;
+}
+
+extern "C" int gbx_startall(int count, gbx_request_t *reqs) {
+    if (count <= 0 || !reqs) return GBX_ERR_ARG;
+    for (int i = 0; i < count; i++) {
+        if (!reqs[i]) return GBX_ERR_ARG;
+        if (reqs[i]->active) return GBX_ERR_ACTIVE;
+        for (int j = 0; j < i; j++) if (reqs[j] == reqs[i]) return GBX_ERR_ARG;
+    }
+    std::vector<gbx_request_s *> key(reqs, reqs + count);
+    Batch *b = nullptr;
+    for (Batch *c : reqs[0]->batches)
+        if (c->members == key) { b = c; break; }
+    if (!b) {
+        b = new Batch();
+        b->members = key;
+        cudaStream_t st = reqs[0]->stream;
+        std::vector<HostOp *> ops;
+        std::vector<int> dts;
+        for (gbx_request_s *r : key)
+            for (HostOp &op : r->ops) { ops.push_back(&op); dts.push_back(r->dtype); }
+        int rc = build_levels(b->mem, ops, dts, b->launches, 256, st);
+        if (rc == GBX_SUCCESS && cudaEventCreateWithFlags(&b->done, cudaEventDisableTiming) != cudaSuccess)
+            rc = GBX_ERR_CUDA;
+        if (rc == GBX_SUCCESS && !b->launches.empty()) rc = capture(b->launches, &b->exec);
+        if (rc != GBX_SUCCESS) {
+            if (b->exec) cudaGraphExecDestroy(b->exec);
+            if (b->done) cudaEventDestroy(b->done);
+            delete b;
+            return rc;
+        }
+        for (gbx_request_s *r : key) r->batches.push_back(b);
+    }
+    cudaStream_t st = reqs[0]->stream;
+    if (b->exec) GBX_CUDA_TRY(cudaGraphLaunch(b->exec, st));
+    GBX_CUDA_TRY(cudaEventRecord(b->done, st));
+    for (gbx_request_s *r : key) {
+        r->active = 1;
+        r->pending = &b->done;
+    }
+    return GBX_SUCCESS;
+}
+
+// ---------------------------------------------------------------- re-binding
+extern "C" int gbx_request_bind(gbx_request_t req, const void *src, void *dst) {
+    if (!req) return GBX_ERR_ARG;
+    if (req->active) return GBX_ERR_ACTIVE;
+    const char *ns = src ? (const char *)src : req->src;
+    char *nd = dst ? (char *)dst : req->dst;
+    for (HostOp &op : req->ops) {
+        const int vec = op.kind == 0 ? op.cd.vec : op.fd.vec;
+        if (((uintptr_t)ns & (uintptr_t)(vec - 1)) || ((uintptr_t)nd & (uintptr_t)(vec - 1))) return GBX_ERR_ARG;
+    }
+    for (HostOp &op : req->ops) {
+        if (op.kind == 0) {
+            if (op.cd.src_role == ROLE_SRC) op.cd.src = ns;
+            if (op.cd.dst_role == ROLE_DST) op.cd.dst = nd;
+        } else {
+            if (op.fd.out_role == ROLE_DST) op.fd.out = nd;
+            if (op.fd.a_role == ROLE_SRC) op.fd.bufA = ns;
+        }
+        GBX_TRY(upload_desc(req, op));
+    }
+    req->src = ns;
+    req->dst = nd;
+    return GBX_SUCCESS;
+}
+
+extern "C" int gbx_start_host(gbx_request_t req, const void *host_src, void *host_dst) {
+    if (!req || (req->src_bytes > 0 && !host_src) || (req->dst_bytes > 0 && !host_dst)) return GBX_ERR_ARG;
+    if (req->active) return GBX_ERR_ACTIVE;
+    if (req->src_bytes > 0)
+        GBX_CUDA_TRY(cudaMemcpyAsync((void *)req->src, host_src, req->src_bytes, cudaMemcpyHostToDevice, req->stream));
+    GBX_TRY(enqueue_start(req));
+    if (req->dst_bytes > 0)
+        GBX_CUDA_TRY(cudaMemcpyAsync(host_dst, req->dst, req->dst_bytes, cudaMemcpyDeviceToHost, req->stream));
+    GBX_CUDA_TRY(cudaEventRecord(req->done, req->stream));
+    return gbx_wait(req);
+}
+
+extern "C" int gbx_request_get_info(gbx_request_t req, gbx_request_info_t *info) {
+    if (!req || !info) return GBX_ERR_ARG;
+    req->info.device_bytes = req->mem.bytes;
+    *info = req->info;
+    return GBX_SUCCESS;
+}
+
+extern "C" int gbx_request_free(gbx_request_t *req) {
+    if (!req) return GBX_ERR_ARG;
+    destroy_request(*req);
+    *req = nullptr;
+    return GBX_SUCCESS;
+}

@@ -1,0 +1,241 @@
+// gbx_internal.cuh -- internal declarations of the gbx library (not installed).
+//
+// Data model (all device memory):
+//   * A "move program" is a list of levels; every level is one or two fused kernel
+//     launches (copy ops, fold ops) whose ops are independent; levels run in order.
+//   * A COPY op moves elements: its element space [0, nelem) is cut into segments,
+//     each a run whose destination is contiguous; the source is contiguous or gathered
+//     through a per-element int32 index (the pack-by-send-index-list step of the
+//     neighbourhood exchange).  Standard forward = 1 copy op; locality forward =
+//     {direct, gather} -> {node-pair block copy} -> {redistribute}.
+//   * A FOLD op sums, for every output row, a fixed-order list of additive terms
+//     (the reverse exchange); terms carry a group-start bit so that one row can fold
+//     per-group partial sums (the node-blocked order).
+//   * Tiles are GBX_TILE chunks (a chunk = one vector of `vec` bytes); every launch
+//     uses blockDim * unroll == GBX_TILE, so ops of different patterns, element sizes and
+//     vector widths share one grid (the batched launch).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/gbx.h"
+
+#define GBX_TILE 1024                    // chunks per tile (block * unroll)
+#define GBX_TERM_GROUP (1ull << 63)      // fold term: first term of a group
+#define GBX_TERM_BUFB (1ull << 62)       // fold term: reads buffer B (else A)
+#define GBX_TERM_MASK ((1ull << 62) - 1)
+
+#define GBX_ERR_NONE 0x7fffffff          // device error word: "no error yet"
+
+// Buffer roles of an op's pointers (for re-binding).
+enum { ROLE_SRC = 0, ROLE_DST = 1, ROLE_AGG = 2, ROLE_NONE = 3 };
+
+struct Seg {
+    int64_t v0;       // first element of the segment in the op's element space
+    int64_t dst_off;  // byte offset of the segment's first destination element
+    int64_t src_off;  // byte offset of the source base (contiguous: of the first element)
+    int64_t idx_off;  // >= 0: element k reads index idx[idx_off + k]; < 0: contiguous
+};
+
+struct CopyDesc {
+    const char *src;
+    char *dst;
+    const Seg *segs;
+    const int32_t *idx;
+    const int64_t *tile_seg;  // ntiles + 1: segment holding each tile's first element
+    const int64_t *tile_e0;   // ntiles: first element of each tile
+    int64_t nseg, nelem, nchunks, ntiles, elem_size;
+    int32_t vec, cpe, cpe_shift;  // chunks per element; log2 of it, or -1
+    uint32_t cpe_magic;           // ceil(2^32 / cpe) when cpe is not a power of two
+    int32_t src_role, dst_role;
+};
+
+struct FoldDesc {
+    char *out;
+    const char *bufA;
+    const char *bufB;
+    const int64_t *row_ptr;   // nrows + 1
+    const int64_t *row_out;   // byte offset of each row's output element
+    const int64_t *terms;     // byte offset | GBX_TERM_GROUP | GBX_TERM_BUFB
+    const int64_t *tile_e0;   // ntiles: first row of each tile
+    int64_t nrows, nchunks, ntiles, elem_size;
+    int32_t vec, cpe, cpe_shift;
+    uint32_t cpe_magic;
+    int32_t dtype, accumulate;
+    int32_t out_role, a_role, b_role;
+};
+
+// ----------------------------------------------------------------------------- util
+#define GBX_CUDA_TRY(expr)                                  \
+    do {                                                    \
+        cudaError_t _e = (expr);                            \
+        if (_e != cudaSuccess) {                            \
+            gbx_note_cuda_error(_e, #expr, __FILE__, __LINE__); \
+            return _e == cudaErrorMemoryAllocation ? GBX_ERR_NOMEM : GBX_ERR_CUDA; \
+        }                                                   \
+    } while (0)
+
+#define GBX_TRY(expr)                  \
+    do {                               \
+        int _rc = (expr);              \
+        if (_rc != GBX_SUCCESS) return _rc; \
+    } while (0)
+
+void gbx_note_cuda_error(cudaError_t e, const char *what, const char *file, int line);
+
+static inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+static inline int bitlen_u64(uint64_t x) { int n = 0; while (x) { n++; x >>= 1; } return n; }
+
+// Device allocations owned by one object; freed together.
+struct DevPool {
+    std::vector<void *> ptrs;
+    int64_t bytes = 0;
+    int alloc(void **p, size_t n);   // GBX_SUCCESS / GBX_ERR_NOMEM
+    template <typename T>
+    int get(T **p, int64_t count) { return alloc(reinterpret_cast<void **>(p), (size_t)(count > 0 ? count : 1) * sizeof(T)); }
+    void release();
+    ~DevPool() { release(); }
+};
+
+// ------------------------------------------------------------------- primitives
+// Exclusive scan of n int64 values into out[0..n]; out[n] receives the total.
+int gbx_scan_i64(const int64_t *in, int64_t *out, int64_t n, cudaStream_t st, DevPool &ws);
+// Stable LSD radix sort of (key, val) pairs on the low `bits` bits of the keys.
+// On return *keys / *vals point at the sorted arrays (one of the two buffers given).
+int gbx_sort_pairs(uint64_t **keys, int64_t **vals, uint64_t *keys_alt, int64_t *vals_alt,
+                   int64_t n, int bits, cudaStream_t st, DevPool &ws);
+int gbx_read_err(int *d_err, cudaStream_t st);   // syncs, returns first (lowest) code
+int gbx_fill_i64(int64_t *p, int64_t v, int64_t n, cudaStream_t st);
+int gbx_iota_i64(int64_t *p, int64_t n, cudaStream_t st);
+int gbx_read_i64(const int64_t *d, int64_t *h, cudaStream_t st);
+
+// ------------------------------------------------------------------ move kernels
+// Kernels are specialised per vector width (copy) or (payload type, vector width)
+// (fold); vec == 0 selects the generic kernel that dispatches per tile, used when one
+// launch mixes ops of different widths (batched patterns).
+int gbx_num_sms(void);
+int gbx_effective_block(int vec, int block);
+int gbx_occupancy(int kind, int dtype, int vec, int block);   // resident blocks per SM
+cudaError_t gbx_launch_copy(const CopyDesc *const *ops, const int64_t *tile_prefix, int nops,
+                            int64_t total_tiles, int vec, int block, int grid, cudaStream_t st);
+cudaError_t gbx_launch_fold(const FoldDesc *const *ops, const int64_t *tile_prefix, int nops,
+                            int64_t total_tiles, int dtype, int vec, int block, int grid,
+                            cudaStream_t st);
+// Per-tile metadata: first unit (element / row) of each tile and, for copy ops, the
+// segment holding it (segs may be NULL for fold ops).
+int gbx_build_tile_meta(const Seg *segs, int64_t nseg, int cpe, int64_t ntiles, int64_t *tile_seg,
+                        int64_t *tile_e0, cudaStream_t st);
+
+// ------------------------------------------------------------------------ objects
+struct gbx_comm_s {
+    int P, ppn, nnodes;
+};
+
+struct gbx_graph_s {
+    gbx_comm_s *comm;
+    int P, ppn, nnodes, device;
+    int64_t E;
+    DevPool mem;
+    int *in_ptr, *sources, *out_ptr, *dests;  // library copies
+    int *in_owner, *out_owner;                // rank owning each in / out edge
+    int64_t *match_out;                       // out-edge -> in-edge
+    int64_t *match_in;                        // in-edge -> out-edge
+};
+
+// One op of a move program, host side.
+struct HostOp {
+    int kind;        // 0 copy, 1 fold
+    int level;
+    int64_t units;   // elements (copy) or rows (fold)
+    int max_vec;     // widest vector the alignment allows
+    int min_vec;     // narrowest vector the kernel accepts (fold: the payload type)
+    int block;       // tuned block size (block * unroll == GBX_TILE)
+    int persistent;  // tuned grid: 1 = resident blocks only, 0 = one block per tile
+    float tuned_ms;  // measured time of the tuned shape (0 if not tuned)
+    int64_t algo_bytes;
+    CopyDesc cd;     // host copies of the descriptor
+    FoldDesc fd;
+    void *d_desc;           // device descriptor
+    int64_t *d_tile_seg;    // copy: tile_seg storage sized for min_vec
+    int64_t *d_tile_e0;     // tile_e0 storage sized for min_vec
+    void **d_self;          // one-entry descriptor list for launching the op alone
+    int64_t *d_self_prefix; // {0, ntiles}
+};
+
+// One kernel launch of a level.
+struct LevelLaunch {
+    int kind;
+    int dtype;              // fold: payload type
+    int vec;                // vector width of every op, or 0 when they differ
+    int block;
+    int grid;
+    int nops;
+    int64_t total_tiles;
+    void **d_ops;           // device array of descriptor pointers
+    int64_t *d_prefix;      // device tile prefix (nops + 1)
+};
+
+struct Batch;
+
+struct gbx_request_s {
+    int device;
+    int kind;                // 0 forward, 1 backward
+    int algorithm;
+    int use_graph, autotune, forced_vec, forced_block;
+    int timeout_ms;
+    gbx_graph_s *graph;
+    gbx_request_s *forward;  // backward: its forward request
+    cudaStream_t stream;
+    cudaEvent_t done;
+    cudaEvent_t *pending;    // event to wait on while active (own or a batch's)
+    int active;
+    const char *src;         // bound buffers
+    char *dst;
+    int64_t src_bytes, dst_bytes;
+    int64_t elem_size;
+    int dtype;
+    DevPool mem;             // everything the request owns
+    std::vector<HostOp> ops;
+    std::vector<LevelLaunch> launches;
+    cudaGraphExec_t exec;
+    gbx_request_info_t info;
+    // maps kept for building the backward of this (forward) request
+    int64_t nseg;            // standard segments (nonzero edges) in receive order
+    Seg *segs_std;           // standard segments
+    int32_t *srcel;          // per element: source element index in its rank's region
+    int *seg_src_rank, *seg_dst_rank;
+    int64_t *segv0;          // nseg + 1 segment starts (last = V)
+    int64_t *send_base_copy; // P byte offsets of the send regions
+    uint64_t align;          // OR of every base offset, pointer and the element size
+    int64_t V;
+    // locality maps
+    int64_t U;
+    int64_t *val_pos;        // per element (standard numbering): aggregate slot, -1 if direct
+    int64_t *agg_rep_off;    // per aggregate slot: byte offset of its representative source
+    int32_t *agg_dst_node;   // per aggregate slot: destination node
+    Seg *segs_pair;          // per node pair: aggregate block (v0 = first slot, count by next)
+    int64_t npairs;
+    char *agg;               // locality scratch: send aggregate | receive aggregate
+    std::vector<Batch *> batches;
+};
+
+// Internal steps shared by the C ABI translation unit.
+int gbx_setup_forward(gbx_request_s *req, const int64_t *send_base, const int *sendcounts,
+                      const int *sdispls, const int64_t *send_slot_ptr, const int *send_idx,
+                      const int64_t *recv_base, const int *recvcounts, const int *rdispls,
+                      const int64_t *recv_slot_ptr, const int64_t *global_sidx,
+                      const int64_t *global_ridx, int want_locality);
+int gbx_setup_backward(gbx_request_s *bwd, int accumulate);
+int gbx_graph_setup(gbx_graph_s *g, int64_t n_in, const int *in_ptr, const int *sources,
+                    int64_t n_out, const int *out_ptr, const int *dests, cudaStream_t st);
+int gbx_make_copy_op(gbx_request_s *req, int level, const char *src, int src_role, char *dst,
+                     int dst_role, const Seg *segs, int64_t nseg, const int32_t *idx,
+                     int64_t nelem, int64_t algo_bytes);
+int gbx_make_fold_op(gbx_request_s *req, int level, char *out, int out_role, const char *bufA,
+                     int a_role, const char *bufB, int b_role, const int64_t *row_ptr,
+                     const int64_t *row_out, const int64_t *terms, int64_t nrows,
+                     int64_t nterms, int accumulate);

@@ -1,0 +1,372 @@
+// gbx_move.cu -- the exchange's data-movement kernels (the hot path).
+//
+// gbx_copy_kernel: for every element e of a copy op, with s = elem_size,
+//     dst[seg.dst_off + k*s .. +s) = src[seg.src_off + sel*s .. +s),  k = e - seg.v0,
+//     sel = idx[seg.idx_off + k] (gather through the send index list) or k (contiguous)
+//   This one kernel is the pack + block copy + unpack of the standard neighbourhood
+//   all-to-all-v (MPI Advance section 2.2: every message, packed by its send list and
+//   unpacked at its receive displacement, in one pass) and each step of the
+//   locality-aware form (direct copy, gather into node-pair aggregates, one block per
+//   node pair, redistribution).  Bytes are copied as opaque vectors: bit-exact.
+// gbx_fold_kernel: for every row of a fold op,
+//     out[row] (+)= fold over the row's groups, in order, of (fold over the group's terms)
+//   with IEEE round-to-nearest adds in the payload type: the reverse exchange.
+//
+// Both kernels walk tiles of GBX_TILE chunks (chunk = one `vec`-byte vector) with a
+// grid-stride loop; a launch may cover several ops (patterns), found by binary search
+// over the tile prefix, so uneven patterns share one grid.  Consecutive threads handle
+// consecutive chunks: destination writes are fully coalesced 16-byte stores, source
+// reads are 16-byte vector gathers of whole elements.  No shared memory, no barriers,
+// no waits: a launch always terminates.
+#include "gbx_internal.cuh"
+
+template <int VEC> struct VecT;
+template <> struct VecT<16> { typedef uint4 T; };
+template <> struct VecT<8> { typedef uint2 T; };
+template <> struct VecT<4> { typedef unsigned int T; };
+template <> struct VecT<2> { typedef unsigned short T; };
+template <> struct VecT<1> { typedef unsigned char T; };
+
+template <int VEC>
+__device__ __forceinline__ typename VecT<VEC>::T ldv(const char *p) {
+    return __ldg(reinterpret_cast<const typename VecT<VEC>::T *>(p));
+}
+template <int VEC>
+__device__ __forceinline__ typename VecT<VEC>::T ldv_plain(const char *p) {
+    return *reinterpret_cast<const typename VecT<VEC>::T *>(p);
+}
+template <int VEC>
+__device__ __forceinline__ void stv(char *p, typename VecT<VEC>::T v) {
+    *reinterpret_cast<typename VecT<VEC>::T *>(p) = v;
+}
+
+// Largest op index whose tile range starts at or before t.
+__device__ __forceinline__ int find_op(const int64_t *__restrict__ prefix, int nops, int64_t t) {
+    int lo = 0, hi = nops - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (__ldg(prefix + mid) <= t) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Unit (element or row) and chunk-in-unit of local chunk x of a tile whose first chunk
+// is chunk r0 of unit e0.  x < GBX_TILE + cpe, so the 32-bit magic multiply is exact.
+__device__ __forceinline__ uint32_t unit_of(uint32_t x, int cpe, int sh, uint32_t magic) {
+    if (sh >= 0) return x >> sh;
+    if (cpe < 32768) return __umulhi(x, magic);
+    return x / (uint32_t)cpe;
+}
+
+// ------------------------------------------------------------------------ copy
+template <int VEC, int U>
+__device__ __forceinline__ void copy_tile(const CopyDesc *__restrict__ d, int64_t t) {
+    typedef typename VecT<VEC>::T V;
+    constexpr int B = GBX_TILE / U;
+    const Seg *__restrict__ segs = d->segs;
+    const int cpe = d->cpe, sh = d->cpe_shift;
+    const uint32_t magic = d->cpe_magic;
+    const int64_t e0 = __ldg(d->tile_e0 + t);
+    const uint32_t r0 = (uint32_t)(t * GBX_TILE - e0 * cpe);
+    const int64_t left = d->nchunks - t * GBX_TILE;   // chunks of this op from the tile start
+    const int64_t slo = __ldg(d->tile_seg + t);
+    const int64_t shi = __ldg(d->tile_seg + t + 1);
+
+    int64_t e[U], pos[U];
+    uint32_t j[U];
+#pragma unroll
+    for (int u = 0; u < U; u++) {
+        const uint32_t x = r0 + (uint32_t)(u * B) + threadIdx.x;
+        const uint32_t el = unit_of(x, cpe, sh, magic);
+        j[u] = x - el * (uint32_t)cpe;
+        e[u] = e0 + el;
+        pos[u] = slo;
+    }
+    // branch-free search: largest segment in [slo, shi] starting at or before e[u]
+    const int64_t span = shi - slo;
+    int64_t step = 1;
+    while (step <= span) step <<= 1;
+    for (step >>= 1; step > 0; step >>= 1) {
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+            const int64_t cand = pos[u] + step;
+            if (cand <= shi && __ldg(&segs[cand].v0) <= e[u]) pos[u] = cand;
+        }
+    }
+    const int64_t s = d->elem_size;
+    const int32_t *__restrict__ idx = d->idx;
+#pragma unroll
+    for (int u = 0; u < U; u++) {   // e[u] := source byte offset, pos[u] := destination byte offset
+        const Seg *sg = segs + pos[u];
+        const int64_t k = e[u] - __ldg(&sg->v0);
+        const int64_t io = __ldg(&sg->idx_off);
+        const bool ok = (int64_t)(u * B + threadIdx.x) < left;
+        const int64_t sel = (io >= 0 && ok) ? (int64_t)__ldg(idx + io + k) : k;
+        e[u] = __ldg(&sg->src_off) + sel * s + (int64_t)j[u] * VEC;
+        pos[u] = __ldg(&sg->dst_off) + k * s + (int64_t)j[u] * VEC;
+    }
+    V val[U];
+#pragma unroll
+    for (int u = 0; u < U; u++)
+        if ((int64_t)(u * B + threadIdx.x) < left) val[u] = ldv<VEC>(d->src + e[u]);
+#pragma unroll
+    for (int u = 0; u < U; u++)
+        if ((int64_t)(u * B + threadIdx.x) < left) stv<VEC>(d->dst + pos[u], val[u]);
+}
+
+// VEC > 0: every op of the launch has that vector width; VEC == 0: mixed widths
+// (batched patterns), dispatched per tile.
+template <int VEC, int U>
+__global__ void __launch_bounds__(GBX_TILE / U)
+gbx_copy_kernel(const CopyDesc *const *__restrict__ ops, const int64_t *__restrict__ prefix,
+                int nops, int64_t total_tiles) {
+    for (int64_t t = blockIdx.x; t < total_tiles; t += gridDim.x) {
+        const int op = nops > 1 ? find_op(prefix, nops, t) : 0;
+        const CopyDesc *d = ops[op];
+        const int64_t lt = t - __ldg(prefix + op);
+        if (VEC) {
+            copy_tile<VEC ? VEC : 1, U>(d, lt);
+        } else {
+            switch (d->vec) {
+                case 16: copy_tile<16, U>(d, lt); break;
+                case 8: copy_tile<8, U>(d, lt); break;
+                case 4: copy_tile<4, U>(d, lt); break;
+                case 2: copy_tile<2, U>(d, lt); break;
+                default: copy_tile<1, U>(d, lt); break;
+            }
+        }
+    }
+}
+
+// ------------------------------------------------------------------------ fold
+// Payload vectors: the CUDA vector type of `VEC` bytes of T, added component-wise with
+// IEEE round-to-nearest adds (never contracted, never reassociated).
+template <typename T, int VEC> struct PackT;
+template <> struct PackT<double, 16> { typedef double2 T; };
+template <> struct PackT<double, 8> { typedef double T; };
+template <> struct PackT<float, 16> { typedef float4 T; };
+template <> struct PackT<float, 8> { typedef float2 T; };
+template <> struct PackT<float, 4> { typedef float T; };
+
+__device__ __forceinline__ double2 padd(double2 a, double2 b) { return make_double2(__dadd_rn(a.x, b.x), __dadd_rn(a.y, b.y)); }
+__device__ __forceinline__ double padd(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ float4 padd(float4 a, float4 b) {
+    return make_float4(__fadd_rn(a.x, b.x), __fadd_rn(a.y, b.y), __fadd_rn(a.z, b.z), __fadd_rn(a.w, b.w));
+}
+__device__ __forceinline__ float2 padd(float2 a, float2 b) { return make_float2(__fadd_rn(a.x, b.x), __fadd_rn(a.y, b.y)); }
+__device__ __forceinline__ float padd(float a, float b) { return __fadd_rn(a, b); }
+
+template <typename P>
+__device__ __forceinline__ P pload(const char *p) { return __ldg(reinterpret_cast<const P *>(p)); }
+
+template <typename T, int VEC, int U>
+__device__ __forceinline__ void fold_tile(const FoldDesc *__restrict__ d, int64_t t) {
+    typedef typename PackT<T, VEC>::T PK;
+    constexpr int B = GBX_TILE / U;
+    const int cpe = d->cpe, sh = d->cpe_shift;
+    const uint32_t magic = d->cpe_magic;
+    const int64_t e0 = __ldg(d->tile_e0 + t);
+    const uint32_t r0 = (uint32_t)(t * GBX_TILE - e0 * cpe);
+    const int64_t left = d->nchunks - t * GBX_TILE;
+    const int64_t *__restrict__ terms = d->terms;
+    int64_t rb[U], re[U];
+    uint32_t jv[U];
+    bool has[U];
+    PK grp[U], tot[U];
+#pragma unroll
+    for (int u = 0; u < U; u++) {
+        const uint32_t x = r0 + (uint32_t)(u * B) + threadIdx.x;
+        const uint32_t el = unit_of(x, cpe, sh, magic);
+        jv[u] = (x - el * (uint32_t)cpe) * VEC;
+        const bool ok = (int64_t)(u * B + threadIdx.x) < left;
+        const int64_t row = e0 + el;
+        rb[u] = ok ? __ldg(d->row_ptr + row) : 0;
+        re[u] = ok ? __ldg(d->row_ptr + row + 1) : 0;
+        has[u] = false;
+    }
+    for (int64_t m = 0;; m++) {
+        bool any = false;
+        int64_t tm[U];
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+            tm[u] = 0;
+            if (rb[u] + m < re[u]) { tm[u] = __ldg(terms + rb[u] + m); any = true; }
+        }
+        if (!any) break;
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+            if (rb[u] + m >= re[u]) continue;
+            const uint64_t w = (uint64_t)tm[u];
+            const char *base = (w & GBX_TERM_BUFB) ? d->bufB : d->bufA;
+            const PK x = pload<PK>(base + (int64_t)(w & GBX_TERM_MASK) + jv[u]);
+            if (m == 0) {
+                grp[u] = x;
+            } else if (w & GBX_TERM_GROUP) {
+                tot[u] = has[u] ? padd(tot[u], grp[u]) : grp[u];
+                has[u] = true;
+                grp[u] = x;
+            } else {
+                grp[u] = padd(grp[u], x);
+            }
+        }
+    }
+#pragma unroll
+    for (int u = 0; u < U; u++) {
+        if ((int64_t)(u * B + threadIdx.x) >= left) continue;
+        const uint32_t x = r0 + (uint32_t)(u * B) + threadIdx.x;
+        const int64_t row = e0 + unit_of(x, cpe, sh, magic);
+        PK r = has[u] ? padd(tot[u], grp[u]) : grp[u];
+        PK *o = reinterpret_cast<PK *>(d->out + __ldg(d->row_out + row) + jv[u]);
+        if (d->accumulate) r = padd(*o, r);
+        *o = r;
+    }
+}
+
+// CLS 1..5: every op of the launch is (f64,16) (f64,8) (f32,16) (f32,8) (f32,4);
+// CLS 0: mixed (batched patterns), dispatched per tile.
+template <int CLS, int U>
+__global__ void __launch_bounds__(GBX_TILE / U)
+gbx_fold_kernel(const FoldDesc *const *__restrict__ ops, const int64_t *__restrict__ prefix,
+                int nops, int64_t total_tiles) {
+    for (int64_t t = blockIdx.x; t < total_tiles; t += gridDim.x) {
+        const int op = nops > 1 ? find_op(prefix, nops, t) : 0;
+        const FoldDesc *d = ops[op];
+        const int64_t lt = t - __ldg(prefix + op);
+        const int cls = CLS ? CLS : (d->dtype == GBX_F64 ? (d->vec == 16 ? 1 : 2)
+                                                         : (d->vec == 16 ? 3 : d->vec == 8 ? 4 : 5));
+        switch (cls) {
+            case 1: fold_tile<double, 16, U>(d, lt); break;
+            case 2: fold_tile<double, 8, U>(d, lt); break;
+            case 3: fold_tile<float, 16, U>(d, lt); break;
+            case 4: fold_tile<float, 8, U>(d, lt); break;
+            default: fold_tile<float, 4, U>(d, lt); break;
+        }
+    }
+}
+
+// ------------------------------------------------------------------- launching
+static int g_num_sms = 0;
+
+int gbx_num_sms(void) {
+    if (!g_num_sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
+        if (g_num_sms <= 0) g_num_sms = 1;
+    }
+    return g_num_sms;
+}
+
+typedef void (*CopyFn)(const CopyDesc *const *, const int64_t *, int, int64_t);
+typedef void (*FoldFn)(const FoldDesc *const *, const int64_t *, int, int64_t);
+
+template <int VEC>
+static CopyFn copy_fn_u(int block) {
+    switch (block) {
+        case 128: return gbx_copy_kernel<VEC, 8>;
+        case 256: return gbx_copy_kernel<VEC, 4>;
+        case 512: return gbx_copy_kernel<VEC, 2>;
+        default: return gbx_copy_kernel<VEC, 1>;
+    }
+}
+
+static CopyFn copy_fn(int vec, int block) {
+    switch (vec) {
+        case 16: return copy_fn_u<16>(block);
+        case 8: return copy_fn_u<8>(block);
+        case 4: return copy_fn_u<4>(block);
+        case 2: return copy_fn_u<2>(block);
+        case 1: return copy_fn_u<1>(block);
+        default: return block == 128 ? gbx_copy_kernel<0, 4> : copy_fn_u<0>(block);  // mixed: U <= 4
+    }
+}
+
+template <int CLS>
+static FoldFn fold_fn_u(int block) {
+    switch (block) {
+        case 128: return gbx_fold_kernel<CLS, 8>;
+        case 256: return gbx_fold_kernel<CLS, 4>;
+        case 512: return gbx_fold_kernel<CLS, 2>;
+        default: return gbx_fold_kernel<CLS, 1>;
+    }
+}
+
+static int fold_cls(int dtype, int vec) {
+    if (vec == 0) return 0;
+    if (dtype == GBX_F64) return vec == 16 ? 1 : 2;
+    return vec == 16 ? 3 : vec == 8 ? 4 : 5;
+}
+
+static FoldFn fold_fn(int dtype, int vec, int block) {
+    switch (fold_cls(dtype, vec)) {
+        case 1: return fold_fn_u<1>(block);
+        case 2: return fold_fn_u<2>(block);
+        case 3: return fold_fn_u<3>(block);
+        case 4: return fold_fn_u<4>(block);
+        case 5: return fold_fn_u<5>(block);
+        default: return block == 128 ? gbx_fold_kernel<0, 4> : fold_fn_u<0>(block);
+    }
+}
+
+// Blocks of the mixed kernels never go below 256 threads (their unroll is capped at 4).
+int gbx_effective_block(int vec_class, int block) { return (vec_class == 0 && block < 256) ? 256 : block; }
+
+int gbx_occupancy(int kind, int dtype, int vec, int block) {
+    const void *f = kind == 0 ? (const void *)copy_fn(vec, block) : (const void *)fold_fn(dtype, vec, block);
+    int n = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, f, gbx_effective_block(vec, block), 0);
+    return n > 0 ? n : 1;
+}
+
+static int clamp_grid(int grid, int64_t total_tiles) {
+    if (grid <= 0 || grid > total_tiles) grid = (int)(total_tiles < (1ll << 30) ? total_tiles : (1ll << 30));
+    return grid;
+}
+
+cudaError_t gbx_launch_copy(const CopyDesc *const *ops, const int64_t *tile_prefix, int nops, int64_t total_tiles,
+                            int vec, int block, int grid, cudaStream_t st) {
+    if (total_tiles <= 0) return cudaSuccess;
+    CopyFn f = copy_fn(vec, block);
+    f<<<clamp_grid(grid, total_tiles), gbx_effective_block(vec, block), 0, st>>>(ops, tile_prefix, nops, total_tiles);
+    return cudaGetLastError();
+}
+
+cudaError_t gbx_launch_fold(const FoldDesc *const *ops, const int64_t *tile_prefix, int nops, int64_t total_tiles,
+                            int dtype, int vec, int block, int grid, cudaStream_t st) {
+    if (total_tiles <= 0) return cudaSuccess;
+    FoldFn f = fold_fn(dtype, vec, block);
+    f<<<clamp_grid(grid, total_tiles), gbx_effective_block(vec, block), 0, st>>>(ops, tile_prefix, nops, total_tiles);
+    return cudaGetLastError();
+}
+
+// tile_e0[t] = first unit of tile t; tile_seg[t] = segment holding it (copy ops);
+// tile_seg[ntiles] = nseg - 1
+__global__ void tile_meta_kernel(const Seg *__restrict__ segs, int64_t nseg, int cpe, int64_t ntiles,
+                                 int64_t *ts, int64_t *te0) {
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t <= ntiles;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        if (t == ntiles) {
+            if (ts) ts[t] = nseg - 1;
+            continue;
+        }
+        const int64_t e = (t * GBX_TILE) / cpe;
+        te0[t] = e;
+        if (!ts) continue;
+        int64_t lo = 0, hi = nseg - 1;
+        while (lo < hi) {
+            int64_t mid = (lo + hi + 1) >> 1;
+            if (segs[mid].v0 <= e) lo = mid; else hi = mid - 1;
+        }
+        ts[t] = lo;
+    }
+}
+
+int gbx_build_tile_meta(const Seg *segs, int64_t nseg, int cpe, int64_t ntiles, int64_t *tile_seg,
+                        int64_t *tile_e0, cudaStream_t st) {
+    int64_t n = ntiles + 1;
+    int64_t g = ceil_div(n, 256);
+    if (g > 65535 * 16) g = 65535 * 16;
+    tile_meta_kernel<<<(unsigned)g, 256, 0, st>>>(segs, nseg, cpe, ntiles, tile_seg, tile_e0);
+    GBX_CUDA_TRY(cudaGetLastError());
+    return GBX_SUCCESS;
+}

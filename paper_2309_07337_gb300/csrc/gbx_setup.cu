@@ -1,0 +1,1017 @@
+// gbx_setup.cu -- device-side setup of the persistent exchange (run once per init).
+//
+// MPI Advance section 2.2: the persistent neighbourhood collective pays every setup
+// cost once, at init, so that start only moves data.  Here that setup runs on the GPU:
+//   graph:    CSR and rank validation; MPI multigraph matching of every out-edge with an
+//             in-edge (both edge lists stably sorted by (receiver, sender): the t-th
+//             listing pairs with the t-th listing);
+//   forward:  count / bound / global-index validation, receive-order segments (one per
+//             message), per-element source indices (the pack-by-send-list step), the
+//             overlap check, and for the locality-aware form (section 1 and section 2.2,
+//             last paragraph) the node-pair aggregates: inter-node elements keyed by
+//             (node pair, global index), deduplicated, ordered by (node pair,
+//             representative rank, global index), plus the step 1 / 2 / 3 descriptors;
+//   backward: reverse maps -- per source element, its receive slots in the fixed order
+//             (a stable sort of the forward's elements by source offset).
+// Errors go to a device word with atomicMin, so the lowest code found wins; the host
+// reads it once per stage.  No kernel waits on another block.
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+
+#include "gbx_internal.cuh"
+
+#define SETUP_T 256
+
+static unsigned grid_of(int64_t n) {
+    int64_t g = ceil_div(n > 0 ? n : 1, SETUP_T);
+    if (g > 65535ll * 32) g = 65535ll * 32;
+    return (unsigned)g;
+}
+
+#define FOR_EACH(i, n) \
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < (n); i += (int64_t)gridDim.x * blockDim.x)
+
+__device__ __forceinline__ void set_err(int *err, int code) { atomicMin(err, code); }
+
+// largest i in [0, n) with a[i] <= x (a non-decreasing, a[0] <= x)
+template <typename T>
+__device__ __forceinline__ int64_t upper_index(const T *a, int64_t n, int64_t x) {
+    int64_t lo = 0, hi = n - 1;
+    while (lo < hi) {
+        int64_t mid = (lo + hi + 1) >> 1;
+        if ((int64_t)a[mid] <= x) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// ------------------------------------------------------------------------ graph
+__global__ void csr_check_kernel(const int *ptr, int P, int64_t n, int *err) {
+    FOR_EACH(r, (int64_t)P + 1) {
+        if (r == 0 && ptr[0] != 0) set_err(err, GBX_ERR_ARG);
+        if (r == P && (int64_t)ptr[P] != n) set_err(err, GBX_ERR_ARG);
+        if (r < P && ptr[r + 1] < ptr[r]) set_err(err, GBX_ERR_ARG);
+    }
+}
+
+__global__ void rank_check_kernel(const int *ranks, int64_t n, int P, int *err) {
+    FOR_EACH(i, n) if (ranks[i] < 0 || ranks[i] >= P) set_err(err, GBX_ERR_RANK);
+}
+
+__global__ void owner_kernel(const int *ptr, int P, int64_t n, int *owner) {
+    FOR_EACH(e, n) owner[e] = (int)upper_index(ptr, P, e);
+}
+
+// key = (receiver << rb) | sender for both edge lists; val = edge index
+__global__ void edge_key_kernel(const int *owner, const int *peer, int64_t n, int rb, int owner_is_receiver,
+                                uint64_t *keys, int64_t *vals) {
+    FOR_EACH(e, n) {
+        uint64_t recv = owner_is_receiver ? (uint64_t)owner[e] : (uint64_t)peer[e];
+        uint64_t send = owner_is_receiver ? (uint64_t)peer[e] : (uint64_t)owner[e];
+        keys[e] = (recv << rb) | send;
+        vals[e] = e;
+    }
+}
+
+__global__ void match_kernel(const uint64_t *ko, const int64_t *vo, const uint64_t *ki, const int64_t *vi,
+                             int64_t n, int64_t *match_out, int64_t *match_in, int *err) {
+    FOR_EACH(m, n) {
+        if (ko[m] != ki[m]) { set_err(err, GBX_ERR_TRUNCATE); continue; }
+        match_out[vo[m]] = vi[m];
+        match_in[vi[m]] = vo[m];
+    }
+}
+
+int gbx_graph_setup(gbx_graph_s *g, int64_t n_in, const int *in_ptr, const int *sources,
+                    int64_t n_out, const int *out_ptr, const int *dests, cudaStream_t st) {
+    const int P = g->P;
+    DevPool ws;
+    int *err;
+    GBX_TRY(ws.get(&err, 1));
+    GBX_CUDA_TRY(cudaMemsetAsync(err, 0x7f, sizeof(int), st));  // 0x7f7f7f7f > any code
+    GBX_TRY(g->mem.get(&g->in_ptr, P + 1));
+    GBX_TRY(g->mem.get(&g->out_ptr, P + 1));
+    GBX_TRY(g->mem.get(&g->sources, n_in));
+    GBX_TRY(g->mem.get(&g->dests, n_out));
+    GBX_CUDA_TRY(cudaMemcpyAsync(g->in_ptr, in_ptr, sizeof(int) * (P + 1), cudaMemcpyDeviceToDevice, st));
+    GBX_CUDA_TRY(cudaMemcpyAsync(g->out_ptr, out_ptr, sizeof(int) * (P + 1), cudaMemcpyDeviceToDevice, st));
+    if (n_in) GBX_CUDA_TRY(cudaMemcpyAsync(g->sources, sources, sizeof(int) * n_in, cudaMemcpyDeviceToDevice, st));
+    if (n_out) GBX_CUDA_TRY(cudaMemcpyAsync(g->dests, dests, sizeof(int) * n_out, cudaMemcpyDeviceToDevice, st));
+    csr_check_kernel<<<grid_of(P + 1), SETUP_T, 0, st>>>(g->in_ptr, P, n_in, err);
+    csr_check_kernel<<<grid_of(P + 1), SETUP_T, 0, st>>>(g->out_ptr, P, n_out, err);
+    GBX_CUDA_TRY(cudaGetLastError());
+    int rc = gbx_read_err(err, st);
+    if (rc == 0x7f7f7f7f) rc = GBX_SUCCESS;
+    if (rc) return rc;
+    if (n_in) rank_check_kernel<<<grid_of(n_in), SETUP_T, 0, st>>>(g->sources, n_in, P, err);
+    if (n_out) rank_check_kernel<<<grid_of(n_out), SETUP_T, 0, st>>>(g->dests, n_out, P, err);
+    GBX_CUDA_TRY(cudaGetLastError());
+    rc = gbx_read_err(err, st);
+    if (rc == 0x7f7f7f7f) rc = GBX_SUCCESS;
+    if (rc) return rc;
+    if (n_in != n_out) return GBX_ERR_TRUNCATE;
+    const int64_t E = n_in;
+    g->E = E;
+    GBX_TRY(g->mem.get(&g->in_owner, E));
+    GBX_TRY(g->mem.get(&g->out_owner, E));
+    GBX_TRY(g->mem.get(&g->match_out, E));
+    GBX_TRY(g->mem.get(&g->match_in, E));
+    if (E == 0) return GBX_SUCCESS;
+    owner_kernel<<<grid_of(E), SETUP_T, 0, st>>>(g->in_ptr, P, E, g->in_owner);
+    owner_kernel<<<grid_of(E), SETUP_T, 0, st>>>(g->out_ptr, P, E, g->out_owner);
+    const int rb = std::max(1, bitlen_u64((uint64_t)P - 1));
+    uint64_t *ko, *ki, *ka;
+    int64_t *vo, *vi, *va;
+    GBX_TRY(ws.get(&ko, E)); GBX_TRY(ws.get(&ki, E)); GBX_TRY(ws.get(&ka, E));
+    GBX_TRY(ws.get(&vo, E)); GBX_TRY(ws.get(&vi, E)); GBX_TRY(ws.get(&va, E));
+    edge_key_kernel<<<grid_of(E), SETUP_T, 0, st>>>(g->out_owner, g->dests, E, rb, 0, ko, vo);
+    edge_key_kernel<<<grid_of(E), SETUP_T, 0, st>>>(g->in_owner, g->sources, E, rb, 1, ki, vi);
+    GBX_CUDA_TRY(cudaGetLastError());
+    uint64_t *ko_s = ko, *ki_s = ki;
+    int64_t *vo_s = vo, *vi_s = vi;
+    GBX_TRY(gbx_sort_pairs(&ko_s, &vo_s, ka, va, E, 2 * rb, st, ws));
+    // second sort needs its own alternate buffers (ka/va may now hold the out result)
+    uint64_t *kb; int64_t *vb;
+    GBX_TRY(ws.get(&kb, E)); GBX_TRY(ws.get(&vb, E));
+    GBX_TRY(gbx_sort_pairs(&ki_s, &vi_s, kb, vb, E, 2 * rb, st, ws));
+    match_kernel<<<grid_of(E), SETUP_T, 0, st>>>(ko_s, vo_s, ki_s, vi_s, E, g->match_out, g->match_in, err);
+    GBX_CUDA_TRY(cudaGetLastError());
+    rc = gbx_read_err(err, st);
+    if (rc == 0x7f7f7f7f) rc = GBX_SUCCESS;
+    return rc;
+}
+
+// ----------------------------------------------------------------- forward setup
+struct FwdArgs {
+    const int64_t *send_base, *recv_base;
+    const int *sendcounts, *sdispls, *recvcounts, *rdispls;
+    const int64_t *send_slot_ptr, *recv_slot_ptr;
+    const int *send_idx;
+    const int64_t *global_sidx, *global_ridx;
+    const int *in_owner, *out_owner;
+    const int64_t *match_in, *match_out;
+    int64_t s, send_bytes, recv_bytes;
+    int P, ppn, nnodes;
+};
+
+__global__ void base_check_kernel(FwdArgs a, int *err, unsigned long long *align_or) {
+    FOR_EACH(r, (int64_t)a.P) {
+        if (a.send_base[r] < 0 || a.recv_base[r] < 0) set_err(err, GBX_ERR_INDEX);
+        atomicOr(align_or, (unsigned long long)(a.send_base[r] | a.recv_base[r]));
+    }
+}
+
+// Stage A, per in-edge i: counts, displacements, bounds (the oracle's rules); sort key
+// (receiver, rdispl) so that segments come out in receive order.
+__global__ void inedge_kernel(FwdArgs a, int64_t E, int64_t *cnt_out, uint64_t *key, int64_t *val, int *err) {
+    FOR_EACH(i, E) {
+        const int64_t e = a.match_in[i];
+        const int r = a.out_owner[e], d = a.in_owner[i];
+        const int64_t cnt = a.sendcounts[e];
+        const int64_t sd = a.sdispls[e], rd = a.rdispls[i];
+        key[i] = ((uint64_t)d << 31) | (uint64_t)(rd >= 0 ? rd : 0);
+        val[i] = i;
+        cnt_out[i] = 0;
+        if ((int64_t)a.recvcounts[i] != cnt || cnt < 0) { set_err(err, GBX_ERR_TRUNCATE); continue; }
+        bool ok = true;
+        if (sd < 0) ok = false;
+        else if (a.send_slot_ptr && sd + cnt > a.send_slot_ptr[r + 1] - a.send_slot_ptr[r]) ok = false;
+        if (ok && a.send_base[r] >= 0) {
+            if (!a.send_idx && a.send_base[r] + (sd + cnt) * a.s > a.send_bytes) ok = false;
+        } else {
+            ok = false;
+        }
+        if (rd < 0) ok = false;
+        else if (a.recv_slot_ptr && rd + cnt > a.recv_slot_ptr[d + 1] - a.recv_slot_ptr[d]) ok = false;
+        else if (a.recv_base[d] < 0 || a.recv_base[d] + (rd + cnt) * a.s > a.recv_bytes) ok = false;
+        if (!ok) { set_err(err, GBX_ERR_INDEX); continue; }
+        if (sd + cnt > 0x7fffffffll) { set_err(err, GBX_ERR_UNSUPPORTED); continue; }
+        cnt_out[i] = cnt;
+    }
+}
+
+__global__ void gather_counts_kernel(const int64_t *cnt_by_edge, const int64_t *order, int64_t n, int64_t *c,
+                                     int64_t *nz) {
+    FOR_EACH(m, n) {
+        int64_t x = cnt_by_edge[order[m]];
+        c[m] = x;
+        nz[m] = x > 0;
+    }
+}
+
+// Compacts non-empty messages into segments (receive order), fills their descriptors.
+__global__ void seg_kernel(FwdArgs a, const int64_t *order, const int64_t *c, const int64_t *v0, const int64_t *nzpos,
+                           int64_t n, Seg *segs, int64_t *segv0, int *seg_src, int *seg_dst, int64_t *seg_sd,
+                           int64_t *seg_rd, int64_t *seg_of_inedge) {
+    FOR_EACH(m, n) {
+        const int64_t i = order[m];
+        if (c[m] == 0) { seg_of_inedge[i] = -1; continue; }
+        const int64_t q = nzpos[m];
+        const int64_t e = a.match_in[i];
+        const int r = a.out_owner[e], d = a.in_owner[i];
+        const int64_t sd = a.sdispls[e], rd = a.rdispls[i];
+        Seg sg;
+        sg.v0 = v0[m];
+        sg.dst_off = a.recv_base[d] + rd * a.s;
+        if (a.send_idx) { sg.src_off = a.send_base[r]; sg.idx_off = v0[m]; }
+        else { sg.src_off = a.send_base[r] + sd * a.s; sg.idx_off = -1; }
+        segs[q] = sg;
+        segv0[q] = v0[m];
+        seg_src[q] = r;
+        seg_dst[q] = d;
+        seg_sd[q] = sd;
+        seg_rd[q] = rd;
+        seg_of_inedge[i] = q;
+    }
+}
+
+// Stage B, per element: source element index (send list), its bound, and the
+// receive-side global index check.
+__global__ void elem_kernel(FwdArgs a, const int64_t *segv0, int64_t nseg, const int *seg_src, const int *seg_dst,
+                            const int64_t *seg_sd, const int64_t *seg_rd, int64_t V, int32_t *srcel, int *err) {
+    FOR_EACH(v, V) {
+        const int64_t q = upper_index(segv0, nseg, v);
+        const int64_t k = v - segv0[q];
+        const int r = seg_src[q], d = seg_dst[q];
+        const int64_t slot = seg_sd[q] + k;
+        int64_t el = slot;
+        if (a.send_idx) {
+            el = a.send_idx[a.send_slot_ptr[r] + slot];
+            if (el < 0 || a.send_base[r] + (el + 1) * a.s > a.send_bytes) {
+                set_err(err, GBX_ERR_INDEX);
+                el = 0;
+            }
+        }
+        srcel[v] = (int32_t)el;
+        if (a.global_ridx &&
+            a.global_ridx[a.recv_slot_ptr[d] + seg_rd[q] + k] != a.global_sidx[a.send_slot_ptr[r] + slot])
+            set_err(err, GBX_ERR_GIDX);
+    }
+}
+
+__global__ void overlap_key_kernel(const Seg *segs, const int64_t *segv0, int64_t nseg, int64_t s, uint64_t *key,
+                                   int64_t *val) {
+    FOR_EACH(q, nseg) {
+        key[q] = (uint64_t)segs[q].dst_off;
+        val[q] = (segv0[q + 1] - segv0[q]) * s;   // byte length
+    }
+}
+
+__global__ void overlap_check_kernel(const uint64_t *key, const int64_t *len, int64_t n, int *err) {
+    FOR_EACH(m, n) if (m > 0 && (int64_t)key[m] < (int64_t)key[m - 1] + len[m - 1]) set_err(err, GBX_ERR_OVERLAP);
+}
+
+static int read_err_stage(int *err, cudaStream_t st) {
+    int rc = gbx_read_err(err, st);
+    return rc == 0x7f7f7f7f ? GBX_SUCCESS : rc;
+}
+
+// ---------------------------------------------------------------- locality maps
+__device__ __forceinline__ int node_sz(int a, int P, int ppn) { int n = P - a * ppn; return n < ppn ? n : ppn; }
+
+__global__ void seg_split_kernel(const int *seg_src, const int *seg_dst, const int64_t *segv0, int64_t nseg, int ppn,
+                                 int64_t *c_intra, int64_t *c_inter, int64_t *f_intra, int64_t *f_inter) {
+    FOR_EACH(q, nseg) {
+        const int64_t c = segv0[q + 1] - segv0[q];
+        const bool inter = seg_src[q] / ppn != seg_dst[q] / ppn;
+        c_intra[q] = inter ? 0 : c;
+        c_inter[q] = inter ? c : 0;
+        f_intra[q] = !inter;
+        f_inter[q] = inter;
+    }
+}
+
+// step 0 (intra, standard descriptors renumbered) and step 3 (inter, read the receive
+// aggregate through idx3) segments
+__global__ void seg03_kernel(const Seg *segs, const int64_t *f_intra, const int64_t *v_intra, const int64_t *p_intra,
+                             const int64_t *v_inter, const int64_t *p_inter, int64_t nseg, int64_t r_base,
+                             Seg *seg0, Seg *seg3) {
+    FOR_EACH(q, nseg) {
+        Seg sg = segs[q];
+        if (f_intra[q]) {
+            sg.v0 = v_intra[q];
+            seg0[p_intra[q]] = sg;
+        } else {
+            Seg t;
+            t.v0 = v_inter[q];
+            t.dst_off = sg.dst_off;
+            t.src_off = r_base;
+            t.idx_off = v_inter[q];
+            seg3[p_inter[q]] = t;
+        }
+    }
+}
+
+// inter-node elements enumerated in out-edge order (the representative order)
+__global__ void out_inter_count_kernel(FwdArgs a, int64_t E, const int64_t *seg_of_inedge, const int64_t *segv0,
+                                       int64_t *c) {
+    FOR_EACH(e, E) {
+        const int64_t q = seg_of_inedge[a.match_out[e]];
+        const int r = a.out_owner[e];
+        const int d = a.in_owner[a.match_out[e]];
+        c[e] = (q >= 0 && r / a.ppn != d / a.ppn) ? segv0[q + 1] - segv0[q] : 0;
+    }
+}
+
+// gidx of the w-th inter element (out order) and its standard element number
+__device__ __forceinline__ void inter_elem(const FwdArgs &a, const int64_t *w0, int64_t E, const int64_t *seg_of_inedge,
+                                           const int64_t *segv0, int64_t w, int64_t *v, int64_t *g, int64_t *pair) {
+    const int64_t e = upper_index(w0, E, w);
+    const int64_t k = w - w0[e];
+    const int64_t i = a.match_out[e];
+    const int64_t q = seg_of_inedge[i];
+    const int r = a.out_owner[e], d = a.in_owner[i];
+    *v = segv0[q] + k;
+    *g = a.global_sidx[a.send_slot_ptr[r] + a.sdispls[e] + k];
+    *pair = (int64_t)(r / a.ppn) * a.nnodes + (d / a.ppn);
+}
+
+__global__ void gidx_range_kernel(FwdArgs a, const int64_t *w0, int64_t E, const int64_t *seg_of_inedge,
+                                  const int64_t *segv0, int64_t W, unsigned long long *mn, unsigned long long *mx) {
+    FOR_EACH(w, W) {
+        int64_t v, g, pair;
+        inter_elem(a, w0, E, seg_of_inedge, segv0, w, &v, &g, &pair);
+        unsigned long long u = (unsigned long long)g ^ 0x8000000000000000ull;  // order-preserving
+        atomicMin(mn, u);
+        atomicMax(mx, u);
+    }
+}
+
+// mode 0: key = (pair << gbits) | (g - gmin); mode 1: key = g - gmin; val = standard element
+__global__ void inter_key_kernel(FwdArgs a, const int64_t *w0, int64_t E, const int64_t *seg_of_inedge,
+                                 const int64_t *segv0, int64_t W, int64_t gmin, int gbits, int mode, uint64_t *key,
+                                 int64_t *val) {
+    FOR_EACH(w, W) {
+        int64_t v, g, pair;
+        inter_elem(a, w0, E, seg_of_inedge, segv0, w, &v, &g, &pair);
+        uint64_t gk = (uint64_t)(g - gmin);
+        key[w] = mode == 0 ? (((uint64_t)pair << gbits) | gk) : gk;
+        val[w] = w;  // out-order id; converted to the standard element after sorting
+    }
+}
+
+__global__ void pair_key_kernel(FwdArgs a, const int64_t *w0, int64_t E, const int64_t *seg_of_inedge,
+                                const int64_t *segv0, const int64_t *val, int64_t W, uint64_t *key) {
+    FOR_EACH(m, W) {
+        int64_t v, g, pair;
+        inter_elem(a, w0, E, seg_of_inedge, segv0, val[m], &v, &g, &pair);
+        key[m] = (uint64_t)pair;
+    }
+}
+
+// per sorted inter element: (pair, g), new-value flag, and its standard element number
+__global__ void value_flag_kernel(FwdArgs a, const int64_t *w0, int64_t E, const int64_t *seg_of_inedge,
+                                  const int64_t *segv0, const int64_t *wsorted, int64_t W, int64_t *flag,
+                                  int64_t *velem) {
+    FOR_EACH(m, W) {
+        int64_t v, g, pair;
+        inter_elem(a, w0, E, seg_of_inedge, segv0, wsorted[m], &v, &g, &pair);
+        velem[m] = v;
+        if (m == 0) { flag[m] = 1; continue; }
+        int64_t v2, g2, pair2;
+        inter_elem(a, w0, E, seg_of_inedge, segv0, wsorted[m - 1], &v2, &g2, &pair2);
+        flag[m] = (pair != pair2 || g != g2);
+    }
+}
+
+// for each distinct value t (at its first sorted occurrence m): aggregate-order key
+__global__ void value_rep_kernel(FwdArgs a, const int64_t *flag, const int64_t *tscan, const int64_t *velem,
+                                 const int64_t *segv0, int64_t nseg, const int *seg_src, const int *seg_dst,
+                                 const int32_t *srcel, int64_t W, int rb, uint64_t *key2, int64_t *val2,
+                                 int64_t *rep_off, int32_t *rep_node, int32_t *rep_rank, int32_t *rep_el) {
+    FOR_EACH(m, W) {
+        if (!flag[m]) continue;
+        const int64_t t = tscan[m];
+        const int64_t v = velem[m];
+        const int64_t q = upper_index(segv0, nseg, v);
+        const int r = seg_src[q], d = seg_dst[q];
+        const int64_t pair = (int64_t)(r / a.ppn) * a.nnodes + d / a.ppn;
+        key2[t] = ((uint64_t)pair << rb) | (uint64_t)r;
+        val2[t] = t;
+        rep_off[t] = a.send_base[r] + (int64_t)srcel[v] * a.s;
+        rep_node[t] = d / a.ppn;
+        rep_rank[t] = r;
+        rep_el[t] = srcel[v];
+    }
+}
+
+// aggregate slot arrays (in aggregate order q) and run flags of step 1 / step 2 segments
+__global__ void agg_order_kernel(const uint64_t *key2s, const int64_t *tsorted, int64_t U, int rb,
+                                 const int64_t *rep_off_t, const int32_t *rep_node_t, const int32_t *rep_el_t,
+                                 int64_t *pos_of_t, int64_t *agg_rep_off, int32_t *agg_node, int32_t *idx1,
+                                 int64_t *f1, int64_t *f2) {
+    FOR_EACH(q, U) {
+        const int64_t t = tsorted[q];
+        pos_of_t[t] = q;
+        agg_rep_off[q] = rep_off_t[t];
+        agg_node[q] = rep_node_t[t];
+        idx1[q] = rep_el_t[t];
+        f1[q] = (q == 0) || key2s[q] != key2s[q - 1];
+        f2[q] = (q == 0) || (key2s[q] >> rb) != (key2s[q - 1] >> rb);
+    }
+}
+
+__global__ void seg12_kernel(FwdArgs a, const uint64_t *key2s, const int64_t *f1, const int64_t *p1,
+                             const int64_t *f2, const int64_t *p2, int64_t U, int rb, int64_t r_base,
+                             Seg *seg1, Seg *seg2, int64_t *m1) {
+    FOR_EACH(q, U) {
+        if (f1[q]) {
+            const int r = (int)(key2s[q] & ((1ull << rb) - 1));
+            const int64_t pair = (int64_t)(key2s[q] >> rb);
+            Seg sg;
+            sg.v0 = q;
+            sg.dst_off = q * a.s;
+            sg.src_off = a.send_base[r];
+            sg.idx_off = q;
+            seg1[p1[q]] = sg;
+            const int an = (int)(pair / a.nnodes), bn = (int)(pair % a.nnodes);
+            const int lead = an * a.ppn + bn % node_sz(an, a.P, a.ppn);
+            if (r != lead) atomicAdd((unsigned long long *)m1, 1ull);
+        }
+        if (f2[q]) {
+            Seg sg;
+            sg.v0 = q;
+            sg.dst_off = r_base + q * a.s;
+            sg.src_off = q * a.s;
+            sg.idx_off = -1;
+            seg2[p2[q]] = sg;
+        }
+    }
+}
+
+__global__ void idx3_kernel(const int64_t *velem, const int64_t *tscan, const int64_t *pos_of_t, int64_t W,
+                            const int64_t *segv0, int64_t nseg, const int64_t *v_inter, int32_t *idx3,
+                            int64_t *val_pos) {
+    FOR_EACH(m, W) {
+        const int64_t v = velem[m];
+        const int64_t q = upper_index(segv0, nseg, v);
+        const int64_t slot = pos_of_t[tscan[m]];
+        idx3[v_inter[q] + (v - segv0[q])] = (int32_t)slot;
+        val_pos[v] = slot;
+    }
+}
+
+// distinct (source node, receiving rank) among inter messages, receiver not the leader
+__global__ void m3_key_kernel(const int *seg_src, const int *seg_dst, const int64_t *f_inter, int64_t nseg, int ppn,
+                              int nb, uint64_t *key, int64_t *cnt) {
+    FOR_EACH(q, nseg) {
+        key[q] = f_inter[q] ? (((uint64_t)seg_dst[q] << nb) | (uint64_t)(seg_src[q] / ppn)) : ~0ull;
+        cnt[q] = f_inter[q];
+    }
+}
+
+__global__ void m3_count_kernel(const uint64_t *key, int64_t n, int nb, int P, int ppn, unsigned long long *m3) {
+    FOR_EACH(m, n) {
+        if (key[m] == ~0ull) continue;
+        if (m > 0 && key[m] == key[m - 1]) continue;
+        const int d = (int)(key[m] >> nb), an = (int)(key[m] & ((1ull << nb) - 1));
+        const int bn = d / ppn;
+        const int lead = bn * ppn + an % node_sz(bn, P, ppn);
+        if (d != lead) atomicAdd(m3, 1ull);
+    }
+}
+
+__global__ void fill_i64_neg_kernel(int64_t *p, int64_t n) { FOR_EACH(i, n) p[i] = -1; }
+
+// --------------------------------------------------------------- forward driver
+int gbx_setup_forward(gbx_request_s *req, const int64_t *send_base, const int *sendcounts, const int *sdispls,
+                      const int64_t *send_slot_ptr, const int *send_idx, const int64_t *recv_base,
+                      const int *recvcounts, const int *rdispls, const int64_t *recv_slot_ptr,
+                      const int64_t *global_sidx, const int64_t *global_ridx, int want_locality) {
+    gbx_graph_s *g = req->graph;
+    cudaStream_t st = req->stream;
+    const int64_t E = g->E;
+    const int64_t s = req->elem_size;
+    DevPool ws;
+    int *err;
+    unsigned long long *align_or;
+    GBX_TRY(ws.get(&err, 1));
+    GBX_TRY(ws.get(&align_or, 1));
+    GBX_CUDA_TRY(cudaMemsetAsync(err, 0x7f, sizeof(int), st));
+    GBX_CUDA_TRY(cudaMemsetAsync(align_or, 0, sizeof(unsigned long long), st));
+
+    FwdArgs a;
+    a.send_base = send_base; a.recv_base = recv_base;
+    a.sendcounts = sendcounts; a.sdispls = sdispls; a.recvcounts = recvcounts; a.rdispls = rdispls;
+    a.send_slot_ptr = send_slot_ptr; a.recv_slot_ptr = recv_slot_ptr; a.send_idx = send_idx;
+    a.global_sidx = global_sidx; a.global_ridx = global_ridx;
+    a.in_owner = g->in_owner; a.out_owner = g->out_owner; a.match_in = g->match_in; a.match_out = g->match_out;
+    a.s = s; a.send_bytes = req->src_bytes; a.recv_bytes = req->dst_bytes;
+    a.P = g->P; a.ppn = g->ppn; a.nnodes = g->nnodes;
+
+    base_check_kernel<<<grid_of(g->P), SETUP_T, 0, st>>>(a, err, align_or);
+    GBX_CUDA_TRY(cudaGetLastError());
+    int64_t *cnt_e = nullptr, *ordv = nullptr, *ordv_alt = nullptr;
+    uint64_t *key = nullptr, *key_alt = nullptr;
+    if (E > 0) {
+        GBX_TRY(ws.get(&cnt_e, E)); GBX_TRY(ws.get(&key, E)); GBX_TRY(ws.get(&key_alt, E));
+        GBX_TRY(ws.get(&ordv, E)); GBX_TRY(ws.get(&ordv_alt, E));
+        inedge_kernel<<<grid_of(E), SETUP_T, 0, st>>>(a, E, cnt_e, key, ordv, err);
+        GBX_CUDA_TRY(cudaGetLastError());
+    }
+    GBX_TRY(read_err_stage(err, st));
+
+    // receive order: (receiver, rdispl)
+    const int rb = std::max(1, bitlen_u64((uint64_t)g->P - 1));
+    int64_t *c = nullptr, *nz = nullptr, *v0 = nullptr, *nzpos = nullptr, *seg_of_inedge = nullptr;
+    int64_t nseg = 0, V = 0;
+    GBX_TRY(req->mem.get(&seg_of_inedge, E));
+    if (E > 0) {
+        GBX_TRY(gbx_sort_pairs(&key, &ordv, key_alt, ordv_alt, E, rb + 31, st, ws));
+        GBX_TRY(ws.get(&c, E)); GBX_TRY(ws.get(&nz, E));
+        GBX_TRY(ws.get(&v0, E + 1)); GBX_TRY(ws.get(&nzpos, E + 1));
+        gather_counts_kernel<<<grid_of(E), SETUP_T, 0, st>>>(cnt_e, ordv, E, c, nz);
+        GBX_CUDA_TRY(cudaGetLastError());
+        GBX_TRY(gbx_scan_i64(c, v0, E, st, ws));
+        GBX_TRY(gbx_scan_i64(nz, nzpos, E, st, ws));
+        GBX_TRY(gbx_read_i64(v0 + E, &V, st));
+        GBX_TRY(gbx_read_i64(nzpos + E, &nseg, st));
+    }
+    req->V = V;
+    req->nseg = nseg;
+    int *seg_src, *seg_dst;
+    int64_t *seg_sd, *seg_rd, *segv0;
+    GBX_TRY(req->mem.get(&req->segs_std, nseg));
+    GBX_TRY(req->mem.get(&segv0, nseg + 1));
+    GBX_TRY(req->mem.get(&seg_src, nseg));
+    GBX_TRY(req->mem.get(&seg_dst, nseg));
+    GBX_TRY(ws.get(&seg_sd, nseg));
+    GBX_TRY(ws.get(&seg_rd, nseg));
+    GBX_TRY(req->mem.get(&req->srcel, V));
+    req->seg_src_rank = seg_src;
+    req->seg_dst_rank = seg_dst;
+    req->segv0 = segv0;
+    GBX_TRY(req->mem.get(&req->send_base_copy, g->P));
+    GBX_CUDA_TRY(cudaMemcpyAsync(req->send_base_copy, send_base, sizeof(int64_t) * g->P, cudaMemcpyDeviceToDevice, st));
+    GBX_CUDA_TRY(cudaMemcpyAsync(segv0 + nseg, &V, sizeof(int64_t), cudaMemcpyHostToDevice, st));
+    if (E > 0) {
+        seg_kernel<<<grid_of(E), SETUP_T, 0, st>>>(a, ordv, c, v0, nzpos, E, req->segs_std, segv0, seg_src, seg_dst,
+                                                   seg_sd, seg_rd, seg_of_inedge);
+        GBX_CUDA_TRY(cudaGetLastError());
+    }
+    if (V > 0) {
+        elem_kernel<<<grid_of(V), SETUP_T, 0, st>>>(a, segv0, nseg, seg_src, seg_dst, seg_sd, seg_rd, V, req->srcel,
+                                                    err);
+        GBX_CUDA_TRY(cudaGetLastError());
+    }
+    GBX_TRY(read_err_stage(err, st));
+    // receive blocks must not overlap
+    if (nseg > 1) {
+        uint64_t *ok_, *ok_alt;
+        int64_t *ol, *ol_alt;
+        GBX_TRY(ws.get(&ok_, nseg)); GBX_TRY(ws.get(&ok_alt, nseg));
+        GBX_TRY(ws.get(&ol, nseg)); GBX_TRY(ws.get(&ol_alt, nseg));
+        overlap_key_kernel<<<grid_of(nseg), SETUP_T, 0, st>>>(req->segs_std, segv0, nseg, s, ok_, ol);
+        GBX_CUDA_TRY(cudaGetLastError());
+        GBX_TRY(gbx_sort_pairs(&ok_, &ol, ok_alt, ol_alt, nseg, bitlen_u64((uint64_t)req->dst_bytes), st, ws));
+        overlap_check_kernel<<<grid_of(nseg), SETUP_T, 0, st>>>(ok_, ol, nseg, err);
+        GBX_CUDA_TRY(cudaGetLastError());
+        GBX_TRY(read_err_stage(err, st));
+    }
+    unsigned long long h_align = 0;
+    GBX_CUDA_TRY(cudaMemcpyAsync(&h_align, align_or, sizeof(h_align), cudaMemcpyDeviceToHost, st));
+    GBX_CUDA_TRY(cudaStreamSynchronize(st));
+    h_align |= (unsigned long long)s | (unsigned long long)(uintptr_t)req->src | (unsigned long long)(uintptr_t)req->dst;
+
+    req->align = h_align;
+
+    // the move program
+    req->info.V = V;
+    req->info.E = E;
+    req->info.E_nonzero = nseg;
+    req->info.elem_size = s;
+    req->info.user_bytes = 2 * V * s;
+    // per-message counts: intra / inter split (reported for both forms)
+    int64_t *c_intra, *c_inter, *f_intra, *f_inter, *v_intra, *v_inter, *p_intra, *p_inter;
+    GBX_TRY(ws.get(&c_intra, nseg)); GBX_TRY(ws.get(&c_inter, nseg));
+    GBX_TRY(ws.get(&f_intra, nseg)); GBX_TRY(ws.get(&f_inter, nseg));
+    GBX_TRY(ws.get(&v_intra, nseg + 1)); GBX_TRY(ws.get(&v_inter, nseg + 1));
+    GBX_TRY(ws.get(&p_intra, nseg + 1)); GBX_TRY(ws.get(&p_inter, nseg + 1));
+    int64_t Vd = 0, Vx = 0, n0 = 0, n3 = 0;
+    if (nseg > 0) {
+        seg_split_kernel<<<grid_of(nseg), SETUP_T, 0, st>>>(seg_src, seg_dst, segv0, nseg, g->ppn, c_intra, c_inter,
+                                                            f_intra, f_inter);
+        GBX_CUDA_TRY(cudaGetLastError());
+        GBX_TRY(gbx_scan_i64(c_intra, v_intra, nseg, st, ws));
+        GBX_TRY(gbx_scan_i64(c_inter, v_inter, nseg, st, ws));
+        GBX_TRY(gbx_scan_i64(f_intra, p_intra, nseg, st, ws));
+        GBX_TRY(gbx_scan_i64(f_inter, p_inter, nseg, st, ws));
+        GBX_TRY(gbx_read_i64(v_intra + nseg, &Vd, st));
+        GBX_TRY(gbx_read_i64(v_inter + nseg, &Vx, st));
+        GBX_TRY(gbx_read_i64(p_intra + nseg, &n0, st));
+        GBX_TRY(gbx_read_i64(p_inter + nseg, &n3, st));
+    }
+    req->info.V_direct = Vd;
+    req->info.V_inter = Vx;
+    req->info.msgs_intra = n0;
+    req->info.msgs_inter = n3;
+    const int64_t idx_bytes = send_idx ? 4 : 0;
+
+    if (!want_locality) {
+        req->algorithm = GBX_ALG_STANDARD;
+        if (V > 0)
+            GBX_TRY(gbx_make_copy_op(req, 0, req->src, ROLE_SRC, req->dst, ROLE_DST, req->segs_std, nseg,
+                                     send_idx ? req->srcel : nullptr, V,
+                                     2 * V * s + V * idx_bytes + nseg * (int64_t)sizeof(Seg)));
+        req->info.U = 0;
+        return GBX_SUCCESS;
+    }
+
+    // ------------------------------------------------------------ locality form
+    req->algorithm = GBX_ALG_LOCALITY;
+    if (!global_sidx || !send_slot_ptr) return GBX_ERR_ARG;
+    Seg *seg0 = nullptr, *seg3 = nullptr;
+    GBX_TRY(req->mem.get(&seg0, n0));
+    GBX_TRY(req->mem.get(&seg3, n3));
+    GBX_TRY(req->mem.get(&req->val_pos, V));
+    if (V > 0) {
+        fill_i64_neg_kernel<<<grid_of(V), SETUP_T, 0, st>>>(req->val_pos, V);
+        GBX_CUDA_TRY(cudaGetLastError());
+    }
+    // inter elements in out-edge order
+    int64_t *c_out, *w0;
+    GBX_TRY(ws.get(&c_out, E)); GBX_TRY(ws.get(&w0, E + 1));
+    int64_t W = 0;
+    if (E > 0) {
+        out_inter_count_kernel<<<grid_of(E), SETUP_T, 0, st>>>(a, E, seg_of_inedge, segv0, c_out);
+        GBX_CUDA_TRY(cudaGetLastError());
+        GBX_TRY(gbx_scan_i64(c_out, w0, E, st, ws));
+        GBX_TRY(gbx_read_i64(w0 + E, &W, st));
+    }
+    if (W != Vx) return GBX_ERR_CUDA;  // internal consistency
+    int64_t U = 0, npairs = 0, m1 = 0, m3 = 0, n1 = 0;
+    int32_t *idx1 = nullptr, *idx3 = nullptr;
+    Seg *seg1 = nullptr, *seg2 = nullptr;
+    const int nbits = std::max(1, bitlen_u64((uint64_t)g->nnodes - 1));
+    const int pbits = std::max(1, bitlen_u64((uint64_t)g->nnodes * (uint64_t)g->nnodes - 1));
+    if (W > 0) {
+        unsigned long long *mn, *mx;
+        GBX_TRY(ws.get(&mn, 1)); GBX_TRY(ws.get(&mx, 1));
+        GBX_CUDA_TRY(cudaMemsetAsync(mn, 0xff, 8, st));
+        GBX_CUDA_TRY(cudaMemsetAsync(mx, 0, 8, st));
+        gidx_range_kernel<<<grid_of(W), SETUP_T, 0, st>>>(a, w0, E, seg_of_inedge, segv0, W, mn, mx);
+        GBX_CUDA_TRY(cudaGetLastError());
+        unsigned long long hmn = 0, hmx = 0;
+        GBX_CUDA_TRY(cudaMemcpyAsync(&hmn, mn, 8, cudaMemcpyDeviceToHost, st));
+        GBX_CUDA_TRY(cudaMemcpyAsync(&hmx, mx, 8, cudaMemcpyDeviceToHost, st));
+        GBX_CUDA_TRY(cudaStreamSynchronize(st));
+        const int64_t gmin = (int64_t)(hmn ^ 0x8000000000000000ull);
+        const int64_t gmax = (int64_t)(hmx ^ 0x8000000000000000ull);
+        const int gbits = std::max(1, bitlen_u64((uint64_t)(gmax - gmin)));
+        uint64_t *k1, *k1a;
+        int64_t *w1, *w1a;
+        GBX_TRY(ws.get(&k1, W)); GBX_TRY(ws.get(&k1a, W));
+        GBX_TRY(ws.get(&w1, W)); GBX_TRY(ws.get(&w1a, W));
+        if (pbits + gbits <= 64) {
+            inter_key_kernel<<<grid_of(W), SETUP_T, 0, st>>>(a, w0, E, seg_of_inedge, segv0, W, gmin, gbits, 0, k1, w1);
+            GBX_CUDA_TRY(cudaGetLastError());
+            GBX_TRY(gbx_sort_pairs(&k1, &w1, k1a, w1a, W, pbits + gbits, st, ws));
+        } else {
+            inter_key_kernel<<<grid_of(W), SETUP_T, 0, st>>>(a, w0, E, seg_of_inedge, segv0, W, gmin, gbits, 1, k1, w1);
+            GBX_CUDA_TRY(cudaGetLastError());
+            uint64_t *kk = k1, *kka = k1a;
+            int64_t *ww = w1, *wwa = w1a;
+            GBX_TRY(gbx_sort_pairs(&kk, &ww, kka, wwa, W, gbits, st, ws));
+            uint64_t *kother = (kk == k1) ? k1a : k1;
+            int64_t *wother = (ww == w1) ? w1a : w1;
+            pair_key_kernel<<<grid_of(W), SETUP_T, 0, st>>>(a, w0, E, seg_of_inedge, segv0, ww, W, kk);
+            GBX_CUDA_TRY(cudaGetLastError());
+            GBX_TRY(gbx_sort_pairs(&kk, &ww, kother, wother, W, pbits, st, ws));
+            k1 = kk;
+            w1 = ww;
+        }
+        int64_t *flag, *tscan, *velem;
+        GBX_TRY(ws.get(&flag, W)); GBX_TRY(ws.get(&tscan, W + 1)); GBX_TRY(ws.get(&velem, W));
+        value_flag_kernel<<<grid_of(W), SETUP_T, 0, st>>>(a, w0, E, seg_of_inedge, segv0, w1, W, flag, velem);
+        GBX_CUDA_TRY(cudaGetLastError());
+        GBX_TRY(gbx_scan_i64(flag, tscan, W, st, ws));
+        GBX_TRY(gbx_read_i64(tscan + W, &U, st));
+        if (pbits + rb > 64) return GBX_ERR_UNSUPPORTED;
+        uint64_t *key2, *key2a;
+        int64_t *val2, *val2a, *rep_off, *pos_of_t;
+        int32_t *rep_node, *rep_rank, *rep_el;
+        GBX_TRY(ws.get(&key2, U)); GBX_TRY(ws.get(&key2a, U));
+        GBX_TRY(ws.get(&val2, U)); GBX_TRY(ws.get(&val2a, U));
+        GBX_TRY(ws.get(&rep_off, U)); GBX_TRY(ws.get(&pos_of_t, U));
+        GBX_TRY(ws.get(&rep_node, U)); GBX_TRY(ws.get(&rep_rank, U)); GBX_TRY(ws.get(&rep_el, U));
+        value_rep_kernel<<<grid_of(W), SETUP_T, 0, st>>>(a, flag, tscan, velem, segv0, nseg, seg_src, seg_dst,
+                                                         req->srcel, W, rb, key2, val2, rep_off, rep_node, rep_rank,
+                                                         rep_el);
+        GBX_CUDA_TRY(cudaGetLastError());
+        GBX_TRY(gbx_sort_pairs(&key2, &val2, key2a, val2a, U, pbits + rb, st, ws));
+        int64_t *f1, *f2, *p1, *p2;
+        GBX_TRY(ws.get(&f1, U)); GBX_TRY(ws.get(&f2, U));
+        GBX_TRY(ws.get(&p1, U + 1)); GBX_TRY(ws.get(&p2, U + 1));
+        GBX_TRY(req->mem.get(&req->agg_rep_off, U));
+        GBX_TRY(req->mem.get(&req->agg_dst_node, U));
+        GBX_TRY(req->mem.get(&idx1, U));
+        agg_order_kernel<<<grid_of(U), SETUP_T, 0, st>>>(key2, val2, U, rb, rep_off, rep_node, rep_el, pos_of_t,
+                                                         req->agg_rep_off, req->agg_dst_node, idx1, f1, f2);
+        GBX_CUDA_TRY(cudaGetLastError());
+        GBX_TRY(gbx_scan_i64(f1, p1, U, st, ws));
+        GBX_TRY(gbx_scan_i64(f2, p2, U, st, ws));
+        GBX_TRY(gbx_read_i64(p1 + U, &n1, st));
+        GBX_TRY(gbx_read_i64(p2 + U, &npairs, st));
+        GBX_TRY(req->mem.get(&seg1, n1));
+        GBX_TRY(req->mem.get(&seg2, npairs));
+        int64_t *dm1;
+        GBX_TRY(ws.get(&dm1, 1));
+        GBX_CUDA_TRY(cudaMemsetAsync(dm1, 0, 8, st));
+        seg12_kernel<<<grid_of(U), SETUP_T, 0, st>>>(a, key2, f1, p1, f2, p2, U, rb, U * s, seg1, seg2, dm1);
+        GBX_CUDA_TRY(cudaGetLastError());
+        GBX_TRY(gbx_read_i64(dm1, &m1, st));
+        GBX_TRY(req->mem.get(&idx3, Vx));
+        idx3_kernel<<<grid_of(W), SETUP_T, 0, st>>>(velem, tscan, pos_of_t, W, segv0, nseg, v_inter, idx3, req->val_pos);
+        GBX_CUDA_TRY(cudaGetLastError());
+        // step 3 messages
+        uint64_t *k3, *k3a;
+        int64_t *c3, *c3a;
+        GBX_TRY(ws.get(&k3, nseg)); GBX_TRY(ws.get(&k3a, nseg));
+        GBX_TRY(ws.get(&c3, nseg)); GBX_TRY(ws.get(&c3a, nseg));
+        m3_key_kernel<<<grid_of(nseg), SETUP_T, 0, st>>>(seg_src, seg_dst, f_inter, nseg, g->ppn, nbits, k3, c3);
+        GBX_CUDA_TRY(cudaGetLastError());
+        GBX_TRY(gbx_sort_pairs(&k3, &c3, k3a, c3a, nseg, 64, st, ws));
+        unsigned long long *dm3;
+        GBX_TRY(ws.get(&dm3, 1));
+        GBX_CUDA_TRY(cudaMemsetAsync(dm3, 0, 8, st));
+        m3_count_kernel<<<grid_of(nseg), SETUP_T, 0, st>>>(k3, nseg, nbits, g->P, g->ppn, dm3);
+        GBX_CUDA_TRY(cudaGetLastError());
+        GBX_TRY(gbx_read_i64((const int64_t *)dm3, &m3, st));
+        GBX_TRY(req->mem.get(&req->segs_pair, npairs));
+        GBX_CUDA_TRY(cudaMemcpyAsync(req->segs_pair, seg2, sizeof(Seg) * npairs, cudaMemcpyDeviceToDevice, st));
+    }
+    if (nseg > 0) {
+        seg03_kernel<<<grid_of(nseg), SETUP_T, 0, st>>>(req->segs_std, f_intra, v_intra, p_intra, v_inter, p_inter,
+                                                        nseg, U * s, seg0, seg3);
+        GBX_CUDA_TRY(cudaGetLastError());
+    }
+    req->U = U;
+    req->npairs = npairs;
+    req->info.U = U;
+    req->info.node_pairs = npairs;
+    req->info.msgs_step1 = m1;
+    req->info.msgs_step3 = m3;
+    if (U > 0) GBX_TRY(req->mem.alloc((void **)&req->agg, (size_t)(2 * U * s)));
+    // level 0: direct copies and the gather into send aggregates; 1: node-pair blocks;
+    // 2: redistribution
+    if (n0 > 0)
+        GBX_TRY(gbx_make_copy_op(req, 0, req->src, ROLE_SRC, req->dst, ROLE_DST, seg0, n0,
+                                 send_idx ? req->srcel : nullptr, Vd,
+                                 2 * Vd * s + Vd * idx_bytes + n0 * (int64_t)sizeof(Seg)));
+    if (U > 0) {
+        GBX_TRY(gbx_make_copy_op(req, 0, req->src, ROLE_SRC, req->agg, ROLE_AGG, seg1, n1, idx1, U,
+                                 2 * U * s + 4 * U));
+        GBX_TRY(gbx_make_copy_op(req, 1, req->agg, ROLE_AGG, req->agg, ROLE_AGG, seg2, npairs, nullptr, U,
+                                 2 * U * s + npairs * (int64_t)sizeof(Seg)));
+        GBX_TRY(gbx_make_copy_op(req, 2, req->agg, ROLE_AGG, req->dst, ROLE_DST, seg3, n3, idx3, Vx,
+                                 2 * Vx * s + 4 * Vx + n3 * (int64_t)sizeof(Seg)));
+    }
+    return GBX_SUCCESS;
+}
+
+// -------------------------------------------------------------- backward maps
+// standard order: per source element (its byte offset), receive slots in (rank, position)
+__global__ void bwd_key_kernel(const int64_t *segv0, int64_t nseg, const int *seg_src, const int32_t *srcel,
+                               const int64_t *send_base, int64_t s, int64_t V, uint64_t *key, int64_t *val) {
+    FOR_EACH(v, V) {
+        const int64_t q = upper_index(segv0, nseg, v);
+        key[v] = (uint64_t)(send_base[seg_src[q]] + (int64_t)srcel[v] * s);
+        val[v] = v;
+    }
+}
+
+__global__ void row_flag_kernel(const uint64_t *key, int64_t n, int64_t *flag) {
+    FOR_EACH(m, n) flag[m] = (m == 0) || key[m] != key[m - 1];
+}
+
+// terms: grad_recv offset of element val[m]; rows: row_ptr / row_out at row starts
+__global__ void bwd_terms_kernel(const uint64_t *key, const int64_t *val, const int64_t *flag, const int64_t *rowid,
+                                 int64_t n, const Seg *segs, const int64_t *segv0, int64_t nseg, int64_t s,
+                                 int64_t out_base, int64_t out_scale, int64_t *terms, int64_t *row_ptr,
+                                 int64_t *row_out) {
+    FOR_EACH(m, n) {
+        const int64_t v = val[m];
+        const int64_t q = upper_index(segv0, nseg, v);
+        const int64_t off = segs[q].dst_off + (v - segv0[q]) * s;
+        terms[m] = off | (flag[m] ? (int64_t)GBX_TERM_GROUP : 0);
+        if (flag[m]) {
+            row_ptr[rowid[m]] = m;
+            row_out[rowid[m]] = out_base + (int64_t)key[m] * out_scale;
+        }
+    }
+}
+
+// node-blocked: reverse step 3 keys (aggregate slot; direct elements sort last)
+__global__ void rev3_key_kernel(const int64_t *val_pos, int64_t V, int64_t U, uint64_t *key, int64_t *val) {
+    FOR_EACH(v, V) {
+        key[v] = val_pos[v] >= 0 ? (uint64_t)val_pos[v] : (uint64_t)U;
+        val[v] = v;
+    }
+}
+
+// node-blocked: records of reverse steps 1 + 0.  Direct element v -> rec v;
+// aggregate slot q -> rec V + q.  key = (destination node << obits) | order
+__global__ void rev1_key_kernel(const int64_t *val_pos, const int64_t *segv0, int64_t nseg, const int *seg_dst,
+                                int64_t V, const int32_t *agg_node, int64_t U, int ppn, int obits, uint64_t sentinel,
+                                uint64_t *key, int64_t *val) {
+    FOR_EACH(x, V + U) {
+        if (x < V) {
+            const int64_t q = upper_index(segv0, nseg, x);
+            const bool direct = val_pos[x] < 0;
+            key[x] = direct ? (((uint64_t)(seg_dst[q] / ppn) << obits) | (uint64_t)x) : sentinel;
+        } else {
+            key[x] = ((uint64_t)agg_node[x - V] << obits) | (uint64_t)(x - V);
+        }
+        val[x] = x;
+    }
+}
+
+__global__ void rev1_srckey_kernel(const int64_t *rec, int64_t n, int64_t V, const int64_t *segv0, int64_t nseg,
+                                   const int *seg_src, const int32_t *srcel, const int64_t *send_base, int64_t s,
+                                   const int64_t *agg_rep_off, uint64_t *key) {
+    FOR_EACH(m, n) {
+        const int64_t x = rec[m];
+        if (x < V) {
+            const int64_t q = upper_index(segv0, nseg, x);
+            key[m] = (uint64_t)(send_base[seg_src[q]] + (int64_t)srcel[x] * s);
+        } else {
+            key[m] = (uint64_t)agg_rep_off[x - V];
+        }
+    }
+}
+
+__global__ void rev1_terms_kernel(const uint64_t *key, const int64_t *rec, const int64_t *rowflag, const int64_t *rowid,
+                                  int64_t n, int64_t V, const Seg *segs, const int64_t *segv0, int64_t nseg,
+                                  const int *seg_dst, const int32_t *agg_node, int ppn, int64_t s, int64_t *terms,
+                                  int64_t *row_ptr, int64_t *row_out) {
+    FOR_EACH(m, n) {
+        const int64_t x = rec[m];
+        int64_t term;
+        int node;
+        if (x < V) {
+            const int64_t q = upper_index(segv0, nseg, x);
+            term = segs[q].dst_off + (x - segv0[q]) * s;
+            node = seg_dst[q] / ppn;
+        } else {
+            term = (x - V) * s | (int64_t)GBX_TERM_BUFB;
+            node = agg_node[x - V];
+        }
+        bool gstart = rowflag[m] != 0;
+        if (!gstart) {
+            const int64_t y = rec[m - 1];
+            int pnode;
+            if (y < V) pnode = seg_dst[upper_index(segv0, nseg, y)] / ppn;
+            else pnode = agg_node[y - V];
+            gstart = pnode != node;
+        }
+        terms[m] = term | (gstart ? (int64_t)GBX_TERM_GROUP : 0);
+        if (rowflag[m]) {
+            row_ptr[rowid[m]] = m;
+            row_out[rowid[m]] = (int64_t)key[m];
+        }
+    }
+}
+
+static int finish_rows(int64_t *row_ptr, int64_t nrows, int64_t nterms, cudaStream_t st) {
+    GBX_CUDA_TRY(cudaMemcpyAsync(row_ptr + nrows, &nterms, sizeof(int64_t), cudaMemcpyHostToDevice, st));
+    GBX_CUDA_TRY(cudaStreamSynchronize(st));
+    return GBX_SUCCESS;
+}
+
+int gbx_setup_backward(gbx_request_s *bwd, int accumulate) {
+    gbx_request_s *f = bwd->forward;
+    cudaStream_t st = bwd->stream;
+    const int64_t V = f->V, s = f->elem_size, nseg = f->nseg;
+    DevPool ws;
+    const int64_t *segv0 = f->segv0;
+    const int64_t *send_base = f->send_base_copy;
+    const int64_t sbits = std::max(1, bitlen_u64((uint64_t)f->src_bytes));
+    bwd->info.V = V;
+    bwd->info.E = f->info.E;
+    bwd->info.E_nonzero = f->info.E_nonzero;
+    bwd->info.elem_size = s;
+    bwd->info.user_bytes = 2 * V * s;
+    if (V == 0) return GBX_SUCCESS;
+
+    if (f->algorithm == GBX_ALG_STANDARD) {
+        uint64_t *k, *ka;
+        int64_t *v, *va, *flag, *rowid, *row_ptr, *row_out, *terms;
+        GBX_TRY(ws.get(&k, V)); GBX_TRY(ws.get(&ka, V));
+        GBX_TRY(ws.get(&v, V)); GBX_TRY(ws.get(&va, V));
+        GBX_TRY(ws.get(&flag, V)); GBX_TRY(ws.get(&rowid, V + 1));
+        bwd_key_kernel<<<grid_of(V), SETUP_T, 0, st>>>(segv0, nseg, f->seg_src_rank, f->srcel, send_base, s, V, k, v);
+        GBX_CUDA_TRY(cudaGetLastError());
+        GBX_TRY(gbx_sort_pairs(&k, &v, ka, va, V, (int)sbits, st, ws));
+        row_flag_kernel<<<grid_of(V), SETUP_T, 0, st>>>(k, V, flag);
+        GBX_CUDA_TRY(cudaGetLastError());
+        GBX_TRY(gbx_scan_i64(flag, rowid, V, st, ws));
+        int64_t nrows = 0;
+        GBX_TRY(gbx_read_i64(rowid + V, &nrows, st));
+        GBX_TRY(bwd->mem.get(&row_ptr, nrows + 1));
+        GBX_TRY(bwd->mem.get(&row_out, nrows));
+        GBX_TRY(bwd->mem.get(&terms, V));
+        bwd_terms_kernel<<<grid_of(V), SETUP_T, 0, st>>>(k, v, flag, rowid, V, f->segs_std, segv0, nseg, s, 0, 1,
+                                                         terms, row_ptr, row_out);
+        GBX_CUDA_TRY(cudaGetLastError());
+        GBX_TRY(finish_rows(row_ptr, nrows, V, st));
+        bwd->info.rows = nrows;
+        bwd->info.terms = V;
+        GBX_TRY(gbx_make_fold_op(bwd, 0, bwd->dst, ROLE_DST, bwd->src, ROLE_SRC, nullptr, ROLE_NONE, row_ptr, row_out,
+                                 terms, nrows, V, accumulate));
+        return GBX_SUCCESS;
+    }
+
+    // node-blocked order: reverse of the three steps
+    const int64_t U = f->U, Vx = f->info.V_inter, Vd = f->info.V_direct;
+    const int ppn = f->graph->ppn;
+    bwd->U = U;
+    bwd->npairs = f->npairs;
+    bwd->info.U = U;
+    bwd->info.node_pairs = f->npairs;
+    if (U > 0) GBX_TRY(bwd->mem.alloc((void **)&bwd->agg, (size_t)(2 * U * s)));
+    int64_t total_terms = 0;
+    if (U > 0) {
+        // reverse step 3: rows = aggregate slots, terms = their receive slots in (rank, position)
+        uint64_t *k, *ka;
+        int64_t *v, *va, *flag, *rowid, *row_ptr, *row_out, *terms;
+        GBX_TRY(ws.get(&k, V)); GBX_TRY(ws.get(&ka, V));
+        GBX_TRY(ws.get(&v, V)); GBX_TRY(ws.get(&va, V));
+        GBX_TRY(ws.get(&flag, Vx)); GBX_TRY(ws.get(&rowid, Vx + 1));
+        rev3_key_kernel<<<grid_of(V), SETUP_T, 0, st>>>(f->val_pos, V, U, k, v);
+        GBX_CUDA_TRY(cudaGetLastError());
+        GBX_TRY(gbx_sort_pairs(&k, &v, ka, va, V, std::max(1, bitlen_u64((uint64_t)U)), st, ws));
+        row_flag_kernel<<<grid_of(Vx), SETUP_T, 0, st>>>(k, Vx, flag);
+        GBX_CUDA_TRY(cudaGetLastError());
+        GBX_TRY(gbx_scan_i64(flag, rowid, Vx, st, ws));
+        GBX_TRY(bwd->mem.get(&row_ptr, U + 1));
+        GBX_TRY(bwd->mem.get(&row_out, U));
+        GBX_TRY(bwd->mem.get(&terms, Vx));
+        // rows write the receive-aggregate half (gR) at U*s + slot*s
+        bwd_terms_kernel<<<grid_of(Vx), SETUP_T, 0, st>>>(k, v, flag, rowid, Vx, f->segs_std, segv0, nseg, s, U * s,
+                                                          s, terms, row_ptr, row_out);
+        GBX_CUDA_TRY(cudaGetLastError());
+        GBX_TRY(finish_rows(row_ptr, U, Vx, st));
+        GBX_TRY(gbx_make_fold_op(bwd, 0, bwd->agg, ROLE_AGG, bwd->src, ROLE_SRC, nullptr, ROLE_NONE, row_ptr, row_out,
+                                 terms, U, Vx, 0));
+        // reverse step 2: gR -> gS per node pair
+        Seg *rseg2;
+        GBX_TRY(bwd->mem.get(&rseg2, f->npairs));
+        {
+            std::vector<Seg> h(f->npairs);
+            GBX_CUDA_TRY(cudaMemcpyAsync(h.data(), f->segs_pair, sizeof(Seg) * f->npairs, cudaMemcpyDeviceToHost, st));
+            GBX_CUDA_TRY(cudaStreamSynchronize(st));
+            for (auto &sg : h) { std::swap(sg.dst_off, sg.src_off); }
+            GBX_CUDA_TRY(cudaMemcpyAsync(rseg2, h.data(), sizeof(Seg) * f->npairs, cudaMemcpyHostToDevice, st));
+            GBX_CUDA_TRY(cudaStreamSynchronize(st));
+        }
+        GBX_TRY(gbx_make_copy_op(bwd, 1, bwd->agg, ROLE_AGG, bwd->agg, ROLE_AGG, rseg2, f->npairs, nullptr, U,
+                                 2 * U * s + f->npairs * (int64_t)sizeof(Seg)));
+        total_terms += Vx;
+    }
+    // reverse steps 1 + 0: rows = source elements; groups by destination node
+    {
+        const int64_t N = V + U;
+        const int obits = std::max(1, bitlen_u64((uint64_t)std::max(V, U)));
+        const int nb = std::max(1, bitlen_u64((uint64_t)f->graph->nnodes));
+        uint64_t *k, *ka;
+        int64_t *x, *xa, *flag, *rowid, *row_ptr, *row_out, *terms;
+        GBX_TRY(ws.get(&k, N)); GBX_TRY(ws.get(&ka, N));
+        GBX_TRY(ws.get(&x, N)); GBX_TRY(ws.get(&xa, N));
+        const uint64_t sentinel = 1ull << (nb + obits);
+        rev1_key_kernel<<<grid_of(N), SETUP_T, 0, st>>>(f->val_pos, segv0, nseg, f->seg_dst_rank, V, f->agg_dst_node,
+                                                        U, ppn, obits, sentinel, k, x);
+        GBX_CUDA_TRY(cudaGetLastError());
+        if (nb + obits + 1 > 64) return GBX_ERR_UNSUPPORTED;
+        GBX_TRY(gbx_sort_pairs(&k, &x, ka, xa, N, nb + obits + 1, st, ws));
+        const int64_t M = Vd + U;   // direct elements and aggregate slots; inter elements sorted last
+        uint64_t *sk, *sk_alt;
+        int64_t *sx, *sx_alt;
+        GBX_TRY(ws.get(&sk, M)); GBX_TRY(ws.get(&sk_alt, M));
+        GBX_TRY(ws.get(&sx, M)); GBX_TRY(ws.get(&sx_alt, M));
+        if (M > 0) GBX_CUDA_TRY(cudaMemcpyAsync(sx, x, sizeof(int64_t) * M, cudaMemcpyDeviceToDevice, st));
+        rev1_srckey_kernel<<<grid_of(M), SETUP_T, 0, st>>>(sx, M, V, segv0, nseg, f->seg_src_rank, f->srcel, send_base,
+                                                           s, f->agg_rep_off, sk);
+        GBX_CUDA_TRY(cudaGetLastError());
+        GBX_TRY(gbx_sort_pairs(&sk, &sx, sk_alt, sx_alt, M, (int)sbits, st, ws));
+        GBX_TRY(ws.get(&flag, M)); GBX_TRY(ws.get(&rowid, M + 1));
+        row_flag_kernel<<<grid_of(M), SETUP_T, 0, st>>>(sk, M, flag);
+        GBX_CUDA_TRY(cudaGetLastError());
+        GBX_TRY(gbx_scan_i64(flag, rowid, M, st, ws));
+        int64_t nrows = 0;
+        GBX_TRY(gbx_read_i64(rowid + M, &nrows, st));
+        GBX_TRY(bwd->mem.get(&row_ptr, nrows + 1));
+        GBX_TRY(bwd->mem.get(&row_out, nrows));
+        GBX_TRY(bwd->mem.get(&terms, M));
+        rev1_terms_kernel<<<grid_of(M), SETUP_T, 0, st>>>(sk, sx, flag, rowid, M, V, f->segs_std, segv0, nseg,
+                                                          f->seg_dst_rank, f->agg_dst_node, ppn, s, terms, row_ptr,
+                                                          row_out);
+        GBX_CUDA_TRY(cudaGetLastError());
+        GBX_TRY(finish_rows(row_ptr, nrows, M, st));
+        bwd->info.rows = nrows;
+        total_terms += M;
+        GBX_TRY(gbx_make_fold_op(bwd, U > 0 ? 2 : 0, bwd->dst, ROLE_DST, bwd->src, ROLE_SRC, bwd->agg, ROLE_AGG,
+                                 row_ptr, row_out, terms, nrows, M, accumulate));
+    }
+    bwd->info.terms = total_terms;
+    return GBX_SUCCESS;
+}

@@ -384,3 +384,128 @@ def restrict_to_receivers(p: Pattern, keep) -> Pattern:
     q.sendcounts = p.sendcounts[ko]
     q.sdispls = p.sdispls[ko]
     return q
+
+
+# ----------------------------------------------------------- random patterns ---
+
+def random_pattern(seed: int, P=None, ppn=None, elem_size=None, indexed=None, dtype=None,
+                   max_deg=6, max_count=5, gaps=True) -> Pattern:
+    """Random valid exchange for fuzzing: repeated neighbours (multigraph), self edges,
+    zero-count edges, isolated ranks, in-lists in shuffled order (each sender's listings
+    keep their relative order, as the multigraph rule pairs them by occurrence), receive
+    blocks placed in random order with gaps, and byte gaps between rank regions so that
+    offsets are not vector aligned.  Global indices name source elements, so equal
+    indices always carry equal bytes."""
+    rng = np.random.default_rng(seed)
+    P = int(P if P is not None else rng.integers(1, 65))
+    ppn = int(ppn if ppn is not None else rng.choice([1, 2, 3, 4, max(P, 1)]))
+    if dtype is None:
+        dtype = "bytes"
+    if elem_size is None:
+        elem_size = int(rng.choice([1, 2, 3, 4, 5, 8, 12, 16, 24, 64, 128])) if dtype == "bytes" else \
+            (8 if dtype == "f64" else 4) * int(rng.choice([1, 2, 3, 4, 8]))
+    s = int(elem_size)
+    indexed = bool(rng.integers(0, 2)) if indexed is None else bool(indexed)
+    region = rng.integers(1, 21, size=P) if indexed else None
+    outs = []   # per rank: list of (dest, count, send elements)
+    for r in range(P):
+        deg = int(rng.integers(0, max_deg + 1)) if rng.random() > 0.1 else 0
+        lst = []
+        for _ in range(deg):
+            d = int(rng.integers(0, P))
+            c = int(rng.integers(0, max_count + 1))
+            els = rng.integers(0, region[r], size=c) if indexed else None
+            lst.append((d, c, els))
+        outs.append(lst)
+    # send slots: packed in out-list order
+    send_elem, send_rank_of_slot = [], []
+    sdispls, out_src, out_dst, out_cnt = [], [], [], []
+    for r in range(P):
+        pos = 0
+        for d, c, els in outs[r]:
+            out_src.append(r); out_dst.append(d); out_cnt.append(c); sdispls.append(pos)
+            send_elem.extend(els.tolist() if indexed else range(pos, pos + c))
+            send_rank_of_slot.extend([r] * c)
+            pos += c
+    nslots = np.bincount(np.array(out_src, dtype=np.int64), weights=np.array(out_cnt), minlength=P).astype(np.int64) \
+        if out_src else np.zeros(P, np.int64)
+    send_slot_ptr = _ptr_from_counts(nslots)
+    region_elems = region if indexed else np.maximum(nslots, 1)
+    # send regions with byte gaps
+    send_base = np.zeros(P, np.int64)
+    off = int(rng.integers(0, 7)) if gaps else 0
+    for r in range(P):
+        send_base[r] = off
+        off += int(region_elems[r]) * s + (int(rng.integers(0, 7)) if gaps else 0)
+    sendbuf_bytes = off
+    # element identity -> global index (equal index <=> same source element)
+    elem_base = _ptr_from_counts(np.asarray(region_elems, np.int64))
+    send_elem = np.asarray(send_elem, dtype=np.int64)
+    srank = np.asarray(send_rank_of_slot, dtype=np.int64)
+    gs = elem_base[srank] + send_elem if len(send_elem) else np.zeros(0, np.int64)
+    # in-lists: every d lists its senders; shuffle but keep each sender's listings in order
+    ins = [[] for _ in range(P)]
+    e = 0
+    for r in range(P):
+        for t, (d, c, els) in enumerate(outs[r]):
+            ins[d].append((r, c, e))
+            e += 1
+    in_dst, in_src, in_cnt, rdispls, rgidx_blocks = [], [], [], [], []
+    recv_slots = np.zeros(P, np.int64)
+    recv_g = []
+    for d in range(P):
+        lst = ins[d]
+        # random interleaving that keeps per-sender order
+        keys = rng.random(len(lst))
+        by_sender = {}
+        for i, (r, c, eid) in enumerate(lst):
+            by_sender.setdefault(r, []).append(i)
+        for r, idxs in by_sender.items():
+            ks = np.sort(keys[idxs])
+            for i, k in zip(idxs, ks):
+                keys[i] = k
+        order = np.argsort(keys, kind="stable")
+        lst = [lst[i] for i in order]
+        # receive blocks in a random order with gaps
+        place = rng.permutation(len(lst))
+        pos = 0
+        disp = [0] * len(lst)
+        for i in place:
+            pos += int(rng.integers(0, 3)) if gaps else 0
+            disp[i] = pos
+            pos += lst[i][1]
+        recv_slots[d] = pos + (int(rng.integers(0, 3)) if gaps else 0)
+        g = np.full(recv_slots[d], -1, np.int64)
+        for (r, c, eid), dp in zip(lst, disp):
+            in_dst.append(d); in_src.append(r); in_cnt.append(c); rdispls.append(dp)
+            so = send_slot_ptr[r] + sdispls[eid]
+            g[dp:dp + c] = gs[so:so + c]
+        recv_g.append(g)
+    recv_slot_ptr = _ptr_from_counts(recv_slots)
+    recv_base = np.zeros(P, np.int64)
+    off = int(rng.integers(0, 7)) if gaps else 0
+    for d in range(P):
+        recv_base[d] = off
+        off += int(recv_slots[d]) * s + (int(rng.integers(0, 7)) if gaps else 0)
+    recvbuf_bytes = off
+    out_ptr = _ptr_from_counts(np.bincount(np.array(out_src, np.int64), minlength=P) if out_src
+                               else np.zeros(P, np.int64)).astype(np.int32)
+    in_ptr = _ptr_from_counts(np.bincount(np.array(in_dst, np.int64), minlength=P) if in_dst
+                              else np.zeros(P, np.int64)).astype(np.int32)
+    return Pattern(
+        name=f"random{seed}_P{P}_ppn{ppn}_s{s}_{'idx' if indexed else 'packed'}", P=P, ppn=ppn,
+        in_ptr=in_ptr, sources=np.asarray(in_src, np.int32), out_ptr=out_ptr,
+        dests=np.asarray(out_dst, np.int32), sendcounts=np.asarray(out_cnt, np.int32),
+        sdispls=np.asarray(sdispls, np.int32), recvcounts=np.asarray(in_cnt, np.int32),
+        rdispls=np.asarray(rdispls, np.int32), elem_size=s, dtype=dtype,
+        send_base=send_base, recv_base=recv_base, sendbuf_bytes=int(sendbuf_bytes),
+        recvbuf_bytes=int(recvbuf_bytes), send_slot_ptr=send_slot_ptr,
+        send_idx=send_elem.astype(np.int32) if indexed else None,
+        recv_slot_ptr=recv_slot_ptr, global_sidx=gs.astype(np.int64),
+        global_ridx=np.concatenate(recv_g) if recv_g else np.zeros(0, np.int64),
+        meta=dict(kind="random", seed=seed))
+
+
+def random_bytes(n: int, seed: int) -> np.ndarray:
+    """Arbitrary payload bytes (includes NaN, -0.0 and denormal bit patterns)."""
+    return np.random.default_rng(seed).integers(0, 256, size=n, dtype=np.uint8)

@@ -1,0 +1,275 @@
+"""GPU parity: the CUDA path against the CPU oracle, byte for byte, through the C ABI."""
+import dataclasses
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a GPU", allow_module_level=True)
+
+import oracle  # noqa: E402
+import paper_2309_07337_gb300 as gbx  # noqa: E402
+import pins  # noqa: E402
+from gpu_util import (assert_bytes_equal, backward, dev_bytes, forward, grad_payload,  # noqa: E402
+                      payload)
+from paper_2309_07337_gb300 import patterns as pt  # noqa: E402
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+# ------------------------------------------------------------------- golden
+@pytest.mark.parametrize("name", ["ring3.json", "multigraph.json", "locality_dedup.json",
+                                  "backward_order.json", "backward_order2.json"])
+def test_golden_forward(name):
+    g = pins.load_golden(name)
+    algs = ["standard"] + (["locality"] if g.global_sidx is not None else [])
+    for alg in algs:
+        got, _ = forward(g, g.sendbuf, alg, recv_init=g.recv_init)
+        assert_bytes_equal(got, np.array(g.expected_recv, dtype=g.vt), f"{name} {alg}")
+
+
+@pytest.mark.parametrize("name", ["locality_dedup.json", "backward_order.json", "backward_order2.json"])
+def test_golden_backward(name):
+    g = pins.load_golden(name)
+    gr = np.array(g.grad_recv, dtype=np.float64)
+    for alg, key in (("standard", "standard"), ("locality", "node_blocked")):
+        _, ex = forward(g, g.sendbuf, alg, recv_init=g.recv_init)
+        got, _ = backward(ex, gr)
+        want = getattr(g, f"expected_grad_{key}", None) or g.expected_grad_send
+        assert_bytes_equal(got, np.array(want, dtype=np.float64), f"{name} {alg}")
+        if hasattr(g, "grad_send_init"):
+            got, _ = backward(ex, gr, np.array(g.grad_send_init), accumulate=True)
+            assert_bytes_equal(got, np.array(getattr(g, f"expected_grad_{key}_accumulate")), f"{name} {alg} acc")
+
+
+def test_golden_locality_stats():
+    g = pins.load_golden("locality_dedup.json")
+    _, ex = forward(g, g.sendbuf, "locality", recv_init=g.recv_init)
+    info = ex.info()
+    for k, v in g.expected_stats.items():
+        assert info[k] == v, (k, info[k], v)
+
+
+# ---------------------------------------------------------- random patterns
+@pytest.mark.parametrize("seed", range(60))
+def test_random_forward(seed):
+    p = pt.random_pattern(seed)
+    x = pt.random_bytes(p.sendbuf_bytes, seed + 1)
+    init = pt.random_bytes(p.recvbuf_bytes, seed + 2)
+    want = oracle.standard(p, x, init)
+    for alg in ("standard", "locality"):
+        got, ex = forward(p, x, alg, recv_init=init)
+        assert_bytes_equal(got, want, f"{p.name} {alg}")
+        info = ex.info()
+        assert info["V"] == p.volume
+
+
+@pytest.mark.parametrize("seed", range(30))
+def test_random_backward(seed):
+    dt = "f64" if seed % 2 else "f32"
+    p = pt.random_pattern(1000 + seed, dtype=dt)
+    x = payload(p, seed)
+    g = grad_payload(p, seed + 5)
+    old = payload(p, seed + 9)
+    for alg, form in (("standard", 0), ("locality", 1)):
+        _, ex = forward(p, x, alg)
+        got, _ = backward(ex, g)
+        assert_bytes_equal(got, oracle.backward(p, g, form=form), f"{p.name} {alg}")
+        got, _ = backward(ex, g, old, accumulate=True)
+        assert_bytes_equal(got, oracle.backward(p, g, old, form=form, accumulate=True), f"{p.name} {alg} acc")
+
+
+# ------------------------------------------------------------------ configs
+def _config_case(p, seed, algs=("standard", "locality"), backward_too=True):
+    x = payload(p, seed)
+    want = oracle.standard(p, x)
+    for alg in algs:
+        got, ex = forward(p, x, alg)
+        assert_bytes_equal(got, want, f"{p.name} {alg}")
+        if backward_too and p.dtype in ("f32", "f64"):
+            g = grad_payload(p, seed + 1)
+            got, _ = backward(ex, g)
+            assert_bytes_equal(got, oracle.backward(p, g, form=0 if alg == "standard" else 1),
+                               f"{p.name} {alg} backward")
+    return ex
+
+
+def test_config1_stencil2d():
+    ex = _config_case(pt.config1(), pt.SEED + 1)
+    assert ex.info()["E"] == 48
+
+
+def test_config2_spmv_halo_full():
+    _config_case(pt.config2(), pt.SEED + 2)
+
+
+def test_config4_small_copy_f32():
+    _config_case(pt.config4(n=4096, P=64), pt.SEED + 4)
+
+
+def test_config5_reduced_128cube():
+    _config_case(pt.config5(edge=8), pt.SEED + 5)
+
+
+def test_config5_message_size_sweep_small():
+    for comps in (1, 2, 4, 16):
+        _config_case(pt.config5(edge=4, comps=comps), pt.SEED + 5 + comps, backward_too=comps == 2)
+
+
+def test_config5_full_512cube():
+    """The full 512^3 27-point stencil (8.59 GB field, 1.6 GB halo) in the launch
+    configuration the benchmark times (persistent request, CUDA graph, tuned shape)."""
+    p = pt.config5()
+    x = pt.stencil_field(p, pt.SEED + 5)
+    want = oracle.standard(p, x)
+    for alg in ("standard", "locality"):
+        got, ex = forward(p, x, alg)
+        assert_bytes_equal(got, want, f"{p.name} {alg}")
+        del ex
+        torch.cuda.empty_cache()
+
+
+# ---------------------------------------------------------------- behaviour
+def test_shapes_and_graph_modes_identical():
+    p = pt.config5(edge=4, comps=3)
+    x = payload(p, 3)
+    want = oracle.standard(p, x)
+    for info in ("graph=0", "autotune=0", "vec=8;block=128", "vec=4;block=1024", "vec=8;block=512;graph=0"):
+        for alg in ("standard", "locality"):
+            got, _ = forward(p, x, alg, info=info)
+            assert_bytes_equal(got, want, f"{info} {alg}")
+
+
+def test_auto_picks_a_form_with_identical_output():
+    p = pt.config2(n=1 << 16, P=64)
+    x = payload(p, 4)
+    got, ex = forward(p, x, "auto")
+    assert_bytes_equal(got, oracle.standard(p, x), "auto")
+    assert ex.info()["algorithm"] in (0, 1)
+
+
+def test_repeated_starts_and_rebind():
+    p = pt.random_pattern(77, elem_size=8, indexed=True)
+    x1, x2 = pt.random_bytes(p.sendbuf_bytes, 1), pt.random_bytes(p.sendbuf_bytes, 2)
+    got, ex = forward(p, x1, "locality")
+    for _ in range(3):
+        ex.start()
+        ex.wait()
+    assert_bytes_equal(ex.recv.cpu().numpy(), oracle.standard(p, x1), "repeat")
+    s2 = dev_bytes(x2)
+    r2 = torch.zeros(p.recvbuf_bytes, dtype=torch.uint8, device="cuda")
+    ex.request.bind(s2, r2)
+    ex.start()
+    ex.wait()
+    assert_bytes_equal(r2.cpu().numpy(), oracle.standard(p, x2), "rebound")
+
+
+def test_start_on_active_request_and_test():
+    p = pt.config1()
+    _, ex = forward(p, payload(p, 1))
+    ex.start()
+    with pytest.raises(gbx.GbxError) as e:
+        ex.start()
+    assert e.value.code == gbx.ERR_ACTIVE
+    ex.wait()
+    assert ex.request.test()
+
+
+def test_wait_timeout_returns_error_then_completes():
+    """Failure detection without a GPU fault: the stream is held by a bounded sleep kernel
+    longer than the request's timeout; wait reports GBX_ERR_TIMEOUT, the request stays
+    active, and a later wait completes it."""
+    p = pt.config1()
+    x = payload(p, 2)
+    send = dev_bytes(x)
+    recv = torch.zeros(p.recvbuf_bytes, dtype=torch.uint8, device="cuda")
+    ex = gbx.Exchange(p, send, recv, info="timeout_ms=100")
+    cycles = int(torch.cuda.get_device_properties(0).clock_rate * 1000 * 1.0)  # about 1 s
+    torch.cuda._sleep(cycles)
+    ex.start()
+    with pytest.raises(gbx.GbxError) as e:
+        ex.wait()
+    assert e.value.code == gbx.ERR_TIMEOUT
+    torch.cuda.synchronize()
+    ex.wait()
+    assert_bytes_equal(recv.cpu().numpy(), oracle.standard(p, x), "after timeout")
+
+
+def test_startall_mixed_sizes_matches_individual():
+    pats = [pt.random_pattern(500 + i, elem_size=[4, 8, 24, 64, 3][i % 5]) for i in range(10)]
+    xs = [pt.random_bytes(p.sendbuf_bytes, i) for i, p in enumerate(pats)]
+    exs = []
+    for p, x in zip(pats, xs):
+        send = dev_bytes(x)
+        recv = torch.zeros(p.recvbuf_bytes, dtype=torch.uint8, device="cuda")
+        ex = gbx.Exchange(p, send, recv, algorithm="locality" if len(exs) % 2 else "standard")
+        ex.send, ex.recv = send, recv
+        exs.append(ex)
+    reqs = [e.request for e in exs]
+    for _ in range(2):
+        for e in exs:
+            e.recv.zero_()
+        gbx.startall(reqs)
+        gbx.waitall(reqs)
+        for p, x, e in zip(pats, xs, exs):
+            assert_bytes_equal(e.recv.cpu().numpy(), oracle.standard(p, x), f"batched {p.name}")
+
+
+def test_host_buffers_end_to_end():
+    p = pt.config1()
+    x = payload(p, 5)
+    send = dev_bytes(x)
+    recv = torch.zeros(p.recvbuf_bytes, dtype=torch.uint8, device="cuda")
+    ex = gbx.Exchange(p, send, recv)
+    hs = torch.from_numpy(x.view(np.uint8).copy()).pin_memory()
+    hr = torch.zeros(p.recvbuf_bytes, dtype=torch.uint8).pin_memory()
+    ex.request.start_host(hs, hr)
+    assert_bytes_equal(hr.numpy(), oracle.standard(p, x), "host buffers")
+
+
+# ------------------------------------------------------------------- errors
+def _error_cases():
+    base = pins.load_golden("ring3.json")
+
+    def mod(**kw):
+        g = pins.load_golden("ring3.json")
+        for k, (i, v) in kw.items():
+            a = getattr(g, k).copy()
+            a[i] = v
+            setattr(g, k, a)
+        return g
+    yield "rank", mod(dests=(0, 5))
+    yield "unmatched", mod(dests=(0, 2))
+    yield "count", mod(recvcounts=(0, 3))
+    yield "rdispl_past_end", mod(rdispls=(3, 9))
+    yield "negative_sdispl", mod(sdispls=(1, -1))
+    yield "overlap", mod(rdispls=(1, 1))
+    yield "not_csr", mod(in_ptr=(1, 4))
+    p = pt.spmv_halo(600, 4, 2, 6, seed=1, dtype="f64", band=80)
+    q = dataclasses.replace(p)
+    q.send_idx = p.send_idx.copy()
+    q.send_idx[3] = 10 ** 6
+    yield "send_idx", q
+    q = dataclasses.replace(p)
+    q.global_ridx = p.global_ridx.copy()
+    q.global_ridx[5] += 1
+    yield "gidx", q
+    del base
+
+
+@pytest.mark.parametrize("case", list(_error_cases()), ids=lambda c: c[0])
+def test_error_codes_match_oracle(case):
+    _, g = case
+    want = oracle.validate(g)
+    assert want != 0
+    sb = np.zeros(max(int(g.sendbuf_bytes), 1), np.uint8)[: g.sendbuf_bytes]
+    with pytest.raises(gbx.GbxError) as e:
+        forward(g, sb, "standard")
+    assert e.value.code == want
