@@ -58,6 +58,8 @@ extern "C" {
 #define GBX_ERR_CUDA         9   /* a CUDA call failed                                   */
 #define GBX_ERR_NOMEM       10   /* device allocation failed                             */
 #define GBX_ERR_UNSUPPORTED 11   /* valid request the library does not implement         */
+#define GBX_ERR_INTERNAL    12   /* a move program built at init failed the library's own
+                                    device-side validation (a library bug); nothing ran    */
 #define GBX_ERR_OVERLAP     13   /* two receive blocks write the same bytes              */
 
 /* payload types: only the backward (which adds) needs to know them */

@@ -36,6 +36,7 @@ extern "C" const char *gbx_error_string(int code) {
         case GBX_ERR_NOMEM: return "out of device memory";
         case GBX_ERR_UNSUPPORTED: return "unsupported request";
         case GBX_ERR_OVERLAP: return "receive blocks overlap";
+        case GBX_ERR_INTERNAL: return "internal error: a generated move program failed validation";
         default: return "unknown error";
     }
 }
@@ -142,7 +143,8 @@ static int vec_of_align(uint64_t align) {
 }
 
 int gbx_make_copy_op(gbx_request_s *req, int level, const char *src, int src_role, char *dst, int dst_role,
-                     const Seg *segs, int64_t nseg, const int32_t *idx, int64_t nelem, int64_t algo_bytes) {
+                     const Seg *segs, int64_t nseg, const int32_t *idx, int64_t idx_len, int64_t nelem,
+                     int64_t algo_bytes) {
     if (nelem <= 0) return GBX_SUCCESS;
     HostOp op;
     memset(&op, 0, sizeof(op));
@@ -155,6 +157,7 @@ int gbx_make_copy_op(gbx_request_s *req, int level, const char *src, int src_rol
     op.block = 256;
     op.persistent = 1;
     op.algo_bytes = algo_bytes;
+    op.idx_len = idx_len;
     CopyDesc &d = op.cd;
     d.src = src; d.dst = dst; d.segs = segs; d.idx = idx; d.nseg = nseg; d.nelem = nelem;
     d.elem_size = req->elem_size; d.src_role = src_role; d.dst_role = dst_role;
@@ -188,6 +191,7 @@ int gbx_make_fold_op(gbx_request_s *req, int level, char *out, int out_role, con
     op.persistent = 1;
     const int64_t s = req->elem_size;
     op.algo_bytes = nterms * s + nrows * s * (accumulate ? 2 : 1) + nterms * 8 + nrows * 16;
+    op.idx_len = nterms;
     FoldDesc &d = op.fd;
     d.out = out; d.bufA = bufA; d.bufB = bufB; d.row_ptr = row_ptr; d.row_out = row_out; d.terms = terms;
     d.nrows = nrows; d.elem_size = s; d.dtype = req->dtype; d.accumulate = accumulate;
@@ -463,6 +467,7 @@ static void fill_info(gbx_request_s *req) {
 }
 
 static int finalize(gbx_request_s *req) {
+    GBX_TRY(gbx_validate_program(req, req->agg ? 2 * req->U * req->elem_size : 0));
     for (HostOp &op : req->ops) GBX_TRY(tune_op(req, op));
     std::vector<HostOp *> ptrs;
     std::vector<int> dts;

@@ -157,6 +157,7 @@ struct HostOp {
     int persistent;  // tuned grid: 1 = resident blocks only, 0 = one block per tile
     float tuned_ms;  // measured time of the tuned shape (0 if not tuned)
     int64_t algo_bytes;
+    int64_t idx_len; // copy: entries of the index array; fold: number of terms
     CopyDesc cd;     // host copies of the descriptor
     FoldDesc fd;
     void *d_desc;           // device descriptor
@@ -234,7 +235,8 @@ int gbx_graph_setup(gbx_graph_s *g, int64_t n_in, const int *in_ptr, const int *
                     int64_t n_out, const int *out_ptr, const int *dests, cudaStream_t st);
 int gbx_make_copy_op(gbx_request_s *req, int level, const char *src, int src_role, char *dst,
                      int dst_role, const Seg *segs, int64_t nseg, const int32_t *idx,
-                     int64_t nelem, int64_t algo_bytes);
+                     int64_t idx_len, int64_t nelem, int64_t algo_bytes);
+int gbx_validate_program(gbx_request_s *req, int64_t agg_bytes);
 int gbx_make_fold_op(gbx_request_s *req, int level, char *out, int out_role, const char *bufA,
                      int a_role, const char *bufB, int b_role, const int64_t *row_ptr,
                      const int64_t *row_out, const int64_t *terms, int64_t nrows,

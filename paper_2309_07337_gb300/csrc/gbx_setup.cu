@@ -439,13 +439,14 @@ __global__ void seg12_kernel(FwdArgs a, const uint64_t *key2s, const int64_t *f1
     }
 }
 
-__global__ void idx3_kernel(const int64_t *velem, const int64_t *tscan, const int64_t *pos_of_t, int64_t W,
-                            const int64_t *segv0, int64_t nseg, const int64_t *v_inter, int32_t *idx3,
+// value id of sorted position m = (inclusive count of first occurrences up to m) - 1
+__global__ void idx3_kernel(const int64_t *velem, const int64_t *flag, const int64_t *tscan, const int64_t *pos_of_t,
+                            int64_t W, const int64_t *segv0, int64_t nseg, const int64_t *v_inter, int32_t *idx3,
                             int64_t *val_pos) {
     FOR_EACH(m, W) {
         const int64_t v = velem[m];
         const int64_t q = upper_index(segv0, nseg, v);
-        const int64_t slot = pos_of_t[tscan[m]];
+        const int64_t slot = pos_of_t[tscan[m] + flag[m] - 1];
         idx3[v_inter[q] + (v - segv0[q])] = (int32_t)slot;
         val_pos[v] = slot;
     }
@@ -611,7 +612,7 @@ int gbx_setup_forward(gbx_request_s *req, const int64_t *send_base, const int *s
         req->algorithm = GBX_ALG_STANDARD;
         if (V > 0)
             GBX_TRY(gbx_make_copy_op(req, 0, req->src, ROLE_SRC, req->dst, ROLE_DST, req->segs_std, nseg,
-                                     send_idx ? req->srcel : nullptr, V,
+                                     send_idx ? req->srcel : nullptr, V, V,
                                      2 * V * s + V * idx_bytes + nseg * (int64_t)sizeof(Seg)));
         req->info.U = 0;
         return GBX_SUCCESS;
@@ -721,7 +722,8 @@ int gbx_setup_forward(gbx_request_s *req, const int64_t *send_base, const int *s
         GBX_CUDA_TRY(cudaGetLastError());
         GBX_TRY(gbx_read_i64(dm1, &m1, st));
         GBX_TRY(req->mem.get(&idx3, Vx));
-        idx3_kernel<<<grid_of(W), SETUP_T, 0, st>>>(velem, tscan, pos_of_t, W, segv0, nseg, v_inter, idx3, req->val_pos);
+        idx3_kernel<<<grid_of(W), SETUP_T, 0, st>>>(velem, flag, tscan, pos_of_t, W, segv0, nseg, v_inter, idx3,
+                                                    req->val_pos);
         GBX_CUDA_TRY(cudaGetLastError());
         // step 3 messages
         uint64_t *k3, *k3a;
@@ -756,14 +758,14 @@ int gbx_setup_forward(gbx_request_s *req, const int64_t *send_base, const int *s
     // 2: redistribution
     if (n0 > 0)
         GBX_TRY(gbx_make_copy_op(req, 0, req->src, ROLE_SRC, req->dst, ROLE_DST, seg0, n0,
-                                 send_idx ? req->srcel : nullptr, Vd,
+                                 send_idx ? req->srcel : nullptr, V, Vd,
                                  2 * Vd * s + Vd * idx_bytes + n0 * (int64_t)sizeof(Seg)));
     if (U > 0) {
-        GBX_TRY(gbx_make_copy_op(req, 0, req->src, ROLE_SRC, req->agg, ROLE_AGG, seg1, n1, idx1, U,
+        GBX_TRY(gbx_make_copy_op(req, 0, req->src, ROLE_SRC, req->agg, ROLE_AGG, seg1, n1, idx1, U, U,
                                  2 * U * s + 4 * U));
-        GBX_TRY(gbx_make_copy_op(req, 1, req->agg, ROLE_AGG, req->agg, ROLE_AGG, seg2, npairs, nullptr, U,
+        GBX_TRY(gbx_make_copy_op(req, 1, req->agg, ROLE_AGG, req->agg, ROLE_AGG, seg2, npairs, nullptr, 0, U,
                                  2 * U * s + npairs * (int64_t)sizeof(Seg)));
-        GBX_TRY(gbx_make_copy_op(req, 2, req->agg, ROLE_AGG, req->dst, ROLE_DST, seg3, n3, idx3, Vx,
+        GBX_TRY(gbx_make_copy_op(req, 2, req->agg, ROLE_AGG, req->dst, ROLE_DST, seg3, n3, idx3, Vx, Vx,
                                  2 * Vx * s + 4 * Vx + n3 * (int64_t)sizeof(Seg)));
     }
     return GBX_SUCCESS;
@@ -964,7 +966,7 @@ int gbx_setup_backward(gbx_request_s *bwd, int accumulate) {
             GBX_CUDA_TRY(cudaMemcpyAsync(rseg2, h.data(), sizeof(Seg) * f->npairs, cudaMemcpyHostToDevice, st));
             GBX_CUDA_TRY(cudaStreamSynchronize(st));
         }
-        GBX_TRY(gbx_make_copy_op(bwd, 1, bwd->agg, ROLE_AGG, bwd->agg, ROLE_AGG, rseg2, f->npairs, nullptr, U,
+        GBX_TRY(gbx_make_copy_op(bwd, 1, bwd->agg, ROLE_AGG, bwd->agg, ROLE_AGG, rseg2, f->npairs, nullptr, 0, U,
                                  2 * U * s + f->npairs * (int64_t)sizeof(Seg)));
         total_terms += Vx;
     }
@@ -1014,4 +1016,85 @@ int gbx_setup_backward(gbx_request_s *bwd, int accumulate) {
     }
     bwd->info.terms = total_terms;
     return GBX_SUCCESS;
+}
+
+// ------------------------------------------------------- program validation
+// Every move program is checked on the device before its first launch: segments strictly
+// increasing and non-empty, every destination / source range and every gathered element
+// inside its buffer, every fold term and output inside its buffer.  A violation is an
+// internal error (GBX_ERR_INTERNAL), reported instead of ever running an out-of-range
+// access.
+__global__ void check_copy_segs_kernel(const Seg *segs, int64_t nseg, int64_t nelem, int64_t s, int64_t src_bytes,
+                                       int64_t dst_bytes, int64_t nidx, int *err) {
+    FOR_EACH(q, nseg) {
+        const Seg sg = segs[q];
+        const int64_t next = q + 1 < nseg ? segs[q + 1].v0 : nelem;
+        const int64_t cnt = next - sg.v0;
+        bool ok = cnt > 0 && (q > 0 || sg.v0 == 0) && sg.dst_off >= 0 && sg.dst_off + cnt * s <= dst_bytes;
+        if (sg.idx_off < 0) ok = ok && sg.src_off >= 0 && sg.src_off + cnt * s <= src_bytes;
+        else ok = ok && sg.idx_off + cnt <= nidx && sg.src_off >= 0;
+        if (!ok) set_err(err, GBX_ERR_INTERNAL);
+    }
+}
+
+__global__ void check_copy_idx_kernel(const Seg *segs, int64_t nseg, int64_t nelem, const int32_t *idx, int64_t s,
+                                      int64_t src_bytes, int *err) {
+    FOR_EACH(v, nelem) {
+        int64_t lo = 0, hi = nseg - 1;
+        while (lo < hi) {
+            int64_t mid = (lo + hi + 1) >> 1;
+            if (segs[mid].v0 <= v) lo = mid; else hi = mid - 1;
+        }
+        const Seg sg = segs[lo];
+        if (sg.idx_off < 0) continue;
+        const int64_t el = idx[sg.idx_off + (v - sg.v0)];
+        if (el < 0 || sg.src_off + (el + 1) * s > src_bytes) set_err(err, GBX_ERR_INTERNAL);
+    }
+}
+
+__global__ void check_fold_kernel(const int64_t *row_ptr, const int64_t *row_out, const int64_t *terms, int64_t nrows,
+                                  int64_t nterms, int64_t s, int64_t out_bytes, int64_t a_bytes, int64_t b_bytes,
+                                  int *err) {
+    FOR_EACH(r, nrows) {
+        const int64_t b = row_ptr[r], e = row_ptr[r + 1];
+        bool ok = b < e && (r > 0 || b == 0) && (r + 1 < nrows || e == nterms) && e <= nterms &&
+                  row_out[r] >= 0 && row_out[r] + s <= out_bytes;
+        for (int64_t m = b; ok && m < e; m++) {
+            const uint64_t w = (uint64_t)terms[m];
+            const int64_t off = (int64_t)(w & GBX_TERM_MASK);
+            const int64_t lim = (w & GBX_TERM_BUFB) ? b_bytes : a_bytes;
+            ok = off + s <= lim && (m > b || (w & GBX_TERM_GROUP));
+        }
+        if (!ok) set_err(err, GBX_ERR_INTERNAL);
+    }
+}
+
+int gbx_validate_program(gbx_request_s *req, int64_t agg_bytes) {
+    cudaStream_t st = req->stream;
+    DevPool ws;
+    int *err;
+    GBX_TRY(ws.get(&err, 1));
+    GBX_CUDA_TRY(cudaMemsetAsync(err, 0x7f, sizeof(int), st));
+    auto bytes_of = [&](int role) -> int64_t {
+        return role == ROLE_SRC ? req->src_bytes : role == ROLE_DST ? req->dst_bytes : role == ROLE_AGG ? agg_bytes : 0;
+    };
+    for (HostOp &op : req->ops) {
+        if (op.kind == 0) {
+            const CopyDesc &d = op.cd;
+            const int64_t nidx = d.idx ? op.idx_len : 0;
+            check_copy_segs_kernel<<<grid_of(d.nseg), SETUP_T, 0, st>>>(d.segs, d.nseg, d.nelem, d.elem_size,
+                                                                        bytes_of(d.src_role), bytes_of(d.dst_role),
+                                                                        nidx, err);
+            if (d.idx)
+                check_copy_idx_kernel<<<grid_of(d.nelem), SETUP_T, 0, st>>>(d.segs, d.nseg, d.nelem, d.idx,
+                                                                            d.elem_size, bytes_of(d.src_role), err);
+        } else {
+            const FoldDesc &d = op.fd;
+            check_fold_kernel<<<grid_of(d.nrows), SETUP_T, 0, st>>>(d.row_ptr, d.row_out, d.terms, d.nrows,
+                                                                    op.idx_len, d.elem_size, bytes_of(d.out_role),
+                                                                    bytes_of(d.a_role), bytes_of(d.b_role), err);
+        }
+        GBX_CUDA_TRY(cudaGetLastError());
+    }
+    return read_err_stage(err, st);
 }
