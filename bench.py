@@ -1,0 +1,473 @@
+#!/usr/bin/env python
+"""Benchmark of the persistent neighbourhood all-to-all-v on one GB300.
+
+Workload (default): the 3D 27-point stencil halo exchange of a 512^3 grid split over
+P = 4096 emulated ranks (16^3 blocks of 32^3 points, 64 ranks per node), 8 fp64
+components per point (64-byte elements, U(-1,1) from a seed); V = 25,002,360 elements
+per exchange from an 8.59 GB field.  Inputs are larger than L2, so no flush is needed.
+
+One step = one start + wait of each of the three persistent requests of that pattern:
+  * the standard exchange        (pack by send list + block copy + unpack, one kernel),
+  * the locality-aware exchange  (direct + gather, node-pair block copy, redistribute),
+  * the backward exchange        (reverse of the standard one, fixed-order sums).
+value = (user-visible bytes of the three exchanges) / step time, where a forward moves
+2*V*s user bytes and the backward reads V*s and writes rows*s.
+
+Also reported (extras, on by default): per-form GB/s and roofline fractions, the fused
+forward+backward vs plain (one launch and one host wait per exchange) factor, the
+batched uneven-patterns (config 3: 64 SpMV halos, mixed fp32/fp64) vs plain factor, and
+the SpMV halo (config 2) standard vs locality rates.
+
+--impl reference times the CPU oracle (the only reference this build has) on a bounded
+sample of the same workload: the exchanges into the first ranks' receive buffers.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2309_07337_gb300 import patterns as pt  # noqa: E402
+
+METRIC = "neighbor_alltoallv effective GB/s (standard + locality-aware forward + backward per step)"
+UNIT = "GB/s"
+
+
+def parse_args():
+    a = argparse.ArgumentParser()
+    a.add_argument("--gpus", type=int, default=1)
+    a.add_argument("--steps", type=int, default=20)
+    a.add_argument("--warmup", type=int, default=5)
+    a.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    a.add_argument("--e2e-steps", type=int, default=3)
+    a.add_argument("--cpu-sample-ranks", type=int, default=256)
+    a.add_argument("--no-extras", action="store_true")
+    a.add_argument("--no-e2e", action="store_true")
+    a.add_argument("--no-cpu", action="store_true")
+    a.add_argument("--edge", type=int, default=32, help="block edge (32 = the 512^3 workload)")
+    return a.parse_args()
+
+
+# ------------------------------------------------------------------- helpers
+def workload(edge=32):
+    p = pt.config5(edge=edge)
+    return p
+
+
+def workload_config(p, edge):
+    return {"workload": f"stencil3d_27pt_{16 * edge}^3_P4096_ppn64_8xf64",
+            "grid": [16 * edge] * 3, "ranks": 4096, "ranks_per_node": 64, "elem_bytes": p.elem_size,
+            "V": p.volume, "E": p.n_edges, "l2": "inputs larger than L2 (8.59 GB field), no flush"
+            if edge == 32 else "reduced size", "seed": pt.SEED + 5}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            m = json.load(f)
+        return float(m["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("gbx_move.cu", "gbx_internal.cuh"):
+        with open(os.path.join(ROOT, "paper_2309_07337_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(kernel_key):
+    """DRAM bytes per launch from the committed ncu summary, if the kernel is unchanged."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "dram_traffic.json")) as f:
+            d = json.load(f)
+        e = d[kernel_key]
+        if e.get("source_hash") != kernel_source_hash():
+            return None
+        return float(e["bytes_per_launch"])
+    except Exception:
+        return None
+
+
+class Clocks:
+    """nvidia-smi samples during the timed region (read-only queries)."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={index}", f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        self.f.flush()
+        self.f.seek(0)
+        sm, mx, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.f.read().splitlines():
+            c = [x.strip() for x in line.split(",")]
+            if len(c) < 9:
+                continue
+            try:
+                sm.append(float(c[1]))
+                mx.append(float(c[2]))
+                power.append(float(c[3]))
+            except ValueError:
+                continue
+            for n, v in zip(names, c[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        os.unlink(self.f.name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
+                "power_w_max": max(power) if power else None, "reasons": sorted(reasons)}
+
+
+# ----------------------------------------------------------------- CPU oracle
+def oracle_sample(p, x_bytes, grad_bytes, nrecv):
+    """The oracle's three exchanges restricted to receivers 0..nrecv-1 (same buffers).
+    Returns (seconds, user bytes)."""
+    import oracle
+    q = pt.restrict_to_receivers(p, np.arange(nrecv))
+    t0 = time.perf_counter()
+    oracle.standard(q, x_bytes)
+    _, st = oracle.locality(q, x_bytes)
+    g = oracle.backward(q, grad_bytes, form=0)
+    dt = time.perf_counter() - t0
+    V = q.volume
+    rows = distinct_sources(q)
+    del g, st
+    user = 2 * 2 * V * q.elem_size + V * q.elem_size + rows * q.elem_size
+    return dt, user, V
+
+
+def distinct_sources(q):
+    """Number of distinct source elements the pattern reads (rows of its backward)."""
+    owner = np.repeat(np.arange(q.P), np.diff(q.out_ptr))
+    cnt = q.sendcounts.astype(np.int64)
+    slot = np.repeat(q.send_slot_ptr[owner] + q.sdispls, cnt) + \
+        (np.arange(int(cnt.sum())) - np.repeat(np.cumsum(cnt) - cnt, cnt))
+    el = q.send_idx[slot] if q.send_idx is not None else slot - np.repeat(q.send_slot_ptr[owner], cnt)
+    off = np.repeat(q.send_base[owner], cnt) + el.astype(np.int64) * q.elem_size
+    return int(len(np.unique(off)))
+
+
+# ---------------------------------------------------------------- reference arm
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    p = workload(args.edge)
+    x = pt.stencil_field(p, pt.SEED + 5)
+    g = np.random.default_rng(pt.SEED + 6).standard_normal(p.recvbuf_bytes // 8)
+    n = args.cpu_sample_ranks
+    for _ in range(args.warmup):
+        oracle_sample(p, x, g, n)
+    ts, ub = [], 0
+    for _ in range(args.steps):
+        dt, ub, Vs = oracle_sample(p, x, g, n)
+        ts.append(dt)
+    t = sum(ts) / len(ts)
+    val = ub / t / 1e9
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": workload_config(p, args.edge),
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"the three exchanges into receivers 0..{n - 1} of 4096 "
+                                       f"({Vs} of {p.volume} elements), full buffers"},
+            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+# ---------------------------------------------------------------------- ours
+def run_ours(args):
+    import torch
+    import paper_2309_07337_gb300 as gbx
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    p = workload(args.edge)
+    s = p.elem_size
+    x = pt.stencil_field(p, pt.SEED + 5)                          # host fp64
+    field = torch.from_numpy(x).cuda()
+    halo_std = torch.zeros(p.recvbuf_bytes // 8, dtype=torch.float64, device="cuda")
+    halo_loc = torch.zeros_like(halo_std)
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(pt.SEED + 6)
+    grad_halo = torch.randn(p.recvbuf_bytes // 8, dtype=torch.float64, device="cuda", generator=gen)
+    grad_field = torch.zeros_like(field)
+    dp = gbx.DevicePattern(p)
+    t_init = time.perf_counter()
+    ex_std = gbx.Exchange(p, field, halo_std, "standard", dp=dp)
+    ex_loc = gbx.Exchange(p, field, halo_loc, "locality", dp=dp, graph=ex_std.graph)
+    bwd = gbx.backward_init(ex_std.request, grad_halo, grad_field)
+    torch.cuda.synchronize()
+    t_init = time.perf_counter() - t_init
+    reqs = [ex_std.request, ex_loc.request, bwd]
+    infos = [r.info() for r in reqs]
+
+    def step(ev=None):
+        for i, r in enumerate(reqs):
+            if ev is not None:
+                ev[i].record()
+            r.start()
+        if ev is not None:
+            ev[3].record()
+        for r in reqs:
+            r.wait()
+
+    for _ in range(args.warmup):
+        step()
+    # the two forms must agree byte for byte
+    assert torch.equal(halo_std.view(torch.uint8), halo_loc.view(torch.uint8)), "standard != locality"
+
+    K = args.steps
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(K)]
+    clocks = Clocks(local)
+    barrier()
+    torch.cuda.nvtx.range_push("timed")
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record()
+    for k in range(K):
+        step(evs[k])
+    t1.record()
+    torch.cuda.nvtx.range_pop()
+    barrier()
+    clk = clocks.stop()
+    total_ms = t0.elapsed_time(t1)
+    per = [sum(evs[k][i].elapsed_time(evs[k][i + 1]) for k in range(K)) / K for i in range(3)]
+    ms_local = total_ms / K
+    if dist is not None:
+        t = torch.tensor([ms_local], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    else:
+        ms = ms_local
+
+    V = p.volume
+    rows = infos[2]["rows"]
+    user = [2 * V * s, 2 * V * s, V * s + rows * s]
+    step_user = sum(user)
+    value = step_user * world / (ms * 1e-3) / 1e9
+    peak, peak_kind = measured_peaks()
+    forms = {}
+    for name, info, u, t in zip(("standard", "locality", "backward"), infos, user, per):
+        forms[name] = {"ms": t, "user_GBps": u / (t * 1e-3) / 1e9,
+                       "algo_bytes": info["algo_bytes"], "algo_GBps": info["algo_bytes"] / (t * 1e-3) / 1e9,
+                       "frac_of_measured_hbm": info["algo_bytes"] / (t * 1e-3) / 1e9 / peak,
+                       "launches": info["launches"], "vec": info["vec_bytes"], "block": info["block"]}
+    forms["locality"].update({"U": infos[1]["U"], "node_pairs": infos[1]["node_pairs"],
+                              "V_direct": infos[1]["V_direct"], "V_inter": infos[1]["V_inter"]})
+    forms["backward"].update({"rows": rows, "terms": infos[2]["terms"]})
+    # dominant kernel: the standard exchange's single move kernel
+    std_ms = per[0]
+    achieved = infos[0]["algo_bytes"] / (std_ms * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": profiled_traffic("gbx_copy_kernel_std_stencil512"),
+                "kernel": "gbx_copy_kernel (standard exchange, one launch per start)",
+                "peak_source": f"{peak_kind} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"}
+    launches = sum(i["launches"] for i in infos) * K
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": dict(workload_config(p, args.edge), parallelism="replicas" if world > 1 else "single"),
+            "roofline": roofline, "gpu_launches": launches, "clocks": clk, "forms": forms,
+            "init_s": t_init}
+
+    # ---------------------------------------------------------------- e2e
+    if not args.no_e2e:
+        hx = torch.empty(p.sendbuf_bytes, dtype=torch.uint8).pin_memory()
+        hx.copy_(torch.from_numpy(x.view(np.uint8)))
+        hh1 = torch.empty(p.recvbuf_bytes, dtype=torch.uint8).pin_memory()
+        hh2 = torch.empty(p.recvbuf_bytes, dtype=torch.uint8).pin_memory()
+        hg = torch.empty(p.recvbuf_bytes, dtype=torch.uint8).pin_memory()
+        hg.copy_(grad_halo.view(torch.uint8).cpu())
+        hgf = torch.empty(p.sendbuf_bytes, dtype=torch.uint8).pin_memory()
+        barrier()
+        e0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            ex_std.request.start_host(hx, hh1)
+            ex_loc.request.start_host(hx, hh2)
+            bwd.start_host(hg, hgf)
+        barrier()
+        e_ms = (time.perf_counter() - e0) / args.e2e_steps * 1e3
+        line["e2e"] = {"value": step_user * world / (e_ms * 1e-3) / 1e9, "unit": UNIT,
+                       "h2d_bytes_per_step": 2 * p.sendbuf_bytes + p.recvbuf_bytes,
+                       "d2h_bytes_per_step": 2 * p.recvbuf_bytes + p.sendbuf_bytes,
+                       "ms_per_step": e_ms, "steps": args.e2e_steps,
+                       "api": "gbx_start_host (host buffers in, exchange, host buffers out) per request"}
+        assert torch.equal(hh1, hh2)
+        del hx, hh1, hh2, hg, hgf
+
+    # ---------------------------------------------------------- cpu baseline
+    if rank == 0 and not args.no_cpu:
+        g_host = grad_halo.cpu().numpy()
+        dt, ub, Vs = oracle_sample(p, x, g_host, args.cpu_sample_ranks)
+        line["cpu_baseline"] = {"value": ub / dt / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                "seconds": dt,
+                                "sample": f"the three exchanges into receivers 0..{args.cpu_sample_ranks - 1} "
+                                          f"of 4096 ({Vs} of {V} elements), full buffers, single thread"}
+
+    # --------------------------------------------------------------- extras
+    if not args.no_extras and rank == 0:
+        line["extras"] = extras(gbx, torch, p, field, halo_std, grad_halo, grad_field, dp, ex_std, bwd)
+    if rank == 0:
+        print(json.dumps(line))
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def _time_loop(torch, fn, reps):
+    fn()
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    for _ in range(reps):
+        fn()
+    torch.cuda.synchronize()
+    return (time.perf_counter() - t) / reps * 1e3
+
+
+def extras(gbx, torch, p, field, halo, grad_halo, grad_field, dp, ex_std, bwd):
+    out = {}
+    # fused forward + backward (one graph, fused level launches) vs plain
+    plain_f = gbx.Exchange(p, field, halo, "standard", info="graph=0", dp=dp, graph=ex_std.graph)
+    plain_b = gbx.backward_init(plain_f.request, grad_halo, grad_field, info="graph=0")
+
+    def plain():
+        plain_f.request.start()
+        plain_f.request.wait()
+        plain_b.start()
+        plain_b.wait()
+
+    def fused():
+        gbx.startall([ex_std.request, bwd])
+        gbx.waitall([ex_std.request, bwd])
+    tp = _time_loop(torch, plain, 10)
+    tf = _time_loop(torch, fused, 10)
+    out["fwd_bwd_cfg5"] = {"plain_ms": tp, "fused_ms": tf, "speedup": tp / tf,
+                           "plain": "eager launches, start+wait per exchange",
+                           "fused": "startall of forward+backward: one CUDA graph, fused launches"}
+    del plain_f, plain_b
+    # batched uneven patterns (config 3) vs plain
+    t = time.perf_counter()
+    pats = pt.config3_torch(64, device="cuda")
+    gen_s = time.perf_counter() - t
+    bufs, g_reqs, p_reqs = [], [], []
+    for j, q in enumerate(pats):
+        n = q.sendbuf_bytes // (8 if q.dtype == "f64" else 4)
+        sb = torch.randn(n, device="cuda", dtype=torch.float64 if q.dtype == "f64" else torch.float32)
+        rb = torch.zeros(q.recvbuf_bytes // sb.element_size(), device="cuda", dtype=sb.dtype)
+        rb2 = torch.zeros_like(rb)
+        dq = gbx.DevicePattern(q)
+        e1 = gbx.Exchange(q, sb, rb, "standard", dp=dq)
+        e2 = gbx.Exchange(q, sb, rb2, "standard", info="graph=0", dp=dq, graph=e1.graph)
+        bufs.append((sb, rb, rb2, e1, e2))
+        g_reqs.append(e1.request)
+        p_reqs.append(e2.request)
+    Vtot = sum(q.volume for q in pats)
+    Btot = sum(q.user_bytes() for q in pats)
+
+    def plain3():
+        for r in p_reqs:
+            r.start()
+            r.wait()
+
+    def batched3():
+        gbx.startall(g_reqs)
+        gbx.waitall(g_reqs)
+    tp = _time_loop(torch, plain3, 5)
+    tb = _time_loop(torch, batched3, 5)
+    same = all(torch.equal(b[1], b[2]) for b in bufs)
+    out["batched_cfg3"] = {"patterns": len(pats), "V_total": Vtot, "plain_ms": tp, "batched_ms": tb,
+                           "speedup": tp / tb, "batched_user_GBps": Btot / (tb * 1e-3) / 1e9,
+                           "identical_results": same, "generation_s": gen_s,
+                           "dtypes": {d: sum(1 for q in pats if q.dtype == d) for d in ("f32", "f64")},
+                           "plain": "eager launches, start+wait per pattern",
+                           "batched": "startall of 64 requests: one CUDA graph, one fused launch per phase"}
+    del bufs, g_reqs, p_reqs
+    torch.cuda.empty_cache()
+    # SpMV halo (config 2), standard vs locality, L2 flushed between repetitions
+    q = pt.config2()
+    xs = torch.randn(q.meta["n"], device="cuda", dtype=torch.float64)
+    r1 = torch.zeros(q.recvbuf_bytes // 8, device="cuda", dtype=torch.float64)
+    r2 = torch.zeros_like(r1)
+    dq = gbx.DevicePattern(q)
+    a = gbx.Exchange(q, xs, r1, "standard", dp=dq)
+    b = gbx.Exchange(q, xs, r2, "locality", dp=dq, graph=a.graph)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    res = {}
+    for name, ex in (("standard", a), ("locality", b)):
+        ts = []
+        for _ in range(10):
+            flush.fill_(1)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            ex.request.start()
+            e1.record()
+            ex.request.wait()
+            ts.append(e0.elapsed_time(e1))
+        ms = statistics.median(ts)
+        res[name] = {"ms": ms, "user_GBps": q.user_bytes() / (ms * 1e-3) / 1e9,
+                     "algo_bytes": ex.info()["algo_bytes"]}
+    res["identical"] = bool(torch.equal(r1, r2))
+    res["V"] = q.volume
+    res["E"] = q.n_edges
+    res["U"] = b.info()["U"]
+    res["node_pairs"] = b.info()["node_pairs"]
+    res["l2"] = "flushed (256 MB write) before every repetition"
+    out["spmv_cfg2"] = res
+    return out
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -203,7 +203,8 @@ int gbx_neighbor_alltoallv_init(const void *sendbuf, int64_t sendbuf_bytes,
  * accumulate=0 stores the sum, accumulate=1 adds it to the existing value; elements no
  * slot reads are never written.  Adds are IEEE round-to-nearest in the payload type
  * (dtype of the forward must be GBX_F32 or GBX_F64, elem_size a multiple of it); the
- * order is fixed, so results are bitwise reproducible.  The forward request must
+ * order is fixed, so results are bitwise reproducible.  Buffers and base offsets must be
+ * aligned to the payload type (GBX_ERR_UNSUPPORTED otherwise).  The forward request must
  * outlive the backward one.  info: graph=, autotune=, timeout_ms= as above. */
 int gbx_backward_init(gbx_request_t forward, const void *grad_recv, void *grad_send,
                       int accumulate, const char *info, void *stream,

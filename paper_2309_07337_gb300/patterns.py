@@ -405,6 +405,7 @@ def random_pattern(seed: int, P=None, ppn=None, elem_size=None, indexed=None, dt
         elem_size = int(rng.choice([1, 2, 3, 4, 5, 8, 12, 16, 24, 64, 128])) if dtype == "bytes" else \
             (8 if dtype == "f64" else 4) * int(rng.choice([1, 2, 3, 4, 8]))
     s = int(elem_size)
+    unit = 1 if dtype == "bytes" else (8 if dtype == "f64" else 4)   # gaps keep float data aligned
     indexed = bool(rng.integers(0, 2)) if indexed is None else bool(indexed)
     region = rng.integers(1, 21, size=P) if indexed else None
     outs = []   # per rank: list of (dest, count, send elements)
@@ -433,10 +434,10 @@ def random_pattern(seed: int, P=None, ppn=None, elem_size=None, indexed=None, dt
     region_elems = region if indexed else np.maximum(nslots, 1)
     # send regions with byte gaps
     send_base = np.zeros(P, np.int64)
-    off = int(rng.integers(0, 7)) if gaps else 0
+    off = int(rng.integers(0, 7)) * unit if gaps else 0
     for r in range(P):
         send_base[r] = off
-        off += int(region_elems[r]) * s + (int(rng.integers(0, 7)) if gaps else 0)
+        off += int(region_elems[r]) * s + (int(rng.integers(0, 7)) * unit if gaps else 0)
     sendbuf_bytes = off
     # element identity -> global index (equal index <=> same source element)
     elem_base = _ptr_from_counts(np.asarray(region_elems, np.int64))
@@ -483,10 +484,10 @@ def random_pattern(seed: int, P=None, ppn=None, elem_size=None, indexed=None, dt
         recv_g.append(g)
     recv_slot_ptr = _ptr_from_counts(recv_slots)
     recv_base = np.zeros(P, np.int64)
-    off = int(rng.integers(0, 7)) if gaps else 0
+    off = int(rng.integers(0, 7)) * unit if gaps else 0
     for d in range(P):
         recv_base[d] = off
-        off += int(recv_slots[d]) * s + (int(rng.integers(0, 7)) if gaps else 0)
+        off += int(recv_slots[d]) * s + (int(rng.integers(0, 7)) * unit if gaps else 0)
     recvbuf_bytes = off
     out_ptr = _ptr_from_counts(np.bincount(np.array(out_src, np.int64), minlength=P) if out_src
                                else np.zeros(P, np.int64)).astype(np.int32)
@@ -509,3 +510,75 @@ def random_pattern(seed: int, P=None, ppn=None, elem_size=None, indexed=None, dt
 def random_bytes(n: int, seed: int) -> np.ndarray:
     """Arbitrary payload bytes (includes NaN, -0.0 and denormal bit patterns)."""
     return np.random.default_rng(seed).integers(0, 256, size=n, dtype=np.uint8)
+
+
+# ------------------------------------------------- device-side SpMV generator ---
+
+def spmv_halo_torch(n: int, P: int, ppn: int, nnz: int, seed: int, dtype: str = "f64",
+                    band: int = 4096, band_frac: float = 0.8, device="cuda", name=None) -> Pattern:
+    """The spmv_halo recipe drawn with torch (on the GPU when device='cuda'), for the
+    large uneven batch whose numpy generation would take minutes.  Same distributions and
+    layout; a different random stream than the numpy version for the same seed."""
+    import torch
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed))
+    nb = int(round(band_frac * nnz))
+    rows = torch.arange(n, device=device, dtype=torch.int64)
+    lo = torch.clamp(rows - band, min=0)
+    width = torch.clamp(rows + band, max=n - 1) - lo + 1
+    assert int(width.min()) >= nb and n >= nnz
+
+    def draw_band(r):
+        u = torch.rand(r.shape, generator=g, device=device, dtype=torch.float64)
+        return lo[r] + torch.minimum((u * width[r]).to(torch.int64), width[r] - 1)
+
+    cols = torch.empty((n, nnz), dtype=torch.int64, device=device)
+    rr = rows[:, None].expand(n, nb)
+    cols[:, :nb] = draw_band(rr)
+    cols[:, nb:] = torch.randint(0, n, (n, nnz - nb), generator=g, device=device)
+    while True:
+        srt, order = torch.sort(cols, dim=1, stable=True)
+        dup_sorted = torch.zeros_like(srt, dtype=torch.bool)
+        dup_sorted[:, 1:] = srt[:, 1:] == srt[:, :-1]
+        if not bool(dup_sorted.any()):
+            break
+        dup = torch.zeros_like(dup_sorted)
+        dup.scatter_(1, order, dup_sorted)
+        ri, ci = torch.nonzero(dup, as_tuple=True)
+        isb = ci < nb
+        cols[ri[isb], ci[isb]] = draw_band(ri[isb])
+        cols[ri[~isb], ci[~isb]] = torch.randint(0, n, (int((~isb).sum()),), generator=g, device=device)
+    rs = torch.from_numpy(row_starts(n, P)).to(device)
+    row_owner = torch.searchsorted(rs, rows, right=True) - 1
+    col_owner = torch.searchsorted(rs, cols, right=True) - 1
+    off = col_owner != row_owner[:, None]
+    keys = (row_owner[:, None].expand_as(cols)[off] * n + cols[off])
+    keys = torch.unique(keys)                       # sorted by (receiver, column)
+    rd = keys // n
+    rcol = keys % n
+    rq = torch.searchsorted(rs, rcol, right=True) - 1
+    ek = rd * P + rq
+    starts = torch.nonzero(torch.cat([torch.ones(1, dtype=torch.bool, device=device), ek[1:] != ek[:-1]])).flatten()
+    ends = torch.cat([starts[1:], torch.tensor([len(ek)], device=device)])
+    in_dst, in_src, in_cnt = rd[starts], rq[starts], ends - starts
+    okey = (rq * P + rd) * n + rcol
+    o = torch.argsort(okey)
+    sq, sd, sc = rq[o], rd[o], rcol[o]
+    ok2 = sq * P + sd
+    ostarts = torch.nonzero(torch.cat([torch.ones(1, dtype=torch.bool, device=device), ok2[1:] != ok2[:-1]])).flatten()
+    oends = torch.cat([ostarts[1:], torch.tensor([len(ok2)], device=device)])
+    out_src, out_dst, out_cnt = sq[ostarts], sd[ostarts], oends - ostarts
+    send_elem = sc - rs[sq]
+    c = lambda t: t.cpu().numpy()
+    esz = 8 if dtype == "f64" else 4
+    meta = dict(kind="spmv", n=n, nnz=nnz, band=band, row_starts=c(rs), seed=seed, generator="torch")
+    return _assemble(name or f"spmv_n{n}_P{P}_nnz{nnz}_{dtype}", P, ppn, c(out_src), c(out_dst), c(out_cnt),
+                     c(send_elem), c(sc), c(in_dst), c(in_src), c(in_cnt), c(rcol), esz, dtype,
+                     np.diff(c(rs)), meta)
+
+
+def config3_torch(count=64, device="cuda"):
+    """The uneven batch drawn on the device (see spmv_halo_torch)."""
+    return [spmv_halo_torch(s["n"], s["P"], s["ppn"], s["nnz"], s["seed"], s["dtype"], device=device,
+                            name=f"cfg3_{j}_n{s['n']}_P{s['P']}_{s['dtype']}")
+            for j, s in enumerate(batched_specs(count, SEED + 3))]
