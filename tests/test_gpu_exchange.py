@@ -191,8 +191,7 @@ def test_wait_timeout_returns_error_then_completes():
     send = dev_bytes(x)
     recv = torch.zeros(p.recvbuf_bytes, dtype=torch.uint8, device="cuda")
     ex = gbx.Exchange(p, send, recv, info="timeout_ms=100")
-    cycles = int(torch.cuda.get_device_properties(0).clock_rate * 1000 * 1.0)  # about 1 s
-    torch.cuda._sleep(cycles)
+    torch.cuda._sleep(2_000_000_000)   # a bounded spin of 2e9 SM cycles: about 1 s at 2 GHz
     ex.start()
     with pytest.raises(gbx.GbxError) as e:
         ex.wait()
