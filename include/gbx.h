@@ -61,6 +61,7 @@ extern "C" {
 #define GBX_ERR_INTERNAL    12   /* a move program built at init failed the library's own
                                     device-side validation (a library bug); nothing ran    */
 #define GBX_ERR_OVERLAP     13   /* two receive blocks write the same bytes              */
+#define GBX_ERR_LIMIT       14   /* beyond the fixed capacity of gbx_neighbor_alltoallv_noalloc */
 
 /* payload types: only the backward (which adds) needs to know them */
 #define GBX_BYTES 0
@@ -249,6 +250,44 @@ int gbx_request_bind(gbx_request_t request, const void *src, void *dst);
 int gbx_start_host(gbx_request_t request, const void *host_src, void *host_dst);
 
 int gbx_request_get_info(gbx_request_t request, gbx_request_info_t *info);
+
+/* Largest edge count gbx_neighbor_alltoallv_noalloc accepts (in-edges and out-edges). */
+#define GBX_NOALLOC_MAX_EDGES (1 << 18)
+
+/* One standard neighbourhood all-to-all-v, executed now, that allocates no memory.
+ * The paper has no counterpart of this call; it exists for callers that cannot call
+ * cudaMalloc: code running under a fixed memory budget whose free memory another
+ * allocator already owns (a framework's caching allocator), latency-critical paths
+ * that cannot afford cudaMalloc's implicit device-wide synchronisation, and plug-ins or
+ * callbacks that are not allowed to touch the allocator.  It does no persistent setup
+ * and returns no handle: every call matches, validates and moves in one go.
+ *   Meaning: that of gbx_neighbor_alltoallv_init with send_idx, the slot CSRs and the
+ *   global indices all NULL (a user-packed send buffer, the plain MPI call of
+ *   section 2.2, Listing 3): for every in-edge i of rank d from r, paired under the
+ *   multigraph rule with out-edge e of r,
+ *     recv bytes [recv_base[d] + rdispls[i]*s, +recvcounts[i]*s) =
+ *     send bytes [send_base[r] + sdispls[e]*s, +sendcounts[e]*s).
+ *   Arguments: as gbx_dist_graph_create_adjacent and gbx_neighbor_alltoallv_init; all
+ *   arrays and both buffers are device memory owned by the caller.
+ *   Scratch: the per-edge tables live in one file-scope device array sized for
+ *   GBX_NOALLOC_MAX_EDGES edges (about 6 MB), which every GPU that loads the library
+ *   holds until the process exits.  Edge counts above the limit return GBX_ERR_LIMIT
+ *   before any device work.  The first call on a device looks the array's device address
+ *   up (cudaGetSymbolAddress) with that device current; make that first call before any
+ *   stream capture.  All calls on a device share the array and a call overwrites what the
+ *   previous one left there, so calls that may overlap on the GPU (different streams,
+ *   other host threads) race and must be serialised by the caller.
+ *   Errors: GBX_ERR_ARG, _RANK, _TRUNCATE, _INDEX, _LIMIT, _CUDA as in the persistent
+ *   path; overlapping receive blocks are not detected (MPI makes them erroneous).
+ *   The call enqueues its kernels on `stream` and blocks until they finish, then returns
+ *   the status; nothing is written to the receive buffer unless every check passed. */
+int gbx_neighbor_alltoallv_noalloc(int P, int64_t n_in_edges, const int *in_ptr, const int *sources,
+                                   int64_t n_out_edges, const int *out_ptr, const int *destinations,
+                                   const void *sendbuf, int64_t sendbuf_bytes, const int64_t *send_base,
+                                   const int *sendcounts, const int *sdispls,
+                                   void *recvbuf, int64_t recvbuf_bytes, const int64_t *recv_base,
+                                   const int *recvcounts, const int *rdispls,
+                                   int64_t elem_size, void *stream);
 
 /* MPI_Request_free: waits for an active request, then releases its device memory and
  * any cached batch that contains it. */

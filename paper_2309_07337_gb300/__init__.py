@@ -19,6 +19,7 @@ LIB_PATH = os.path.join(_HERE, "libgbx.so")
 
 SUCCESS, ERR_ARG, ERR_RANK, ERR_TRUNCATE, ERR_INDEX, ERR_DUP, ERR_GIDX = 0, 1, 2, 3, 4, 5, 6
 ERR_ACTIVE, ERR_TIMEOUT, ERR_CUDA, ERR_NOMEM, ERR_UNSUPPORTED, ERR_INTERNAL, ERR_OVERLAP = 7, 8, 9, 10, 11, 12, 13
+ERR_LIMIT = 14
 BYTES, F32, F64 = 0, 1, 2
 ALG_STANDARD, ALG_LOCALITY = 0, 1
 DTYPE_CODES = {"bytes": BYTES, "f32": F32, "f64": F64}

@@ -37,6 +37,7 @@ extern "C" const char *gbx_error_string(int code) {
         case GBX_ERR_UNSUPPORTED: return "unsupported request";
         case GBX_ERR_OVERLAP: return "receive blocks overlap";
         case GBX_ERR_INTERNAL: return "internal error: a generated move program failed validation";
+        case GBX_ERR_LIMIT: return "size beyond the fixed scratch of the allocation-free exchange";
         default: return "unknown error";
     }
 }
