@@ -47,11 +47,14 @@ UNIT = "GB/s"
 def parse_args():
     a = argparse.ArgumentParser()
     a.add_argument("--gpus", type=int, default=1)
-    a.add_argument("--steps", type=int, default=20)
+    a.add_argument("--steps", type=int, default=100)
     a.add_argument("--warmup", type=int, default=5)
     a.add_argument("--impl", default="ours", choices=["ours", "reference"])
     a.add_argument("--e2e-steps", type=int, default=3)
-    a.add_argument("--cpu-sample-ranks", type=int, default=256)
+    a.add_argument("--cpu-sample-ranks", type=int, default=4096,
+                   help="receivers in the CPU-oracle baseline sample (4096 = the whole exchange)")
+    a.add_argument("--ref-sample-ranks", type=int, default=256,
+                   help="receivers per step of --impl reference")
     a.add_argument("--no-extras", action="store_true")
     a.add_argument("--no-e2e", action="store_true")
     a.add_argument("--no-cpu", action="store_true")
@@ -112,7 +115,7 @@ class Clocks:
         self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
         try:
             self.p = subprocess.Popen(["nvidia-smi", f"--id={index}", f"--query-gpu={self.Q}",
-                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                       "--format=csv,noheader,nounits", "-lms", "100"],
                                       stdout=self.f, stderr=subprocess.DEVNULL)
         except Exception:
             self.p = None
@@ -186,7 +189,7 @@ def run_reference(args):
     p = workload(args.edge)
     x = pt.stencil_field(p, pt.SEED + 5)
     g = np.random.default_rng(pt.SEED + 6).standard_normal(p.recvbuf_bytes // 8)
-    n = args.cpu_sample_ranks
+    n = args.ref_sample_ranks
     for _ in range(args.warmup):
         oracle_sample(p, x, g, n)
     ts, ub = [], 0

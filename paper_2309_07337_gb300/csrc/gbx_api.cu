@@ -191,7 +191,9 @@ int gbx_make_fold_op(gbx_request_s *req, int level, char *out, int out_role, con
     op.block = 256;
     op.persistent = 1;
     const int64_t s = req->elem_size;
-    op.algo_bytes = nterms * s + nrows * s * (accumulate ? 2 : 1) + nterms * 8 + nrows * 16;
+    // per row: its 16-byte record, its output element (read too when accumulating); per term:
+    // the gradient element, plus the 8-byte term entry for rows with more than one term
+    op.algo_bytes = nterms * s + nrows * s * (accumulate ? 2 : 1) + nrows * 16 + (nterms - nrows) * 8;
     op.idx_len = nterms;
     FoldDesc &d = op.fd;
     d.out = out; d.bufA = bufA; d.bufB = bufB; d.row_ptr = row_ptr; d.row_out = row_out; d.terms = terms;
@@ -200,6 +202,9 @@ int gbx_make_fold_op(gbx_request_s *req, int level, char *out, int out_role, con
     const int64_t max_tiles = ceil_div(nrows * (s / op.min_vec), GBX_TILE);
     GBX_TRY(req->mem.get(&op.d_tile_e0, max_tiles + 1));
     d.tile_e0 = op.d_tile_e0;
+    GBX_TRY(req->mem.get(&op.d_rec, nrows));
+    GBX_TRY(gbx_build_fold_records(row_ptr, row_out, terms, nrows, op.d_rec, req->stream));
+    d.rec = op.d_rec;
     GBX_TRY(req->mem.alloc(&op.d_desc, sizeof(FoldDesc)));
     GBX_TRY(req->mem.get(&op.d_self, 1));
     GBX_TRY(req->mem.get(&op.d_self_prefix, 2));
@@ -354,10 +359,10 @@ static int tune_op(gbx_request_s *req, HostOp &op) {
 
 // ------------------------------------------------------- levels and the graph
 // One launch per (level, kind, vector class).  Single requests keep every vector class
-// in its own specialised launch; a batch (fixed_block != 0) puts all of a level's copy
-// ops into one launch (the generic kernel when their widths differ).
+// in its own specialised launch; a batch (batch != 0) puts all of a level's copy ops into
+// one launch (the generic kernel when their widths differ).
 static int build_levels(DevPool &mem, const std::vector<HostOp *> &ops, const std::vector<int> &dtypes,
-                        std::vector<LevelLaunch> &out, int fixed_block, cudaStream_t st) {
+                        std::vector<LevelLaunch> &out, int batch, cudaStream_t st) {
     int nlev = 0;
     for (HostOp *op : ops) nlev = std::max(nlev, op->level + 1);
     for (int lv = 0; lv < nlev; lv++)
@@ -369,8 +374,8 @@ static int build_levels(DevPool &mem, const std::vector<HostOp *> &ops, const st
                 if (op->level != lv || op->kind != kind || op_tiles(*op) <= 0) continue;
                 // batches fuse copy ops of every width into one launch; fold ops stay grouped
                 // by payload class (the generic fold kernel needs far more registers)
-                std::pair<int, int> k = (fixed_block && kind == 0) ? std::make_pair(0, 0)
-                                                                   : std::make_pair(kind ? dtypes[i] : 0, op_vec(*op));
+                std::pair<int, int> k = (batch && kind == 0) ? std::make_pair(0, 0)
+                                                             : std::make_pair(kind ? dtypes[i] : 0, op_vec(*op));
                 size_t g = 0;
                 while (g < keys.size() && keys[g] != k) g++;
                 if (g == keys.size()) { keys.push_back(k); groups.emplace_back(); }
@@ -398,9 +403,9 @@ static int build_levels(DevPool &mem, const std::vector<HostOp *> &ops, const st
                     if (op_tiles(*ops[i]) > op_tiles(*big)) big = ops[i];
                 }
                 L.total_tiles = pre.back();
-                L.block = gbx_effective_block(L.vec, fixed_block ? fixed_block : big->block);
-                const int persistent = fixed_block ? 1 : big->persistent;
-                L.grid = grid_for(kind, L.dtype, L.vec, L.block, persistent, L.total_tiles);
+                // the launch takes the tuned shape of its largest op
+                L.block = gbx_effective_block(L.vec, big->block);
+                L.grid = grid_for(kind, L.dtype, L.vec, L.block, big->persistent, L.total_tiles);
                 GBX_TRY(mem.get(&L.d_ops, L.nops));
                 GBX_TRY(mem.get(&L.d_prefix, L.nops + 1));
                 GBX_CUDA_TRY(cudaMemcpyAsync(L.d_ops, ptrs.data(), sizeof(void *) * ptrs.size(),
@@ -714,7 +719,7 @@ extern "C" int gbx_startall(int count, gbx_request_t *reqs) {
         std::vector<int> dts;
         for (gbx_request_s *r : key)
             for (HostOp &op : r->ops) { ops.push_back(&op); dts.push_back(r->dtype); }
-        int rc = build_levels(b->mem, ops, dts, b->launches, 256, st);
+        int rc = build_levels(b->mem, ops, dts, b->launches, 1, st);
         if (rc == GBX_SUCCESS && cudaEventCreateWithFlags(&b->done, cudaEventDisableTiming) != cudaSuccess)
             rc = GBX_ERR_CUDA;
         if (rc == GBX_SUCCESS && !b->launches.empty()) rc = capture(b->launches, &b->exec);

@@ -28,6 +28,10 @@
 #define GBX_TERM_GROUP (1ull << 63)      // fold term: first term of a group
 #define GBX_TERM_BUFB (1ull << 62)       // fold term: reads buffer B (else A)
 #define GBX_TERM_MASK ((1ull << 62) - 1)
+// fold row record: a = output byte offset | GBX_ROW_SINGLE; b = the row's only term when
+// GBX_ROW_SINGLE is set, else (first term index << 24) | term count
+#define GBX_ROW_SINGLE (1ull << 63)
+#define GBX_ROW_CNT_BITS 24
 
 #define GBX_ERR_NONE 0x7fffffff          // device error word: "no error yet"
 
@@ -58,8 +62,9 @@ struct FoldDesc {
     char *out;
     const char *bufA;
     const char *bufB;
-    const int64_t *row_ptr;   // nrows + 1
-    const int64_t *row_out;   // byte offset of each row's output element
+    const int64_t *row_ptr;   // nrows + 1 (setup and validation)
+    const int64_t *row_out;   // byte offset of each row's output element (setup and validation)
+    const longlong2 *rec;     // nrows packed row records (the kernel's view)
     const int64_t *terms;     // byte offset | GBX_TERM_GROUP | GBX_TERM_BUFB
     const int64_t *tile_e0;   // ntiles: first row of each tile
     int64_t nrows, nchunks, ntiles, elem_size;
@@ -161,6 +166,7 @@ struct HostOp {
     CopyDesc cd;     // host copies of the descriptor
     FoldDesc fd;
     void *d_desc;           // device descriptor
+    longlong2 *d_rec;       // fold: packed row records
     int64_t *d_tile_seg;    // copy: tile_seg storage sized for min_vec
     int64_t *d_tile_e0;     // tile_e0 storage sized for min_vec
     void **d_self;          // one-entry descriptor list for launching the op alone
@@ -237,6 +243,8 @@ int gbx_make_copy_op(gbx_request_s *req, int level, const char *src, int src_rol
                      int dst_role, const Seg *segs, int64_t nseg, const int32_t *idx,
                      int64_t idx_len, int64_t nelem, int64_t algo_bytes);
 int gbx_validate_program(gbx_request_s *req, int64_t agg_bytes);
+int gbx_build_fold_records(const int64_t *row_ptr, const int64_t *row_out, const int64_t *terms, int64_t nrows,
+                           longlong2 *rec, cudaStream_t st);
 int gbx_make_fold_op(gbx_request_s *req, int level, char *out, int out_role, const char *bufA,
                      int a_role, const char *bufB, int b_role, const int64_t *row_ptr,
                      const int64_t *row_out, const int64_t *terms, int64_t nrows,

@@ -169,54 +169,64 @@ __device__ __forceinline__ void fold_tile(const FoldDesc *__restrict__ d, int64_
     const uint32_t r0 = (uint32_t)(t * GBX_TILE - e0 * cpe);
     const int64_t left = d->nchunks - t * GBX_TILE;
     const int64_t *__restrict__ terms = d->terms;
-    int64_t rb[U], re[U];
+    // one 16-byte record per row: most rows have a single term, which it holds inline
+    int64_t oa[U], ob[U];
     uint32_t jv[U];
-    bool has[U];
-    PK grp[U], tot[U];
 #pragma unroll
     for (int u = 0; u < U; u++) {
         const uint32_t x = r0 + (uint32_t)(u * B) + threadIdx.x;
         const uint32_t el = unit_of(x, cpe, sh, magic);
         jv[u] = (x - el * (uint32_t)cpe) * VEC;
         const bool ok = (int64_t)(u * B + threadIdx.x) < left;
-        const int64_t row = e0 + el;
-        rb[u] = ok ? __ldg(d->row_ptr + row) : 0;
-        re[u] = ok ? __ldg(d->row_ptr + row + 1) : 0;
-        has[u] = false;
-    }
-    for (int64_t m = 0;; m++) {
-        bool any = false;
-        int64_t tm[U];
-#pragma unroll
-        for (int u = 0; u < U; u++) {
-            tm[u] = 0;
-            if (rb[u] + m < re[u]) { tm[u] = __ldg(terms + rb[u] + m); any = true; }
+        if (ok) {
+            const longlong2 r = __ldg(d->rec + e0 + el);
+            oa[u] = r.x;
+            ob[u] = r.y;
+        } else {
+            oa[u] = 0;
+            ob[u] = 0;
         }
-        if (!any) break;
+    }
+    PK res[U];
+    bool multi = false;
+#pragma unroll
+    for (int u = 0; u < U; u++) {
+        if ((uint64_t)oa[u] & GBX_ROW_SINGLE) {
+            const uint64_t w = (uint64_t)ob[u];
+            res[u] = pload<PK>(((w & GBX_TERM_BUFB) ? d->bufB : d->bufA) + (int64_t)(w & GBX_TERM_MASK) + jv[u]);
+        } else if ((int64_t)(u * B + threadIdx.x) < left) {
+            multi = true;
+        }
+    }
+    if (multi) {
 #pragma unroll
         for (int u = 0; u < U; u++) {
-            if (rb[u] + m >= re[u]) continue;
-            const uint64_t w = (uint64_t)tm[u];
-            const char *base = (w & GBX_TERM_BUFB) ? d->bufB : d->bufA;
-            const PK x = pload<PK>(base + (int64_t)(w & GBX_TERM_MASK) + jv[u]);
-            if (m == 0) {
-                grp[u] = x;
-            } else if (w & GBX_TERM_GROUP) {
-                tot[u] = has[u] ? padd(tot[u], grp[u]) : grp[u];
-                has[u] = true;
-                grp[u] = x;
-            } else {
-                grp[u] = padd(grp[u], x);
+            if (((uint64_t)oa[u] & GBX_ROW_SINGLE) || (int64_t)(u * B + threadIdx.x) >= left) continue;
+            const int64_t b = (int64_t)((uint64_t)ob[u] >> GBX_ROW_CNT_BITS);
+            const int64_t n = (int64_t)((uint64_t)ob[u] & ((1ull << GBX_ROW_CNT_BITS) - 1));
+            PK grp, tot;
+            bool has = false;
+            for (int64_t m = 0; m < n; m++) {
+                const uint64_t w = (uint64_t)__ldg(terms + b + m);
+                const PK x = pload<PK>(((w & GBX_TERM_BUFB) ? d->bufB : d->bufA) + (int64_t)(w & GBX_TERM_MASK) + jv[u]);
+                if (m == 0) {
+                    grp = x;
+                } else if (w & GBX_TERM_GROUP) {
+                    tot = has ? padd(tot, grp) : grp;
+                    has = true;
+                    grp = x;
+                } else {
+                    grp = padd(grp, x);
+                }
             }
+            res[u] = has ? padd(tot, grp) : grp;
         }
     }
 #pragma unroll
     for (int u = 0; u < U; u++) {
         if ((int64_t)(u * B + threadIdx.x) >= left) continue;
-        const uint32_t x = r0 + (uint32_t)(u * B) + threadIdx.x;
-        const int64_t row = e0 + unit_of(x, cpe, sh, magic);
-        PK r = has[u] ? padd(tot[u], grp[u]) : grp[u];
-        PK *o = reinterpret_cast<PK *>(d->out + __ldg(d->row_out + row) + jv[u]);
+        PK *o = reinterpret_cast<PK *>(d->out + (oa[u] & (int64_t)~GBX_ROW_SINGLE) + jv[u]);
+        PK r = res[u];
         if (d->accumulate) r = padd(*o, r);
         *o = r;
     }

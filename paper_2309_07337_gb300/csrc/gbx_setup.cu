@@ -1052,13 +1052,18 @@ __global__ void check_copy_idx_kernel(const Seg *segs, int64_t nseg, int64_t nel
     }
 }
 
-__global__ void check_fold_kernel(const int64_t *row_ptr, const int64_t *row_out, const int64_t *terms, int64_t nrows,
-                                  int64_t nterms, int64_t s, int64_t out_bytes, int64_t a_bytes, int64_t b_bytes,
-                                  int *err) {
+__global__ void check_fold_kernel(const int64_t *row_ptr, const int64_t *row_out, const longlong2 *rec,
+                                  const int64_t *terms, int64_t nrows, int64_t nterms, int64_t s, int64_t out_bytes,
+                                  int64_t a_bytes, int64_t b_bytes, int *err) {
     FOR_EACH(r, nrows) {
         const int64_t b = row_ptr[r], e = row_ptr[r + 1];
         bool ok = b < e && (r > 0 || b == 0) && (r + 1 < nrows || e == nterms) && e <= nterms &&
                   row_out[r] >= 0 && row_out[r] + s <= out_bytes;
+        const longlong2 x = rec[r];
+        if (e - b == 1)
+            ok = ok && (uint64_t)x.x == ((uint64_t)row_out[r] | GBX_ROW_SINGLE) && x.y == terms[b];
+        else
+            ok = ok && x.x == row_out[r] && (uint64_t)x.y == (((uint64_t)b << GBX_ROW_CNT_BITS) | (uint64_t)(e - b));
         for (int64_t m = b; ok && m < e; m++) {
             const uint64_t w = (uint64_t)terms[m];
             const int64_t off = (int64_t)(w & GBX_TERM_MASK);
@@ -1090,11 +1095,41 @@ int gbx_validate_program(gbx_request_s *req, int64_t agg_bytes) {
                                                                             d.elem_size, bytes_of(d.src_role), err);
         } else {
             const FoldDesc &d = op.fd;
-            check_fold_kernel<<<grid_of(d.nrows), SETUP_T, 0, st>>>(d.row_ptr, d.row_out, d.terms, d.nrows,
+            check_fold_kernel<<<grid_of(d.nrows), SETUP_T, 0, st>>>(d.row_ptr, d.row_out, d.rec, d.terms, d.nrows,
                                                                     op.idx_len, d.elem_size, bytes_of(d.out_role),
                                                                     bytes_of(d.a_role), bytes_of(d.b_role), err);
         }
         GBX_CUDA_TRY(cudaGetLastError());
     }
+    return read_err_stage(err, st);
+}
+
+// packed row records of a fold op (see GBX_ROW_SINGLE)
+__global__ void fold_rec_kernel(const int64_t *row_ptr, const int64_t *row_out, const int64_t *terms, int64_t nrows,
+                                longlong2 *rec, int *err) {
+    FOR_EACH(r, nrows) {
+        const int64_t b = row_ptr[r], n = row_ptr[r + 1] - b;
+        longlong2 x;
+        if (n == 1) {
+            x.x = (long long)((uint64_t)row_out[r] | GBX_ROW_SINGLE);
+            x.y = terms[b];
+        } else {
+            x.x = row_out[r];
+            x.y = (long long)(((uint64_t)b << GBX_ROW_CNT_BITS) | (uint64_t)n);
+            if (n <= 0 || n >= (1ll << GBX_ROW_CNT_BITS) || b >= (1ll << (64 - GBX_ROW_CNT_BITS)))
+                set_err(err, GBX_ERR_UNSUPPORTED);
+        }
+        rec[r] = x;
+    }
+}
+
+int gbx_build_fold_records(const int64_t *row_ptr, const int64_t *row_out, const int64_t *terms, int64_t nrows,
+                           longlong2 *rec, cudaStream_t st) {
+    DevPool ws;
+    int *err;
+    GBX_TRY(ws.get(&err, 1));
+    GBX_CUDA_TRY(cudaMemsetAsync(err, 0x7f, sizeof(int), st));
+    fold_rec_kernel<<<grid_of(nrows), SETUP_T, 0, st>>>(row_ptr, row_out, terms, nrows, rec, err);
+    GBX_CUDA_TRY(cudaGetLastError());
     return read_err_stage(err, st);
 }
