@@ -173,6 +173,13 @@ int gbx_graph_free(gbx_graph_t *graph);
  *       graph=0|1          capture the start sequence in a CUDA graph (default 1)
  *       autotune=0|1       time candidate kernel shapes at init (default 1)
  *       vec=V block=B      force the move kernel's vector width / block size
+ *       min_run=N          gathered runs of >= N consecutive source elements are copied as
+ *                          contiguous blocks (default 4; 0 keeps every element gathered)
+ *       flat=0|1           force / forbid the flat form of a copy (one contiguous destination
+ *                          run, one source index per element, no segment search); by
+ *                          default the autotuner picks it where it applies
+ *       piece=N            run copies in ascending source order, in pieces of <= N elements
+ *                          (default 0: receive order)
  *       timeout_ms=T       limit of gbx_wait (default 60000)
  * Errors: GBX_ERR_ARG, _TRUNCATE, _INDEX, _GIDX, _OVERLAP (receive blocks must not
  * overlap), _NOMEM, _CUDA.  Validation and map building run as device kernels; the
@@ -202,11 +209,15 @@ int gbx_neighbor_alltoallv_init(const void *sendbuf, int64_t sendbuf_bytes,
  *     pair, then per source element its groups folded in ascending destination node
  *     (its own node's group = its direct slots in (rank, position) order).
  * accumulate=0 stores the sum, accumulate=1 adds it to the existing value; elements no
- * slot reads are never written.  Adds are IEEE round-to-nearest in the payload type
+ * slot reads are never written.  Init's autotuner may write grad_send (with the correct
+ * sums for the gradients present then) when accumulate=0; with accumulate=1 it never
+ * launches, so grad_send is untouched until the first start.  Adds are IEEE round-to-nearest in the payload type
  * (dtype of the forward must be GBX_F32 or GBX_F64, elem_size a multiple of it); the
  * order is fixed, so results are bitwise reproducible.  Buffers and base offsets must be
  * aligned to the payload type (GBX_ERR_UNSUPPORTED otherwise).  The forward request must
- * outlive the backward one.  info: graph=, autotune=, timeout_ms= as above. */
+ * outlive the backward one.  info: graph=, autotune=, timeout_ms=, vec=, block= as above;
+ * single_split=0 keeps rows with a single term in the summing kernel (by default, without
+ * accumulate, such rows are plain copies and run as one two-index gather-scatter). */
 int gbx_backward_init(gbx_request_t forward, const void *grad_recv, void *grad_send,
                       int accumulate, const char *info, void *stream,
                       gbx_request_t *request);

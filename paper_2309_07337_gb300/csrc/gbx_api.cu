@@ -48,7 +48,8 @@ extern "C" int gbx_version(void) { return 100; }
 struct Opts {
     int algorithm = GBX_ALG_STANDARD;
     int algorithm_auto = 0;
-    int graph = 1, autotune = 1, vec = 0, block = 0, timeout_ms = 60000;
+    int graph = 1, autotune = 1, vec = 0, block = 0, timeout_ms = 60000, min_run = 4, piece = 0, flat = -1;
+    int split = 1;
     bool ok = true;
 };
 
@@ -76,11 +77,15 @@ static Opts parse_info(const char *info) {
         else if (k == "vec") o.vec = atoi(v.c_str());
         else if (k == "block") o.block = atoi(v.c_str());
         else if (k == "timeout_ms") o.timeout_ms = atoi(v.c_str());
+        else if (k == "min_run") o.min_run = atoi(v.c_str());
+        else if (k == "piece") o.piece = atoi(v.c_str());
+        else if (k == "flat") o.flat = atoi(v.c_str()) != 0;
+        else if (k == "single_split") o.split = atoi(v.c_str()) != 0;
         else o.ok = false;
     }
     if (o.vec && !(o.vec == 1 || o.vec == 2 || o.vec == 4 || o.vec == 8 || o.vec == 16)) o.ok = false;
     if (o.block && !(o.block == 128 || o.block == 256 || o.block == 512 || o.block == 1024)) o.ok = false;
-    if (o.timeout_ms <= 0) o.ok = false;
+    if (o.timeout_ms <= 0 || o.min_run < 0 || o.piece < 0) o.ok = false;
     return o;
 }
 
@@ -147,6 +152,25 @@ int gbx_make_copy_op(gbx_request_s *req, int level, const char *src, int src_rol
                      const Seg *segs, int64_t nseg, const int32_t *idx, int64_t idx_len, int64_t nelem,
                      int64_t algo_bytes) {
     if (nelem <= 0) return GBX_SUCCESS;
+    if (idx && req->min_run > 0) {
+        // contiguous source runs become contiguous segments (same elements, same bytes)
+        Seg *split = nullptr;
+        int64_t nsplit = 0;
+        GBX_TRY(gbx_split_runs(req, segs, nseg, idx, nelem, req->min_run, &split, &nsplit));
+        algo_bytes += (nsplit - nseg) * (int64_t)sizeof(Seg);
+        segs = split;
+        nseg = nsplit;
+    }
+    if (req->piece > 0) {
+        // pieces in ascending source address (same elements, same bytes)
+        const int64_t src_bytes = src_role == ROLE_SRC ? req->src_bytes : 2 * req->U * req->elem_size;
+        Seg *ord = nullptr;
+        int64_t nord = 0;
+        GBX_TRY(gbx_order_by_source(req, segs, nseg, idx, nelem, src_bytes, req->piece, &ord, &nord));
+        algo_bytes += (nord - nseg) * (int64_t)sizeof(Seg);
+        segs = ord;
+        nseg = nord;
+    }
     HostOp op;
     memset(&op, 0, sizeof(op));
     op.kind = 0;
@@ -170,7 +194,56 @@ int gbx_make_copy_op(gbx_request_s *req, int level, const char *src, int src_rol
     GBX_TRY(req->mem.get(&op.d_self_prefix, 2));
     d.tile_seg = op.d_tile_seg;
     d.tile_e0 = op.d_tile_e0;
+    if (req->allow_flat) {
+        GBX_TRY(gbx_make_flat(req, segs, nseg, idx, nelem, &op.d_flat_idx, &op.flat_dst0, &op.flat_ok));
+        d.flat_idx = op.d_flat_idx;
+        d.dst_flat0 = op.flat_dst0;
+        op.algo_bytes_flat = 2 * nelem * req->elem_size + 4 * nelem;
+    }
     req->ops.push_back(op);
+    return GBX_SUCCESS;
+}
+
+int gbx_make_flat_op(gbx_request_s *req, int level, const char *src, int src_role, const char *src2, int src2_role,
+                     char *dst, int dst_role, const int32_t *g, int64_t nelem, int64_t dst0) {
+    if (nelem <= 0) return GBX_SUCCESS;
+    HostOp op;
+    memset(&op, 0, sizeof(op));
+    op.kind = 0;
+    op.level = level;
+    op.units = nelem;
+    op.max_vec = vec_of_align(req->align);
+    op.min_vec = req->forced_vec ? std::min(req->forced_vec, op.max_vec) : std::max(1, op.max_vec / 2);
+    if (req->forced_vec) op.max_vec = op.min_vec;
+    op.block = 256;
+    op.persistent = 1;
+    op.flat_ok = 1;
+    op.flat_only = 1;
+    op.algo_bytes = op.algo_bytes_flat = 2 * nelem * req->elem_size + 4 * nelem;
+    op.idx_len = 0;
+    op.d_flat_idx = (int32_t *)g;
+    op.flat_dst0 = dst0;
+    CopyDesc &d = op.cd;
+    d.src = src; d.dst = dst; d.segs = nullptr; d.idx = nullptr; d.nseg = 0; d.nelem = nelem;
+    d.elem_size = req->elem_size; d.src_role = src_role; d.dst_role = dst_role;
+    d.flat = 1; d.flat_idx = g; d.dst_flat0 = dst0; d.src2 = src2; d.src2_role = src2_role;
+    const int64_t max_tiles = ceil_div(nelem * (req->elem_size / op.min_vec), GBX_TILE);
+    GBX_TRY(req->mem.get(&op.d_tile_e0, max_tiles + 1));
+    d.tile_e0 = op.d_tile_e0;
+    GBX_TRY(req->mem.alloc(&op.d_desc, sizeof(CopyDesc)));
+    GBX_TRY(req->mem.get(&op.d_self, 1));
+    GBX_TRY(req->mem.get(&op.d_self_prefix, 2));
+    req->ops.push_back(op);
+    return GBX_SUCCESS;
+}
+
+int gbx_make_flat2_op(gbx_request_s *req, int level, const char *src, int src_role, const char *src2, int src2_role,
+                      char *dst, int dst_role, const int32_t *gs, const int32_t *gd, int64_t nelem) {
+    GBX_TRY(gbx_make_flat_op(req, level, src, src_role, src2, src2_role, dst, dst_role, gs, nelem, 0));
+    HostOp &op = req->ops.back();
+    op.cd.flat = 3;
+    op.cd.flat_didx = gd;
+    op.algo_bytes = op.algo_bytes_flat = 2 * nelem * req->elem_size + 8 * nelem;
     return GBX_SUCCESS;
 }
 
@@ -178,6 +251,23 @@ int gbx_make_fold_op(gbx_request_s *req, int level, char *out, int out_role, con
                      const char *bufB, int b_role, const int64_t *row_ptr, const int64_t *row_out,
                      const int64_t *terms, int64_t nrows, int64_t nterms, int accumulate) {
     if (nrows <= 0) return GBX_SUCCESS;
+    if (!accumulate && !req->no_single_split) {
+        // rows with one term are copies: a two-index flat copy op takes them
+        int32_t *gs = nullptr, *gd = nullptr;
+        int64_t *rp2 = nullptr, *ro2 = nullptr, *t2 = nullptr, ns = 0, nm = 0, nt = 0;
+        int ok = 0;
+        GBX_TRY(gbx_split_single_rows(req, row_ptr, row_out, terms, nrows, &gs, &gd, &ns, &rp2, &ro2, &t2, &nm, &nt,
+                                      &ok));
+        if (ok) {
+            GBX_TRY(gbx_make_flat2_op(req, level, bufA, a_role, bufB, b_role, out, out_role, gs, gd, ns));
+            if (nm == 0) return GBX_SUCCESS;
+            row_ptr = rp2;
+            row_out = ro2;
+            terms = t2;
+            nrows = nm;
+            nterms = nt;
+        }
+    }
     HostOp op;
     memset(&op, 0, sizeof(op));
     op.kind = 1;
@@ -234,7 +324,10 @@ static int set_vec(gbx_request_s *req, HostOp &op, int vec) {
         d.vec = vec; d.cpe = cpe; d.cpe_shift = shift; d.cpe_magic = magic;
         d.nchunks = d.nelem * cpe;
         d.ntiles = ceil_div(d.nchunks, GBX_TILE);
-        GBX_TRY(gbx_build_tile_meta(d.segs, d.nseg, cpe, d.ntiles, op.d_tile_seg, op.d_tile_e0, req->stream));
+        if (op.flat_only)
+            GBX_TRY(gbx_build_tile_meta(nullptr, 0, cpe, d.ntiles, nullptr, op.d_tile_e0, req->stream));
+        else
+            GBX_TRY(gbx_build_tile_meta(d.segs, d.nseg, cpe, d.ntiles, op.d_tile_seg, op.d_tile_e0, req->stream));
     } else {
         FoldDesc &d = op.fd;
         d.vec = vec; d.cpe = cpe; d.cpe_shift = shift; d.cpe_magic = magic;
@@ -253,24 +346,26 @@ static int set_vec(gbx_request_s *req, HostOp &op, int vec) {
 
 static int op_vec(const HostOp &op) { return op.kind == 0 ? op.cd.vec : op.fd.vec; }
 
-static int grid_for(int kind, int dtype, int vec, int block, int persistent, int64_t tiles) {
+static int grid_for(int kind, int dtype, int vec, int flat, int block, int persistent, int64_t tiles) {
     if (!persistent) return (int)std::min<int64_t>(tiles, 1ll << 30);
-    int64_t g = (int64_t)gbx_num_sms() * gbx_occupancy(kind, dtype, vec, block);
+    int64_t g = (int64_t)gbx_num_sms() * gbx_occupancy(kind, dtype, vec, block, flat);
     return (int)std::max<int64_t>(1, std::min<int64_t>(g, tiles));
 }
 
-static cudaError_t launch_list(int kind, int dtype, int vec, void **d_ops, int64_t *d_prefix, int nops,
+static cudaError_t launch_list(int kind, int dtype, int vec, int flat, void **d_ops, int64_t *d_prefix, int nops,
                                int64_t tiles, int block, int grid, cudaStream_t st) {
     if (kind == 0)
-        return gbx_launch_copy((const CopyDesc *const *)d_ops, d_prefix, nops, tiles, vec, block, grid, st);
+        return gbx_launch_copy((const CopyDesc *const *)d_ops, d_prefix, nops, tiles, vec, flat, block, grid, st);
     return gbx_launch_fold((const FoldDesc *const *)d_ops, d_prefix, nops, tiles, dtype, vec, block, grid, st);
 }
 
+static int op_flat(const HostOp &op) { return op.kind == 0 ? op.cd.flat : 0; }
+
 static cudaError_t launch_op_alone(gbx_request_s *req, HostOp &op, int block, int persistent) {
     int64_t tiles = op_tiles(op);
-    const int vec = op_vec(op);
-    return launch_list(op.kind, req->dtype, vec, op.d_self, op.d_self_prefix, 1, tiles, block,
-                       grid_for(op.kind, req->dtype, vec, block, persistent, tiles), req->stream);
+    const int vec = op_vec(op), flat = op_flat(op);
+    return launch_list(op.kind, req->dtype, vec, flat, op.d_self, op.d_self_prefix, 1, tiles, block,
+                       grid_for(op.kind, req->dtype, vec, flat, block, persistent, tiles), req->stream);
 }
 
 // ------------------------------------------------------------------ autotuner
@@ -279,13 +374,13 @@ static cudaError_t launch_op_alone(gbx_request_s *req, HostOp &op, int block, in
 // the shape: every candidate moves the same bytes to the same places.  Chosen shapes are
 // cached by a signature of the op, so identical patterns are tuned once per process.
 struct TuneKey {
-    int kind, max_vec, min_vec, dtype;
+    int kind, max_vec, min_vec, dtype, flat_ok;
     int64_t units, nseg, elem_size, nterms;
     bool operator<(const TuneKey &o) const {
         return memcmp(this, &o, sizeof(TuneKey)) < 0;
     }
 };
-struct TuneVal { int vec, block, persistent; float ms; };
+struct TuneVal { int vec, block, persistent, flat; float ms; };
 static std::map<TuneKey, TuneVal> g_tune_cache;
 static std::mutex g_tune_mu;
 
@@ -321,11 +416,23 @@ static int tune_op(gbx_request_s *req, HostOp &op) {
     key.units = op.units; key.elem_size = req->elem_size;
     key.nseg = op.kind == 0 ? op.cd.nseg : 0;
     key.nterms = op.kind == 1 ? op.fd.nchunks : 0;
+    key.flat_ok = op.kind == 0 ? op.flat_ok + 2 * op.flat_only + 4 * (op.cd.flat == 3) : 0;
     int blocks[4] = {128, 256, 512, 1024};
     if (!req->autotune || req->forced_block) {
         op.block = req->forced_block ? req->forced_block : 256;
         op.persistent = 1;
+        if (op.kind == 0 && !op.flat_only) op.cd.flat = op.flat_ok && req->forced_flat != 0;
+        if (op.kind == 0 && op.cd.flat) op.algo_bytes = op.algo_bytes_flat;
         return set_vec(req, op, op.max_vec);
+    }
+    if (op.kind == 1 && op.fd.accumulate) {
+        // an accumulating fold adds into the caller's buffer, so it is never trial-launched:
+        // it takes the shape tuned for the same rows without accumulation, or the default
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tune_cache.find(key);
+        op.block = it != g_tune_cache.end() ? it->second.block : 256;
+        op.persistent = it != g_tune_cache.end() ? it->second.persistent : 1;
+        return set_vec(req, op, it != g_tune_cache.end() ? it->second.vec : op.max_vec);
     }
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
@@ -334,23 +441,31 @@ static int tune_op(gbx_request_s *req, HostOp &op) {
             op.block = it->second.block;
             op.persistent = it->second.persistent;
             op.tuned_ms = it->second.ms;
+            if (op.kind == 0 && !op.flat_only) op.cd.flat = it->second.flat;
+            if (op.kind == 0 && op.cd.flat) op.algo_bytes = op.algo_bytes_flat;
             return set_vec(req, op, it->second.vec);
         }
     }
-    TuneVal best = {op.max_vec, 256, 1, 1e30f};
-    for (int vec = op.max_vec; vec >= op.min_vec; vec >>= 1) {
-        GBX_TRY(set_vec(req, op, vec));
-        for (int bi = 0; bi < 4; bi++)
-            for (int pers = 1; pers >= 0; pers--) {
-                float ms = 0;
-                GBX_TRY(time_op(req, op, blocks[bi], pers, 3, &ms));
-                if (ms < best.ms) best = {vec, blocks[bi], pers, ms};
-            }
-        if (vec == 1) break;
+    TuneVal best = {op.max_vec, 256, 1, 0, 1e30f};
+    const int nflat = (op.kind == 0 && op.flat_ok && !op.flat_only && req->forced_flat < 0) ? 2 : 1;
+    for (int fl = 0; fl < nflat; fl++) {
+        if (op.kind == 0 && !op.flat_only) op.cd.flat = nflat == 2 ? fl : (op.flat_ok && req->forced_flat > 0);
+        for (int vec = op.max_vec; vec >= op.min_vec; vec >>= 1) {
+            GBX_TRY(set_vec(req, op, vec));
+            for (int bi = 0; bi < 4; bi++)
+                for (int pers = 1; pers >= 0; pers--) {
+                    float ms = 0;
+                    GBX_TRY(time_op(req, op, blocks[bi], pers, 3, &ms));
+                    if (ms < best.ms) best = {vec, blocks[bi], pers, op.kind == 0 ? op.cd.flat : 0, ms};
+                }
+            if (vec == 1) break;
+        }
     }
     op.block = best.block;
     op.persistent = best.persistent;
     op.tuned_ms = best.ms;
+    if (op.kind == 0 && !op.flat_only) op.cd.flat = best.flat;
+    if (op.kind == 0 && op.cd.flat) op.algo_bytes = op.algo_bytes_flat;
     GBX_TRY(set_vec(req, op, best.vec));
     std::lock_guard<std::mutex> lk(g_tune_mu);
     g_tune_cache[key] = best;
@@ -358,9 +473,10 @@ static int tune_op(gbx_request_s *req, HostOp &op) {
 }
 
 // ------------------------------------------------------- levels and the graph
-// One launch per (level, kind, vector class).  Single requests keep every vector class
-// in its own specialised launch; a batch (batch != 0) puts all of a level's copy ops into
-// one launch (the generic kernel when their widths differ).
+// One launch per (level, kind, class): a class is (form, vector width) for copies and
+// (payload type, vector width) for folds, so every launch runs a specialised kernel.  For a
+// batch the ops of all its requests are pooled, so each launch covers every pattern of its
+// class (the generic width-dispatching kernels stay available but are not needed).
 static int build_levels(DevPool &mem, const std::vector<HostOp *> &ops, const std::vector<int> &dtypes,
                         std::vector<LevelLaunch> &out, int batch, cudaStream_t st) {
     int nlev = 0;
@@ -368,14 +484,14 @@ static int build_levels(DevPool &mem, const std::vector<HostOp *> &ops, const st
     for (int lv = 0; lv < nlev; lv++)
         for (int kind = 0; kind < 2; kind++) {
             std::vector<std::vector<size_t>> groups;
-            std::vector<std::pair<int, int>> keys;   // (dtype, vec) of each group
+            std::vector<std::pair<int, int>> keys;   // (dtype or form, vec) of each group
             for (size_t i = 0; i < ops.size(); i++) {
                 HostOp *op = ops[i];
                 if (op->level != lv || op->kind != kind || op_tiles(*op) <= 0) continue;
-                // batches fuse copy ops of every width into one launch; fold ops stay grouped
-                // by payload class (the generic fold kernel needs far more registers)
-                std::pair<int, int> k = (batch && kind == 0) ? std::make_pair(0, 0)
-                                                             : std::make_pair(kind ? dtypes[i] : 0, op_vec(*op));
+                // every launch is specialised: ops are grouped by (form, vector width) for copies
+                // and (payload type, vector width) for folds; a batch fuses all patterns of a class
+                std::pair<int, int> k = kind ? std::make_pair(dtypes[i], op_vec(*op))
+                                             : std::make_pair(op_flat(*op), op_vec(*op));
                 size_t g = 0;
                 while (g < keys.size() && keys[g] != k) g++;
                 if (g == keys.size()) { keys.push_back(k); groups.emplace_back(); }
@@ -385,15 +501,17 @@ static int build_levels(DevPool &mem, const std::vector<HostOp *> &ops, const st
                 LevelLaunch L;
                 L.kind = kind;
                 L.nops = (int)groups[g].size();
-                // common payload type and vector width, or 0 (= mixed)
-                int dt = dtypes[groups[g][0]], vec = op_vec(*ops[groups[g][0]]);
+                // common payload type, vector width and form, or 0 / 2 (= mixed)
+                int dt = dtypes[groups[g][0]], vec = op_vec(*ops[groups[g][0]]), fl = op_flat(*ops[groups[g][0]]);
                 for (size_t i : groups[g]) {
                     if (dtypes[i] != dt) dt = -1;
                     if (op_vec(*ops[i]) != vec) vec = 0;
+                    if (op_flat(*ops[i]) != fl) fl = 2;
                 }
-                if (dt < 0) vec = 0;
+                if (dt < 0 && kind == 1) vec = 0;
                 L.dtype = dt < 0 ? GBX_F32 : dt;
                 L.vec = vec;
+                L.flat = vec == 0 ? 2 : fl;
                 std::vector<void *> ptrs;
                 std::vector<int64_t> pre(1, 0);
                 const HostOp *big = ops[groups[g][0]];
@@ -405,7 +523,7 @@ static int build_levels(DevPool &mem, const std::vector<HostOp *> &ops, const st
                 L.total_tiles = pre.back();
                 // the launch takes the tuned shape of its largest op
                 L.block = gbx_effective_block(L.vec, big->block);
-                L.grid = grid_for(kind, L.dtype, L.vec, L.block, big->persistent, L.total_tiles);
+                L.grid = grid_for(kind, L.dtype, L.vec, L.flat, L.block, big->persistent, L.total_tiles);
                 GBX_TRY(mem.get(&L.d_ops, L.nops));
                 GBX_TRY(mem.get(&L.d_prefix, L.nops + 1));
                 GBX_CUDA_TRY(cudaMemcpyAsync(L.d_ops, ptrs.data(), sizeof(void *) * ptrs.size(),
@@ -421,8 +539,8 @@ static int build_levels(DevPool &mem, const std::vector<HostOp *> &ops, const st
 
 static cudaError_t enqueue_levels(const std::vector<LevelLaunch> &levels, cudaStream_t st) {
     for (const LevelLaunch &L : levels) {
-        cudaError_t e = launch_list(L.kind, L.dtype, L.vec, L.d_ops, L.d_prefix, L.nops, L.total_tiles, L.block,
-                                    L.grid, st);
+        cudaError_t e = launch_list(L.kind, L.dtype, L.vec, L.flat, L.d_ops, L.d_prefix, L.nops, L.total_tiles,
+                                    L.block, L.grid, st);
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
@@ -520,6 +638,12 @@ static gbx_request_s *new_request(const Opts &o, void *stream) {
     req->forced_vec = o.vec;
     req->forced_block = o.block;
     req->timeout_ms = o.timeout_ms;
+    req->min_run = o.min_run;
+    req->piece = o.piece;
+    req->forced_flat = o.flat;
+    req->allow_flat = o.flat != 0;
+    req->no_combine = o.flat == 0;
+    req->no_single_split = !o.split;
     if (cudaEventCreateWithFlags(&req->done, cudaEventDisableTiming) != cudaSuccess) {
         cudaGetLastError();
         req->done = nullptr;

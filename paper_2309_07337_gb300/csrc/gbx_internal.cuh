@@ -56,7 +56,19 @@ struct CopyDesc {
     int32_t vec, cpe, cpe_shift;  // chunks per element; log2 of it, or -1
     uint32_t cpe_magic;           // ceil(2^32 / cpe) when cpe is not a power of two
     int32_t src_role, dst_role;
+    // flat form (when set): destinations are one contiguous run from dst_flat0 and element
+    // e reads source element flat_idx[e]; no segment search
+    int32_t flat;
+    const int32_t *flat_idx;
+    int64_t dst_flat0;
+    // flat form with two sources: an index with bit 31 set reads src2 (e.g. the receive
+    // aggregate) instead of src
+    const char *src2;
+    int32_t src2_role;
+    // two-index flat form (flat == 3): element e also writes destination element flat_didx[e]
+    const int32_t *flat_didx;
 };
+#define GBX_FLAT_SRC2 0x80000000u
 
 struct FoldDesc {
     char *out;
@@ -124,9 +136,10 @@ int gbx_read_i64(const int64_t *d, int64_t *h, cudaStream_t st);
 // launch mixes ops of different widths (batched patterns).
 int gbx_num_sms(void);
 int gbx_effective_block(int vec, int block);
-int gbx_occupancy(int kind, int dtype, int vec, int block);   // resident blocks per SM
+int gbx_occupancy(int kind, int dtype, int vec, int block, int flat);   // resident blocks per SM
+// flat: 0 every op in segment form, 1 every op in flat form, 2 decided per op
 cudaError_t gbx_launch_copy(const CopyDesc *const *ops, const int64_t *tile_prefix, int nops,
-                            int64_t total_tiles, int vec, int block, int grid, cudaStream_t st);
+                            int64_t total_tiles, int vec, int flat, int block, int grid, cudaStream_t st);
 cudaError_t gbx_launch_fold(const FoldDesc *const *ops, const int64_t *tile_prefix, int nops,
                             int64_t total_tiles, int dtype, int vec, int block, int grid,
                             cudaStream_t st);
@@ -169,6 +182,11 @@ struct HostOp {
     longlong2 *d_rec;       // fold: packed row records
     int64_t *d_tile_seg;    // copy: tile_seg storage sized for min_vec
     int64_t *d_tile_e0;     // tile_e0 storage sized for min_vec
+    int32_t *d_flat_idx;    // copy: source element of every element when the flat form applies
+    int64_t flat_dst0;
+    int flat_ok;            // the flat form is available
+    int flat_only;          // the op exists only in flat form (cd.flat is 1 or 3)
+    int64_t algo_bytes_flat;
     void **d_self;          // one-entry descriptor list for launching the op alone
     int64_t *d_self_prefix; // {0, ntiles}
 };
@@ -178,6 +196,7 @@ struct LevelLaunch {
     int kind;
     int dtype;              // fold: payload type
     int vec;                // vector width of every op, or 0 when they differ
+    int flat;               // copy: 0 / 1 when every op uses the segment / flat form, 2 mixed
     int block;
     int grid;
     int nops;
@@ -193,6 +212,12 @@ struct gbx_request_s {
     int kind;                // 0 forward, 1 backward
     int algorithm;
     int use_graph, autotune, forced_vec, forced_block;
+    int min_run;             // gathered runs of at least this many elements become contiguous (0 = off)
+    int piece;               // > 0: copy ops run in source order, in pieces of at most this many elements
+    int forced_flat;         // -1: the tuner chooses the flat form or segments; 0 / 1: forced
+    int allow_flat;
+    int no_combine;          // locality form: keep direct copies and redistribution apart
+    int no_single_split;     // keep single-term fold rows in the fold
     int timeout_ms;
     gbx_graph_s *graph;
     gbx_request_s *forward;  // backward: its forward request
@@ -243,6 +268,19 @@ int gbx_make_copy_op(gbx_request_s *req, int level, const char *src, int src_rol
                      int dst_role, const Seg *segs, int64_t nseg, const int32_t *idx,
                      int64_t idx_len, int64_t nelem, int64_t algo_bytes);
 int gbx_validate_program(gbx_request_s *req, int64_t agg_bytes);
+int gbx_split_runs(gbx_request_s *req, const Seg *segs, int64_t nseg, const int32_t *idx, int64_t nelem,
+                   int min_run, Seg **out, int64_t *out_nseg);
+int gbx_make_flat_op(gbx_request_s *req, int level, const char *src, int src_role, const char *src2, int src2_role,
+                     char *dst, int dst_role, const int32_t *g, int64_t nelem, int64_t dst0);
+int gbx_split_single_rows(gbx_request_s *req, const int64_t *row_ptr, const int64_t *row_out, const int64_t *terms,
+                          int64_t nrows, int32_t **gs, int32_t **gd, int64_t *nsingle, int64_t **row_ptr2,
+                          int64_t **row_out2, int64_t **terms2, int64_t *nmulti, int64_t *nmterms, int *ok);
+int gbx_make_flat2_op(gbx_request_s *req, int level, const char *src, int src_role, const char *src2, int src2_role,
+                      char *dst, int dst_role, const int32_t *gs, const int32_t *gd, int64_t nelem);
+int gbx_make_flat(gbx_request_s *req, const Seg *segs, int64_t nseg, const int32_t *idx, int64_t nelem,
+                  int32_t **flat_idx, int64_t *dst0, int *ok);
+int gbx_order_by_source(gbx_request_s *req, const Seg *segs, int64_t nseg, const int32_t *idx, int64_t nelem,
+                        int64_t src_bytes, int64_t max_piece, Seg **out, int64_t *out_nseg);
 int gbx_build_fold_records(const int64_t *row_ptr, const int64_t *row_out, const int64_t *terms, int64_t nrows,
                            longlong2 *rec, cudaStream_t st);
 int gbx_make_fold_op(gbx_request_s *req, int level, char *out, int out_role, const char *bufA,

@@ -27,9 +27,35 @@ template <> struct VecT<4> { typedef unsigned int T; };
 template <> struct VecT<2> { typedef unsigned short T; };
 template <> struct VecT<1> { typedef unsigned char T; };
 
+// Cache behaviour of the payload loads and stores (index and descriptor loads always go
+// through L1).  GBX_LD_MODE 0: ld.global.nc; 1: + L1::no_allocate; 2: + L1::no_allocate and
+// an L2 256-byte prefetch.  GBX_ST_MODE 0: st.global; 1: st.global.cs (evict first).
+#ifndef GBX_LD_MODE
+#define GBX_LD_MODE 0
+#endif
+#ifndef GBX_ST_MODE
+#define GBX_ST_MODE 0
+#endif
+
 template <int VEC>
 __device__ __forceinline__ typename VecT<VEC>::T ldv(const char *p) {
+#if GBX_LD_MODE == 0
     return __ldg(reinterpret_cast<const typename VecT<VEC>::T *>(p));
+#else
+    if constexpr (VEC == 16) {
+        uint4 v;
+#if GBX_LD_MODE == 1
+        asm("ld.global.nc.L1::no_allocate.v4.u32 {%0,%1,%2,%3}, [%4];"
+            : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "l"(p));
+#else
+        asm("ld.global.nc.L1::no_allocate.L2::256B.v4.u32 {%0,%1,%2,%3}, [%4];"
+            : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "l"(p));
+#endif
+        return v;
+    } else {
+        return __ldg(reinterpret_cast<const typename VecT<VEC>::T *>(p));
+    }
+#endif
 }
 template <int VEC>
 __device__ __forceinline__ typename VecT<VEC>::T ldv_plain(const char *p) {
@@ -37,6 +63,12 @@ __device__ __forceinline__ typename VecT<VEC>::T ldv_plain(const char *p) {
 }
 template <int VEC>
 __device__ __forceinline__ void stv(char *p, typename VecT<VEC>::T v) {
+#if GBX_ST_MODE == 1
+    if constexpr (VEC == 16) {
+        __stcs(reinterpret_cast<uint4 *>(p), v);
+        return;
+    }
+#endif
     *reinterpret_cast<typename VecT<VEC>::T *>(p) = v;
 }
 
@@ -59,6 +91,81 @@ __device__ __forceinline__ uint32_t unit_of(uint32_t x, int cpe, int sh, uint32_
 }
 
 // ------------------------------------------------------------------------ copy
+// flat form: destinations contiguous from dst_flat0, element e reads source element
+// flat_idx[e]; the index load is the only dependency of the data load
+template <int VEC, int U>
+__device__ __forceinline__ void copy_tile_flat(const CopyDesc *__restrict__ d, int64_t t) {
+    typedef typename VecT<VEC>::T V;
+    constexpr int B = GBX_TILE / U;
+    const int cpe = d->cpe, sh = d->cpe_shift;
+    const uint32_t magic = d->cpe_magic;
+    const int64_t e0 = __ldg(d->tile_e0 + t);
+    const uint32_t r0 = (uint32_t)(t * GBX_TILE - e0 * cpe);
+    const int64_t left = d->nchunks - t * GBX_TILE;
+    const int64_t s = d->elem_size;
+    const int32_t *__restrict__ g = d->flat_idx;
+    int64_t soff[U], doff[U];
+#pragma unroll
+    for (int u = 0; u < U; u++) {
+        const uint32_t x = r0 + (uint32_t)(u * B) + threadIdx.x;
+        const uint32_t el = unit_of(x, cpe, sh, magic);
+        const int64_t j = (int64_t)(x - el * (uint32_t)cpe) * VEC;
+        const int64_t e = e0 + el;
+        const bool ok = (int64_t)(u * B + threadIdx.x) < left;
+        const uint32_t gi = ok ? (uint32_t)__ldg(g + e) : 0u;
+        // bit 31 selects the second source; offsets stay below 2^63 so the bit survives
+        soff[u] = (((int64_t)(gi & ~GBX_FLAT_SRC2)) * s + j) | ((int64_t)(gi >> 31) << 62);
+        doff[u] = d->dst_flat0 + e * s + j;
+    }
+    V val[U];
+#pragma unroll
+    for (int u = 0; u < U; u++)
+        if ((int64_t)(u * B + threadIdx.x) < left) {
+            const char *base = (soff[u] >> 62) ? d->src2 : d->src;
+            val[u] = ldv<VEC>(base + (soff[u] & ((1ll << 62) - 1)));
+        }
+#pragma unroll
+    for (int u = 0; u < U; u++)
+        if ((int64_t)(u * B + threadIdx.x) < left) stv<VEC>(d->dst + doff[u], val[u]);
+}
+
+// two-index flat form: element e reads source element flat_idx[e] (bit 31 = second source)
+// and writes destination element flat_didx[e]
+template <int VEC, int U>
+__device__ __forceinline__ void copy_tile_flat2(const CopyDesc *__restrict__ d, int64_t t) {
+    typedef typename VecT<VEC>::T V;
+    constexpr int B = GBX_TILE / U;
+    const int cpe = d->cpe, sh = d->cpe_shift;
+    const uint32_t magic = d->cpe_magic;
+    const int64_t e0 = __ldg(d->tile_e0 + t);
+    const uint32_t r0 = (uint32_t)(t * GBX_TILE - e0 * cpe);
+    const int64_t left = d->nchunks - t * GBX_TILE;
+    const int64_t s = d->elem_size;
+    int64_t soff[U], doff[U];
+#pragma unroll
+    for (int u = 0; u < U; u++) {
+        const uint32_t x = r0 + (uint32_t)(u * B) + threadIdx.x;
+        const uint32_t el = unit_of(x, cpe, sh, magic);
+        const int64_t j = (int64_t)(x - el * (uint32_t)cpe) * VEC;
+        const int64_t e = e0 + el;
+        const bool ok = (int64_t)(u * B + threadIdx.x) < left;
+        const uint32_t gi = ok ? (uint32_t)__ldg(d->flat_idx + e) : 0u;
+        const int64_t go = ok ? (int64_t)__ldg(d->flat_didx + e) : 0;
+        soff[u] = (((int64_t)(gi & ~GBX_FLAT_SRC2)) * s + j) | ((int64_t)(gi >> 31) << 62);
+        doff[u] = go * s + j;
+    }
+    V val[U];
+#pragma unroll
+    for (int u = 0; u < U; u++)
+        if ((int64_t)(u * B + threadIdx.x) < left) {
+            const char *base = (soff[u] >> 62) ? d->src2 : d->src;
+            val[u] = ldv<VEC>(base + (soff[u] & ((1ll << 62) - 1)));
+        }
+#pragma unroll
+    for (int u = 0; u < U; u++)
+        if ((int64_t)(u * B + threadIdx.x) < left) stv<VEC>(d->dst + doff[u], val[u]);
+}
+
 template <int VEC, int U>
 __device__ __forceinline__ void copy_tile(const CopyDesc *__restrict__ d, int64_t t) {
     typedef typename VecT<VEC>::T V;
@@ -115,9 +222,22 @@ __device__ __forceinline__ void copy_tile(const CopyDesc *__restrict__ d, int64_
 }
 
 // VEC > 0: every op of the launch has that vector width; VEC == 0: mixed widths
-// (batched patterns), dispatched per tile.
+// (batched patterns), dispatched per tile.  FLAT 0: segment form, 1: flat form, 3: two-index
+// flat form, 2: per op.
+// GBX_COPY_OCC (threads per SM the register budget must allow; 0 = no constraint) trades
+// registers for resident warps.
+#ifndef GBX_COPY_OCC
+#define GBX_COPY_OCC 0
+#endif
 template <int VEC, int U>
-__global__ void __launch_bounds__(GBX_TILE / U)
+__device__ __forceinline__ void copy_tile_any(const CopyDesc *__restrict__ d, int64_t t, int flat) {
+    if (flat == 3) copy_tile_flat2<VEC, U>(d, t);
+    else if (flat) copy_tile_flat<VEC, U>(d, t);
+    else copy_tile<VEC, U>(d, t);
+}
+
+template <int VEC, int U, int FLAT>
+__global__ void __launch_bounds__(GBX_TILE / U, GBX_COPY_OCC ? GBX_COPY_OCC / (GBX_TILE / U) : 1)
 gbx_copy_kernel(const CopyDesc *const *__restrict__ ops, const int64_t *__restrict__ prefix,
                 int nops, int64_t total_tiles) {
     for (int64_t t = blockIdx.x; t < total_tiles; t += gridDim.x) {
@@ -125,14 +245,18 @@ gbx_copy_kernel(const CopyDesc *const *__restrict__ ops, const int64_t *__restri
         const CopyDesc *d = ops[op];
         const int64_t lt = t - __ldg(prefix + op);
         if (VEC) {
-            copy_tile<VEC ? VEC : 1, U>(d, lt);
+            if (FLAT == 1) copy_tile_flat<VEC ? VEC : 1, U>(d, lt);
+            else if (FLAT == 3) copy_tile_flat2<VEC ? VEC : 1, U>(d, lt);
+            else if (FLAT == 0) copy_tile<VEC ? VEC : 1, U>(d, lt);
+            else copy_tile_any<VEC ? VEC : 1, U>(d, lt, d->flat);
         } else {
+            const int fl = d->flat;
             switch (d->vec) {
-                case 16: copy_tile<16, U>(d, lt); break;
-                case 8: copy_tile<8, U>(d, lt); break;
-                case 4: copy_tile<4, U>(d, lt); break;
-                case 2: copy_tile<2, U>(d, lt); break;
-                default: copy_tile<1, U>(d, lt); break;
+                case 16: copy_tile_any<16, U>(d, lt, fl); break;
+                case 8: copy_tile_any<8, U>(d, lt, fl); break;
+                case 4: copy_tile_any<4, U>(d, lt, fl); break;
+                case 2: copy_tile_any<2, U>(d, lt, fl); break;
+                default: copy_tile_any<1, U>(d, lt, fl); break;
             }
         }
     }
@@ -234,8 +358,11 @@ __device__ __forceinline__ void fold_tile(const FoldDesc *__restrict__ d, int64_
 
 // CLS 1..5: every op of the launch is (f64,16) (f64,8) (f32,16) (f32,8) (f32,4);
 // CLS 0: mixed (batched patterns), dispatched per tile.
+#ifndef GBX_FOLD_OCC
+#define GBX_FOLD_OCC 0
+#endif
 template <int CLS, int U>
-__global__ void __launch_bounds__(GBX_TILE / U)
+__global__ void __launch_bounds__(GBX_TILE / U, GBX_FOLD_OCC ? GBX_FOLD_OCC / (GBX_TILE / U) : 1)
 gbx_fold_kernel(const FoldDesc *const *__restrict__ ops, const int64_t *__restrict__ prefix,
                 int nops, int64_t total_tiles) {
     for (int64_t t = blockIdx.x; t < total_tiles; t += gridDim.x) {
@@ -270,24 +397,38 @@ int gbx_num_sms(void) {
 typedef void (*CopyFn)(const CopyDesc *const *, const int64_t *, int, int64_t);
 typedef void (*FoldFn)(const FoldDesc *const *, const int64_t *, int, int64_t);
 
-template <int VEC>
+template <int VEC, int FLAT>
 static CopyFn copy_fn_u(int block) {
     switch (block) {
-        case 128: return gbx_copy_kernel<VEC, 8>;
-        case 256: return gbx_copy_kernel<VEC, 4>;
-        case 512: return gbx_copy_kernel<VEC, 2>;
-        default: return gbx_copy_kernel<VEC, 1>;
+        case 128: return gbx_copy_kernel<VEC, 8, FLAT>;
+        case 256: return gbx_copy_kernel<VEC, 4, FLAT>;
+        case 512: return gbx_copy_kernel<VEC, 2, FLAT>;
+        default: return gbx_copy_kernel<VEC, 1, FLAT>;
     }
 }
 
-static CopyFn copy_fn(int vec, int block) {
+template <int VEC>
+static CopyFn copy_fn_v(int block, int flat) {
+    if (flat == 1) return copy_fn_u<VEC, 1>(block);
+    if (flat == 3) return copy_fn_u<VEC, 3>(block);
+    if (flat == 0) return copy_fn_u<VEC, 0>(block);
+    return copy_fn_u<VEC, 2>(block);
+}
+
+// flat: 0 segment form, 1 flat form, 3 two-index flat form, 2 decided per op (mixed launches)
+static CopyFn copy_fn(int vec, int block, int flat) {
     switch (vec) {
-        case 16: return copy_fn_u<16>(block);
-        case 8: return copy_fn_u<8>(block);
-        case 4: return copy_fn_u<4>(block);
-        case 2: return copy_fn_u<2>(block);
-        case 1: return copy_fn_u<1>(block);
-        default: return block == 128 ? gbx_copy_kernel<0, 4> : copy_fn_u<0>(block);  // mixed: U <= 4
+        case 16: return copy_fn_v<16>(block, flat);
+        case 8: return copy_fn_v<8>(block, flat);
+        case 4: return copy_fn_v<4>(block, flat);
+        case 2: return copy_fn_v<2>(block, flat);
+        case 1: return copy_fn_v<1>(block, flat);
+        default:   // mixed widths: U <= 4
+            switch (block) {
+                case 512: return gbx_copy_kernel<0, 2, 2>;
+                case 1024: return gbx_copy_kernel<0, 1, 2>;
+                default: return gbx_copy_kernel<0, 4, 2>;
+            }
     }
 }
 
@@ -321,8 +462,8 @@ static FoldFn fold_fn(int dtype, int vec, int block) {
 // Blocks of the mixed kernels never go below 256 threads (their unroll is capped at 4).
 int gbx_effective_block(int vec_class, int block) { return (vec_class == 0 && block < 256) ? 256 : block; }
 
-int gbx_occupancy(int kind, int dtype, int vec, int block) {
-    const void *f = kind == 0 ? (const void *)copy_fn(vec, block) : (const void *)fold_fn(dtype, vec, block);
+int gbx_occupancy(int kind, int dtype, int vec, int block, int flat) {
+    const void *f = kind == 0 ? (const void *)copy_fn(vec, block, flat) : (const void *)fold_fn(dtype, vec, block);
     int n = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, f, gbx_effective_block(vec, block), 0);
     return n > 0 ? n : 1;
@@ -334,9 +475,9 @@ static int clamp_grid(int grid, int64_t total_tiles) {
 }
 
 cudaError_t gbx_launch_copy(const CopyDesc *const *ops, const int64_t *tile_prefix, int nops, int64_t total_tiles,
-                            int vec, int block, int grid, cudaStream_t st) {
+                            int vec, int flat, int block, int grid, cudaStream_t st) {
     if (total_tiles <= 0) return cudaSuccess;
-    CopyFn f = copy_fn(vec, block);
+    CopyFn f = copy_fn(vec, block, flat);
     f<<<clamp_grid(grid, total_tiles), gbx_effective_block(vec, block), 0, st>>>(ops, tile_prefix, nops, total_tiles);
     return cudaGetLastError();
 }

@@ -474,6 +474,26 @@ __global__ void m3_count_kernel(const uint64_t *key, int64_t n, int nb, int P, i
 
 __global__ void fill_i64_neg_kernel(int64_t *p, int64_t n) { FOR_EACH(i, n) p[i] = -1; }
 
+// Receive-order flat index of the locality form's last level: direct elements read the send
+// buffer (element index of their source), inter-node elements read the receive aggregate
+// (GBX_FLAT_SRC2 | element index in the aggregate buffer).
+__global__ void loc_final_index_kernel(const int64_t *segv0, int64_t nseg, const int *seg_src,
+                                       const int64_t *send_base, const int32_t *srcel, const int64_t *val_pos,
+                                       int64_t V, int64_t s, int64_t U, int32_t *g, int *bad) {
+    FOR_EACH(v, V) {
+        if (val_pos[v] >= 0) {
+            const int64_t el = U + val_pos[v];
+            if (el > 0x7fffffffll) { atomicOr(bad, 1); continue; }
+            g[v] = (int32_t)(GBX_FLAT_SRC2 | (uint32_t)el);
+        } else {
+            const int64_t q = upper_index(segv0, nseg, v);
+            const int64_t so = send_base[seg_src[q]] + (int64_t)srcel[v] * s;
+            if (so % s != 0 || so / s > 0x7fffffffll) { atomicOr(bad, 1); continue; }
+            g[v] = (int32_t)(so / s);
+        }
+    }
+}
+
 // --------------------------------------------------------------- forward driver
 int gbx_setup_forward(gbx_request_s *req, const int64_t *send_base, const int *sendcounts, const int *sdispls,
                       const int64_t *send_slot_ptr, const int *send_idx, const int64_t *recv_base,
@@ -754,9 +774,31 @@ int gbx_setup_forward(gbx_request_s *req, const int64_t *send_base, const int *s
     req->info.msgs_step1 = m1;
     req->info.msgs_step3 = m3;
     if (U > 0) GBX_TRY(req->mem.alloc((void **)&req->agg, (size_t)(2 * U * s)));
-    // level 0: direct copies and the gather into send aggregates; 1: node-pair blocks;
-    // 2: redistribution
-    if (n0 > 0)
+    // When the receive buffer is one contiguous run in receive order, the direct copies and
+    // the redistribution become one receive-order flat op of the last level (each element
+    // reads the send buffer or the receive aggregate); otherwise direct copies run in level 0
+    // and the redistribution in level 2.
+    int combined = 0;
+    int32_t *gfin = nullptr;
+    int64_t dst0 = 0;
+    if (U > 0 && V > 0 && !req->no_combine) {
+        int ok = 0;
+        int32_t *gtmp = nullptr;
+        GBX_TRY(gbx_make_flat(req, req->segs_std, nseg, send_idx ? req->srcel : nullptr, V, &gtmp, &dst0, &ok));
+        if (ok) {
+            int *bad;
+            GBX_TRY(ws.get(&bad, 1));
+            GBX_CUDA_TRY(cudaMemsetAsync(bad, 0, sizeof(int), st));
+            loc_final_index_kernel<<<grid_of(V), SETUP_T, 0, st>>>(segv0, nseg, seg_src, req->send_base_copy,
+                                                                   req->srcel, req->val_pos, V, s, U, gtmp, bad);
+            GBX_CUDA_TRY(cudaGetLastError());
+            int hb = 0;
+            GBX_CUDA_TRY(cudaMemcpyAsync(&hb, bad, sizeof(int), cudaMemcpyDeviceToHost, st));
+            GBX_CUDA_TRY(cudaStreamSynchronize(st));
+            if (!hb) { combined = 1; gfin = gtmp; }
+        }
+    }
+    if (!combined && n0 > 0)
         GBX_TRY(gbx_make_copy_op(req, 0, req->src, ROLE_SRC, req->dst, ROLE_DST, seg0, n0,
                                  send_idx ? req->srcel : nullptr, V, Vd,
                                  2 * Vd * s + Vd * idx_bytes + n0 * (int64_t)sizeof(Seg)));
@@ -765,8 +807,12 @@ int gbx_setup_forward(gbx_request_s *req, const int64_t *send_base, const int *s
                                  2 * U * s + 4 * U));
         GBX_TRY(gbx_make_copy_op(req, 1, req->agg, ROLE_AGG, req->agg, ROLE_AGG, seg2, npairs, nullptr, 0, U,
                                  2 * U * s + npairs * (int64_t)sizeof(Seg)));
-        GBX_TRY(gbx_make_copy_op(req, 2, req->agg, ROLE_AGG, req->dst, ROLE_DST, seg3, n3, idx3, Vx, Vx,
-                                 2 * Vx * s + 4 * Vx + n3 * (int64_t)sizeof(Seg)));
+        if (combined)
+            GBX_TRY(gbx_make_flat_op(req, 2, req->src, ROLE_SRC, req->agg, ROLE_AGG, req->dst, ROLE_DST, gfin, V,
+                                     dst0));
+        else
+            GBX_TRY(gbx_make_copy_op(req, 2, req->agg, ROLE_AGG, req->dst, ROLE_DST, seg3, n3, idx3, Vx, Vx,
+                                     2 * Vx * s + 4 * Vx + n3 * (int64_t)sizeof(Seg)));
     }
     return GBX_SUCCESS;
 }
@@ -1074,6 +1120,11 @@ __global__ void check_fold_kernel(const int64_t *row_ptr, const int64_t *row_out
     }
 }
 
+__global__ void check_flat_kernel(const int32_t *g, int64_t nelem, int64_t s, int64_t dst0, int64_t src_bytes,
+                                  int64_t src2_bytes, int64_t dst_bytes, int *err);
+__global__ void check_flat2_kernel(const int32_t *gs, const int32_t *gd, int64_t n, int64_t s, int64_t src_bytes,
+                                   int64_t src2_bytes, int64_t dst_bytes, int *err);
+
 int gbx_validate_program(gbx_request_s *req, int64_t agg_bytes) {
     cudaStream_t st = req->stream;
     DevPool ws;
@@ -1093,6 +1144,16 @@ int gbx_validate_program(gbx_request_s *req, int64_t agg_bytes) {
             if (d.idx)
                 check_copy_idx_kernel<<<grid_of(d.nelem), SETUP_T, 0, st>>>(d.segs, d.nseg, d.nelem, d.idx,
                                                                             d.elem_size, bytes_of(d.src_role), err);
+            if (op.flat_ok && d.flat == 3)
+                check_flat2_kernel<<<grid_of(d.nelem), SETUP_T, 0, st>>>(d.flat_idx, d.flat_didx, d.nelem, d.elem_size,
+                                                                         bytes_of(d.src_role),
+                                                                         d.src2 ? bytes_of(d.src2_role) : 0,
+                                                                         bytes_of(d.dst_role), err);
+            else if (op.flat_ok)
+                check_flat_kernel<<<grid_of(d.nelem), SETUP_T, 0, st>>>(op.d_flat_idx, d.nelem, d.elem_size,
+                                                                        op.flat_dst0, bytes_of(d.src_role),
+                                                                        d.src2 ? bytes_of(d.src2_role) : 0,
+                                                                        bytes_of(d.dst_role), err);
         } else {
             const FoldDesc &d = op.fd;
             check_fold_kernel<<<grid_of(d.nrows), SETUP_T, 0, st>>>(d.row_ptr, d.row_out, d.rec, d.terms, d.nrows,
@@ -1132,4 +1193,329 @@ int gbx_build_fold_records(const int64_t *row_ptr, const int64_t *row_out, const
     fold_rec_kernel<<<grid_of(nrows), SETUP_T, 0, st>>>(row_ptr, row_out, terms, nrows, rec, err);
     GBX_CUDA_TRY(cudaGetLastError());
     return read_err_stage(err, st);
+}
+
+// ------------------------------------------------------------ run splitting
+// Re-cuts the segments of a gathering copy op so that every run of >= min_run elements
+// whose source indices are consecutive becomes a contiguous segment (its elements need
+// no index load, so the data load no longer waits for one), while stretches of shorter
+// runs stay index-gathered.  The element numbering, the destinations and the bytes moved
+// are unchanged.
+__device__ __forceinline__ int64_t seg_of(const Seg *segs, int64_t nseg, int64_t v) {
+    int64_t lo = 0, hi = nseg - 1;
+    while (lo < hi) {
+        int64_t mid = (lo + hi + 1) >> 1;
+        if (segs[mid].v0 <= v) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+__global__ void run_start_kernel(const Seg *segs, int64_t nseg, const int32_t *idx, int64_t nelem, int64_t *rs) {
+    FOR_EACH(v, nelem) {
+        const int64_t q = seg_of(segs, nseg, v);
+        const Seg sg = segs[q];
+        const int64_t k = v - sg.v0;
+        rs[v] = (k == 0) || (sg.idx_off >= 0 && idx[sg.idx_off + k] != idx[sg.idx_off + k - 1] + 1);
+    }
+}
+
+// run r begins at element begin[r]; a run is long if it has >= min_run elements or lies in
+// a segment that was already contiguous
+__global__ void run_begin_kernel(const int64_t *rs, const int64_t *rid, int64_t nelem, int64_t *begin) {
+    FOR_EACH(v, nelem) if (rs[v]) begin[rid[v]] = v;
+}
+
+__global__ void run_long_kernel(const Seg *segs, int64_t nseg, const int64_t *begin, int64_t nruns, int64_t nelem,
+                                int min_run, int64_t *is_long) {
+    FOR_EACH(r, nruns) {
+        const int64_t end = r + 1 < nruns ? begin[r + 1] : nelem;
+        const Seg sg = segs[seg_of(segs, nseg, begin[r])];
+        is_long[r] = sg.idx_off < 0 || end - begin[r] >= min_run;
+    }
+}
+
+__global__ void new_seg_flag_kernel(const Seg *segs, int64_t nseg, const int64_t *rs, const int64_t *rid,
+                                    const int64_t *is_long, int64_t nelem, int64_t *ns) {
+    FOR_EACH(v, nelem) {
+        const int64_t q = seg_of(segs, nseg, v);
+        const int64_t run = rid[v] + rs[v] - 1;
+        ns[v] = (v == segs[q].v0) || (rs[v] && (is_long[run] || is_long[run - 1]));
+    }
+}
+
+__global__ void new_seg_kernel(const Seg *segs, int64_t nseg, const int32_t *idx, const int64_t *rs, const int64_t *rid,
+                               const int64_t *is_long, const int64_t *ns, const int64_t *nsid, int64_t nelem, int64_t s,
+                               Seg *out) {
+    FOR_EACH(v, nelem) {
+        if (!ns[v]) continue;
+        const Seg sg = segs[seg_of(segs, nseg, v)];
+        const int64_t k = v - sg.v0;
+        const int64_t run = rid[v] + rs[v] - 1;
+        Seg t;
+        t.v0 = v;
+        t.dst_off = sg.dst_off + k * s;
+        if (sg.idx_off < 0) {
+            t.src_off = sg.src_off + k * s;
+            t.idx_off = -1;
+        } else if (is_long[run]) {
+            t.src_off = sg.src_off + (int64_t)idx[sg.idx_off + k] * s;
+            t.idx_off = -1;
+        } else {
+            t.src_off = sg.src_off;
+            t.idx_off = sg.idx_off + k;
+        }
+        out[nsid[v]] = t;
+    }
+}
+
+int gbx_split_runs(gbx_request_s *req, const Seg *segs, int64_t nseg, const int32_t *idx, int64_t nelem,
+                   int min_run, Seg **out, int64_t *out_nseg) {
+    cudaStream_t st = req->stream;
+    DevPool ws;
+    int64_t *rs, *rid, *begin, *is_long, *ns, *nsid;
+    GBX_TRY(ws.get(&rs, nelem)); GBX_TRY(ws.get(&rid, nelem + 1));
+    run_start_kernel<<<grid_of(nelem), SETUP_T, 0, st>>>(segs, nseg, idx, nelem, rs);
+    GBX_CUDA_TRY(cudaGetLastError());
+    GBX_TRY(gbx_scan_i64(rs, rid, nelem, st, ws));
+    int64_t nruns = 0;
+    GBX_TRY(gbx_read_i64(rid + nelem, &nruns, st));
+    GBX_TRY(ws.get(&begin, nruns)); GBX_TRY(ws.get(&is_long, nruns));
+    run_begin_kernel<<<grid_of(nelem), SETUP_T, 0, st>>>(rs, rid, nelem, begin);
+    run_long_kernel<<<grid_of(nruns), SETUP_T, 0, st>>>(segs, nseg, begin, nruns, nelem, min_run, is_long);
+    GBX_TRY(ws.get(&ns, nelem)); GBX_TRY(ws.get(&nsid, nelem + 1));
+    new_seg_flag_kernel<<<grid_of(nelem), SETUP_T, 0, st>>>(segs, nseg, rs, rid, is_long, nelem, ns);
+    GBX_CUDA_TRY(cudaGetLastError());
+    GBX_TRY(gbx_scan_i64(ns, nsid, nelem, st, ws));
+    int64_t n = 0;
+    GBX_TRY(gbx_read_i64(nsid + nelem, &n, st));
+    Seg *o;
+    GBX_TRY(req->mem.get(&o, n));
+    new_seg_kernel<<<grid_of(nelem), SETUP_T, 0, st>>>(segs, nseg, idx, rs, rid, is_long, ns, nsid, nelem,
+                                                       req->elem_size, o);
+    GBX_CUDA_TRY(cudaGetLastError());
+    GBX_CUDA_TRY(cudaStreamSynchronize(st));
+    *out = o;
+    *out_nseg = n;
+    return GBX_SUCCESS;
+}
+
+// ------------------------------------------------------- source-ordered pieces
+// Cuts every segment into pieces of at most max_piece elements and renumbers the op's
+// element space so that pieces come in ascending source address.  Reads that are close in
+// memory (for a stencil, the two x faces of a rank, 1984 bytes apart) are then issued
+// together, while every piece still writes one contiguous run.  Same elements, same bytes.
+__global__ void piece_count_kernel(const Seg *segs, int64_t nseg, int64_t nelem, int64_t max_piece, int64_t *np) {
+    FOR_EACH(q, nseg) {
+        const int64_t c = (q + 1 < nseg ? segs[q + 1].v0 : nelem) - segs[q].v0;
+        np[q] = (c + max_piece - 1) / max_piece;
+    }
+}
+
+__global__ void piece_make_kernel(const Seg *segs, int64_t nseg, int64_t nelem, int64_t max_piece, const int64_t *pstart,
+                                  const int32_t *idx, int64_t s, Seg *pieces, int64_t *len, uint64_t *key, int64_t *pid) {
+    FOR_EACH(q, nseg) {
+        const Seg sg = segs[q];
+        const int64_t c = (q + 1 < nseg ? segs[q + 1].v0 : nelem) - sg.v0;
+        for (int64_t j = 0; j * max_piece < c; j++) {
+            const int64_t p = pstart[q] + j, k = j * max_piece;
+            Seg t;
+            t.v0 = 0;
+            t.dst_off = sg.dst_off + k * s;
+            if (sg.idx_off < 0) { t.src_off = sg.src_off + k * s; t.idx_off = -1; }
+            else { t.src_off = sg.src_off; t.idx_off = sg.idx_off + k; }
+            pieces[p] = t;
+            len[p] = c - k < max_piece ? c - k : max_piece;
+            key[p] = (uint64_t)(t.idx_off < 0 ? t.src_off : t.src_off + (int64_t)idx[t.idx_off] * s);
+            pid[p] = p;
+        }
+    }
+}
+
+__global__ void piece_gather_len_kernel(const int64_t *len, const int64_t *order, int64_t n, int64_t *olen) {
+    FOR_EACH(m, n) olen[m] = len[order[m]];
+}
+
+__global__ void piece_place_kernel(const Seg *pieces, const int64_t *order, const int64_t *v0, int64_t n, Seg *out) {
+    FOR_EACH(m, n) {
+        Seg t = pieces[order[m]];
+        t.v0 = v0[m];
+        out[m] = t;
+    }
+}
+
+int gbx_order_by_source(gbx_request_s *req, const Seg *segs, int64_t nseg, const int32_t *idx, int64_t nelem,
+                        int64_t src_bytes, int64_t max_piece, Seg **out, int64_t *out_nseg) {
+    cudaStream_t st = req->stream;
+    DevPool ws;
+    int64_t *np, *pstart;
+    GBX_TRY(ws.get(&np, nseg)); GBX_TRY(ws.get(&pstart, nseg + 1));
+    piece_count_kernel<<<grid_of(nseg), SETUP_T, 0, st>>>(segs, nseg, nelem, max_piece, np);
+    GBX_CUDA_TRY(cudaGetLastError());
+    GBX_TRY(gbx_scan_i64(np, pstart, nseg, st, ws));
+    int64_t n = 0;
+    GBX_TRY(gbx_read_i64(pstart + nseg, &n, st));
+    Seg *pieces, *o;
+    int64_t *len, *pid, *pida, *olen, *v0;
+    uint64_t *key, *keya;
+    GBX_TRY(ws.get(&pieces, n)); GBX_TRY(ws.get(&len, n)); GBX_TRY(ws.get(&olen, n)); GBX_TRY(ws.get(&v0, n + 1));
+    GBX_TRY(ws.get(&key, n)); GBX_TRY(ws.get(&keya, n)); GBX_TRY(ws.get(&pid, n)); GBX_TRY(ws.get(&pida, n));
+    piece_make_kernel<<<grid_of(nseg), SETUP_T, 0, st>>>(segs, nseg, nelem, max_piece, pstart, idx, req->elem_size,
+                                                         pieces, len, key, pid);
+    GBX_CUDA_TRY(cudaGetLastError());
+    GBX_TRY(gbx_sort_pairs(&key, &pid, keya, pida, n, std::max(1, bitlen_u64((uint64_t)src_bytes)), st, ws));
+    piece_gather_len_kernel<<<grid_of(n), SETUP_T, 0, st>>>(len, pid, n, olen);
+    GBX_CUDA_TRY(cudaGetLastError());
+    GBX_TRY(gbx_scan_i64(olen, v0, n, st, ws));
+    GBX_TRY(req->mem.get(&o, n));
+    piece_place_kernel<<<grid_of(n), SETUP_T, 0, st>>>(pieces, pid, v0, n, o);
+    GBX_CUDA_TRY(cudaGetLastError());
+    GBX_CUDA_TRY(cudaStreamSynchronize(st));
+    *out = o;
+    *out_nseg = n;
+    return GBX_SUCCESS;
+}
+
+// ------------------------------------------------------------------ flat form
+// A copy op whose destinations form one contiguous run (every segment starts where the
+// previous one ended) and whose source offsets are all multiples of the element size can
+// run as a plain indexed gather, dst[e] = src[g[e]], with no segment search.
+__global__ void flat_dst_kernel(const Seg *segs, int64_t nseg, int64_t s, int *bad) {
+    FOR_EACH(q, nseg) if (segs[q].dst_off != segs[0].dst_off + segs[q].v0 * s) atomicOr(bad, 1);
+}
+
+__global__ void flat_build_kernel(const Seg *segs, int64_t nseg, const int32_t *idx, int64_t nelem, int64_t s,
+                                  int32_t *g, int *bad) {
+    FOR_EACH(v, nelem) {
+        const Seg sg = segs[seg_of(segs, nseg, v)];
+        const int64_t k = v - sg.v0;
+        const int64_t so = sg.src_off + (sg.idx_off >= 0 ? (int64_t)idx[sg.idx_off + k] : k) * s;
+        if (so % s != 0 || so / s > 0x7fffffffll) { atomicOr(bad, 1); continue; }
+        g[v] = (int32_t)(so / s);
+    }
+}
+
+int gbx_make_flat(gbx_request_s *req, const Seg *segs, int64_t nseg, const int32_t *idx, int64_t nelem,
+                  int32_t **flat_idx, int64_t *dst0, int *ok) {
+    cudaStream_t st = req->stream;
+    *ok = 0;
+    DevPool ws;
+    int *bad;
+    GBX_TRY(ws.get(&bad, 1));
+    GBX_CUDA_TRY(cudaMemsetAsync(bad, 0, sizeof(int), st));
+    flat_dst_kernel<<<grid_of(nseg), SETUP_T, 0, st>>>(segs, nseg, req->elem_size, bad);
+    GBX_CUDA_TRY(cudaGetLastError());
+    int hb = 0;
+    GBX_CUDA_TRY(cudaMemcpyAsync(&hb, bad, sizeof(int), cudaMemcpyDeviceToHost, st));
+    GBX_CUDA_TRY(cudaStreamSynchronize(st));
+    if (hb) return GBX_SUCCESS;
+    int32_t *g;
+    GBX_TRY(req->mem.get(&g, nelem));
+    flat_build_kernel<<<grid_of(nelem), SETUP_T, 0, st>>>(segs, nseg, idx, nelem, req->elem_size, g, bad);
+    GBX_CUDA_TRY(cudaGetLastError());
+    Seg first;
+    GBX_CUDA_TRY(cudaMemcpyAsync(&first, segs, sizeof(Seg), cudaMemcpyDeviceToHost, st));
+    GBX_CUDA_TRY(cudaMemcpyAsync(&hb, bad, sizeof(int), cudaMemcpyDeviceToHost, st));
+    GBX_CUDA_TRY(cudaStreamSynchronize(st));
+    if (hb) return GBX_SUCCESS;   // g stays allocated with the request; the flat form is unused
+    *flat_idx = g;
+    *dst0 = first.dst_off;
+    *ok = 1;
+    return GBX_SUCCESS;
+}
+
+__global__ void check_flat_kernel(const int32_t *g, int64_t nelem, int64_t s, int64_t dst0, int64_t src_bytes,
+                                  int64_t src2_bytes, int64_t dst_bytes, int *err) {
+    FOR_EACH(v, nelem) {
+        const uint32_t x = (uint32_t)g[v];
+        const int64_t el = (int64_t)(x & ~GBX_FLAT_SRC2);
+        const int64_t lim = (x & GBX_FLAT_SRC2) ? src2_bytes : src_bytes;
+        if ((el + 1) * s > lim || dst0 < 0 || dst0 + (v + 1) * s > dst_bytes) set_err(err, GBX_ERR_INTERNAL);
+    }
+}
+
+// ------------------------------------------------ single-term rows of a fold
+// When a fold does not accumulate, a row with one term is a copy out[row] = term: those rows
+// become a two-index flat copy and only rows with several terms stay in the fold.  Needs
+// every offset to be a multiple of the element size below 2^31 elements (else ok = 0).
+__global__ void row_kind_kernel(const int64_t *row_ptr, int64_t nrows, int64_t *single, int64_t *multi,
+                                int64_t *mcnt) {
+    FOR_EACH(r, nrows) {
+        const int64_t c = row_ptr[r + 1] - row_ptr[r];
+        single[r] = c == 1;
+        multi[r] = c > 1;
+        mcnt[r] = c > 1 ? c : 0;
+    }
+}
+
+__global__ void row_split_kernel(const int64_t *row_ptr, const int64_t *row_out, const int64_t *terms, int64_t nrows,
+                                 int64_t s, const int64_t *sidx, const int64_t *mrow, const int64_t *mterm,
+                                 int32_t *gs, int32_t *gd, int64_t *row_ptr2, int64_t *row_out2, int64_t *terms2,
+                                 int *bad) {
+    FOR_EACH(r, nrows) {
+        const int64_t b = row_ptr[r], c = row_ptr[r + 1] - b;
+        if (c == 1) {
+            const uint64_t w = (uint64_t)terms[b];
+            const int64_t off = (int64_t)(w & GBX_TERM_MASK);
+            if (off % s || row_out[r] % s || off / s > 0x7fffffffll || row_out[r] / s > 0x7fffffffll) {
+                atomicOr(bad, 1);
+                continue;
+            }
+            gs[sidx[r]] = (int32_t)(((w & GBX_TERM_BUFB) ? GBX_FLAT_SRC2 : 0u) | (uint32_t)(off / s));
+            gd[sidx[r]] = (int32_t)(row_out[r] / s);
+        } else {
+            const int64_t m = mrow[r], t0 = mterm[r];
+            row_ptr2[m] = t0;
+            row_out2[m] = row_out[r];
+            for (int64_t k = 0; k < c; k++) terms2[t0 + k] = terms[b + k];
+        }
+    }
+}
+
+int gbx_split_single_rows(gbx_request_s *req, const int64_t *row_ptr, const int64_t *row_out, const int64_t *terms,
+                          int64_t nrows, int32_t **gs, int32_t **gd, int64_t *nsingle, int64_t **row_ptr2,
+                          int64_t **row_out2, int64_t **terms2, int64_t *nmulti, int64_t *nmterms, int *ok) {
+    cudaStream_t st = req->stream;
+    *ok = 0;
+    DevPool ws;
+    int64_t *single, *multi, *mcnt, *sidx, *mrow, *mterm;
+    int *bad;
+    GBX_TRY(ws.get(&single, nrows)); GBX_TRY(ws.get(&multi, nrows)); GBX_TRY(ws.get(&mcnt, nrows));
+    GBX_TRY(ws.get(&sidx, nrows + 1)); GBX_TRY(ws.get(&mrow, nrows + 1)); GBX_TRY(ws.get(&mterm, nrows + 1));
+    GBX_TRY(ws.get(&bad, 1));
+    GBX_CUDA_TRY(cudaMemsetAsync(bad, 0, sizeof(int), st));
+    row_kind_kernel<<<grid_of(nrows), SETUP_T, 0, st>>>(row_ptr, nrows, single, multi, mcnt);
+    GBX_CUDA_TRY(cudaGetLastError());
+    GBX_TRY(gbx_scan_i64(single, sidx, nrows, st, ws));
+    GBX_TRY(gbx_scan_i64(multi, mrow, nrows, st, ws));
+    GBX_TRY(gbx_scan_i64(mcnt, mterm, nrows, st, ws));
+    int64_t ns = 0, nm = 0, nt = 0;
+    GBX_TRY(gbx_read_i64(sidx + nrows, &ns, st));
+    GBX_TRY(gbx_read_i64(mrow + nrows, &nm, st));
+    GBX_TRY(gbx_read_i64(mterm + nrows, &nt, st));
+    if (ns == 0) return GBX_SUCCESS;
+    GBX_TRY(req->mem.get(gs, ns)); GBX_TRY(req->mem.get(gd, ns));
+    GBX_TRY(req->mem.get(row_ptr2, nm + 1)); GBX_TRY(req->mem.get(row_out2, nm)); GBX_TRY(req->mem.get(terms2, nt));
+    row_split_kernel<<<grid_of(nrows), SETUP_T, 0, st>>>(row_ptr, row_out, terms, nrows, req->elem_size, sidx, mrow,
+                                                         mterm, *gs, *gd, *row_ptr2, *row_out2, *terms2, bad);
+    GBX_CUDA_TRY(cudaGetLastError());
+    GBX_CUDA_TRY(cudaMemcpyAsync(*row_ptr2 + nm, &nt, sizeof(int64_t), cudaMemcpyHostToDevice, st));
+    int hb = 0;
+    GBX_CUDA_TRY(cudaMemcpyAsync(&hb, bad, sizeof(int), cudaMemcpyDeviceToHost, st));
+    GBX_CUDA_TRY(cudaStreamSynchronize(st));
+    if (hb) return GBX_SUCCESS;
+    *nsingle = ns;
+    *nmulti = nm;
+    *nmterms = nt;
+    *ok = 1;
+    return GBX_SUCCESS;
+}
+
+__global__ void check_flat2_kernel(const int32_t *gs, const int32_t *gd, int64_t n, int64_t s, int64_t src_bytes,
+                                   int64_t src2_bytes, int64_t dst_bytes, int *err) {
+    FOR_EACH(v, n) {
+        const uint32_t x = (uint32_t)gs[v];
+        const int64_t el = (int64_t)(x & ~GBX_FLAT_SRC2);
+        const int64_t lim = (x & GBX_FLAT_SRC2) ? src2_bytes : src_bytes;
+        if ((el + 1) * s > lim || gd[v] < 0 || ((int64_t)gd[v] + 1) * s > dst_bytes) set_err(err, GBX_ERR_INTERNAL);
+    }
 }

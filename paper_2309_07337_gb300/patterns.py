@@ -133,11 +133,12 @@ def _assemble(name, P, ppn, out_src, out_dst, out_cnt, send_elem, send_gidx,
 
 # ------------------------------------------------------------------ stencils ---
 
-def stencil(grid, ranks, ppn, comps=1, dtype="f64", neighbors="all", name=None) -> Pattern:
+def stencil(grid, ranks, ppn, comps=1, dtype="f64", neighbors="all", name=None, directions=None) -> Pattern:
     """Halo exchange of a structured grid split into equal rank blocks (no periodicity).
 
     grid, ranks: per-axis point and rank counts (x first), 2 or 3 axes.
     neighbors: 'faces' (5-point in 2D, 7-point in 3D) or 'all' (9- / 27-point).
+    directions: optional subset of neighbour offsets (x first) to keep.
     Each point carries `comps` values stored together (one element of comps*8 or
     comps*4 bytes).  The send list towards direction delta is the boundary layer facing
     it (coordinate 0 where delta=-1, n-1 where delta=+1, all where delta=0), in
@@ -158,7 +159,8 @@ def stencil(grid, ranks, ppn, comps=1, dtype="f64", neighbors="all", name=None) 
     for d in itertools.product((-1, 0, 1), repeat=D):
         dd = tuple(reversed(d))  # dd[0] = dx
         if any(dd) and (neighbors == "all" or sum(map(abs, dd)) == 1):
-            dirs.append(dd)
+            if directions is None or dd in [tuple(x) for x in directions]:
+                dirs.append(dd)
 
     # local coordinates of each local point (x fastest)
     loc = np.indices(tuple(reversed(blk))).reshape(D, -1)[::-1]  # loc[axis][point]

@@ -141,7 +141,9 @@ def test_shapes_and_graph_modes_identical():
     p = pt.config5(edge=4, comps=3)
     x = payload(p, 3)
     want = oracle.standard(p, x)
-    for info in ("graph=0", "autotune=0", "vec=8;block=128", "vec=4;block=1024", "vec=8;block=512;graph=0"):
+    for info in ("graph=0", "autotune=0", "vec=8;block=128", "vec=4;block=1024", "vec=8;block=512;graph=0",
+                 "min_run=0", "min_run=1;vec=8", "min_run=2;block=256", "piece=32", "piece=7;min_run=0",
+                 "piece=1;vec=4", "flat=1", "flat=0", "flat=1;block=128;min_run=0"):
         for alg in ("standard", "locality"):
             got, _ = forward(p, x, alg, info=info)
             assert_bytes_equal(got, want, f"{info} {alg}")
@@ -272,3 +274,39 @@ def test_error_codes_match_oracle(case):
     with pytest.raises(gbx.GbxError) as e:
         forward(g, sb, "standard")
     assert e.value.code == want
+
+
+@pytest.mark.parametrize("info", ["", "single_split=0", "flat=0", "vec=8;block=128", "single_split=0;block=1024"])
+def test_backward_modes_identical(info):
+    """Every backward program shape (single-term rows split out or folded, flat or segment
+    copies, any launch shape) gives the oracle's bytes."""
+    for p in (pt.config5(edge=4, comps=2), pt.random_pattern(321, dtype="f32"), pt.config4(n=4096, P=64)):
+        x = payload(p, 1)
+        g = grad_payload(p, 2)
+        old = payload(p, 3)
+        for alg, form in (("standard", 0), ("locality", 1)):
+            _, ex = forward(p, x, alg, info=info)
+            got, _ = backward(ex, g, info=info)
+            assert_bytes_equal(got, oracle.backward(p, g, form=form), f"{p.name} {alg} {info}")
+            got, _ = backward(ex, g, old, accumulate=True, info=info)
+            assert_bytes_equal(got, oracle.backward(p, g, old, form=form, accumulate=True),
+                               f"{p.name} {alg} {info} acc")
+
+
+def test_accumulating_backward_init_leaves_gradient_untouched():
+    """Init of an accumulating backward must not launch into the caller's gradient buffer
+    (the autotuner never trial-runs it); the first start adds exactly once."""
+    p = pt.config5(edge=4, comps=2)
+    x = payload(p, 1)
+    g = grad_payload(p, 2)
+    old = payload(p, 3)
+    for alg, form in (("standard", 0), ("locality", 1)):
+        _, ex = forward(p, x, alg)
+        gr = dev_bytes(g)
+        gs = dev_bytes(old.copy())
+        b = gbx.backward_init(ex.request, gr, gs, accumulate=True)
+        torch.cuda.synchronize()
+        assert_bytes_equal(gs.cpu().numpy(), old, f"{alg}: init changed the gradient buffer")
+        b.start()
+        b.wait()
+        assert_bytes_equal(gs.cpu().numpy(), oracle.backward(p, g, old, form=form, accumulate=True), alg)
