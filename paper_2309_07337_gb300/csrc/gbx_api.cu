@@ -49,7 +49,7 @@ struct Opts {
     int algorithm = GBX_ALG_STANDARD;
     int algorithm_auto = 0;
     int graph = 1, autotune = 1, vec = 0, block = 0, timeout_ms = 60000, min_run = 4, piece = 0, flat = -1;
-    int split = 1;
+    int split = 1, split_order = 0;
     bool ok = true;
 };
 
@@ -81,11 +81,12 @@ static Opts parse_info(const char *info) {
         else if (k == "piece") o.piece = atoi(v.c_str());
         else if (k == "flat") o.flat = atoi(v.c_str()) != 0;
         else if (k == "single_split") o.split = atoi(v.c_str()) != 0;
+        else if (k == "split_order") o.split_order = v == "source" ? 1 : v == "dest" ? 0 : -1;
         else o.ok = false;
     }
     if (o.vec && !(o.vec == 1 || o.vec == 2 || o.vec == 4 || o.vec == 8 || o.vec == 16)) o.ok = false;
     if (o.block && !(o.block == 128 || o.block == 256 || o.block == 512 || o.block == 1024)) o.ok = false;
-    if (o.timeout_ms <= 0 || o.min_run < 0 || o.piece < 0) o.ok = false;
+    if (o.timeout_ms <= 0 || o.min_run < 0 || o.piece < 0 || o.split_order < 0) o.ok = false;
     return o;
 }
 
@@ -259,6 +260,7 @@ int gbx_make_fold_op(gbx_request_s *req, int level, char *out, int out_role, con
         GBX_TRY(gbx_split_single_rows(req, row_ptr, row_out, terms, nrows, &gs, &gd, &ns, &rp2, &ro2, &t2, &nm, &nt,
                                       &ok));
         if (ok) {
+            if (req->split_order == 1) GBX_TRY(gbx_sort_pairs_by_source(req, gs, gd, ns));
             GBX_TRY(gbx_make_flat2_op(req, level, bufA, a_role, bufB, b_role, out, out_role, gs, gd, ns));
             if (nm == 0) return GBX_SUCCESS;
             row_ptr = rp2;
@@ -644,6 +646,7 @@ static gbx_request_s *new_request(const Opts &o, void *stream) {
     req->allow_flat = o.flat != 0;
     req->no_combine = o.flat == 0;
     req->no_single_split = !o.split;
+    req->split_order = o.split_order;
     if (cudaEventCreateWithFlags(&req->done, cudaEventDisableTiming) != cudaSuccess) {
         cudaGetLastError();
         req->done = nullptr;

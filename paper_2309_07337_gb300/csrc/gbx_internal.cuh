@@ -218,6 +218,7 @@ struct gbx_request_s {
     int allow_flat;
     int no_combine;          // locality form: keep direct copies and redistribution apart
     int no_single_split;     // keep single-term fold rows in the fold
+    int split_order;         // single-term rows as copies: 0 in row (destination) order, 1 in source order
     int timeout_ms;
     gbx_graph_s *graph;
     gbx_request_s *forward;  // backward: its forward request
@@ -275,6 +276,7 @@ int gbx_make_flat_op(gbx_request_s *req, int level, const char *src, int src_rol
 int gbx_split_single_rows(gbx_request_s *req, const int64_t *row_ptr, const int64_t *row_out, const int64_t *terms,
                           int64_t nrows, int32_t **gs, int32_t **gd, int64_t *nsingle, int64_t **row_ptr2,
                           int64_t **row_out2, int64_t **terms2, int64_t *nmulti, int64_t *nmterms, int *ok);
+int gbx_sort_pairs_by_source(gbx_request_s *req, int32_t *gs, int32_t *gd, int64_t n);
 int gbx_make_flat2_op(gbx_request_s *req, int level, const char *src, int src_role, const char *src2, int src2_role,
                       char *dst, int dst_role, const int32_t *gs, const int32_t *gd, int64_t nelem);
 int gbx_make_flat(gbx_request_s *req, const Seg *segs, int64_t nseg, const int32_t *idx, int64_t nelem,

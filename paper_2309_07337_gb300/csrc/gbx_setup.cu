@@ -1519,3 +1519,33 @@ __global__ void check_flat2_kernel(const int32_t *gs, const int32_t *gd, int64_t
         if ((el + 1) * s > lim || gd[v] < 0 || ((int64_t)gd[v] + 1) * s > dst_bytes) set_err(err, GBX_ERR_INTERNAL);
     }
 }
+
+// Reorders a two-index copy by its source index (ascending read addresses; bit 31, the
+// second buffer, sorts after the first).  Same pairs, same bytes.
+__global__ void pair_to_sort_kernel(const int32_t *gs, const int32_t *gd, int64_t n, uint64_t *k, int64_t *v) {
+    FOR_EACH(i, n) {
+        k[i] = (uint64_t)(uint32_t)gs[i];
+        v[i] = gd[i];
+    }
+}
+__global__ void pair_from_sort_kernel(const uint64_t *k, const int64_t *v, int64_t n, int32_t *gs, int32_t *gd) {
+    FOR_EACH(i, n) {
+        gs[i] = (int32_t)(uint32_t)k[i];
+        gd[i] = (int32_t)v[i];
+    }
+}
+
+int gbx_sort_pairs_by_source(gbx_request_s *req, int32_t *gs, int32_t *gd, int64_t n) {
+    cudaStream_t st = req->stream;
+    DevPool ws;
+    uint64_t *k, *ka;
+    int64_t *v, *va;
+    GBX_TRY(ws.get(&k, n)); GBX_TRY(ws.get(&ka, n)); GBX_TRY(ws.get(&v, n)); GBX_TRY(ws.get(&va, n));
+    pair_to_sort_kernel<<<grid_of(n), SETUP_T, 0, st>>>(gs, gd, n, k, v);
+    GBX_CUDA_TRY(cudaGetLastError());
+    GBX_TRY(gbx_sort_pairs(&k, &v, ka, va, n, 32, st, ws));
+    pair_from_sort_kernel<<<grid_of(n), SETUP_T, 0, st>>>(k, v, n, gs, gd);
+    GBX_CUDA_TRY(cudaGetLastError());
+    GBX_CUDA_TRY(cudaStreamSynchronize(st));
+    return GBX_SUCCESS;
+}
