@@ -198,6 +198,49 @@ int gbx_neighbor_alltoallv_init(const void *sendbuf, int64_t sendbuf_bytes,
                                 gbx_graph_t graph, const char *info, void *stream,
                                 gbx_request_t *request);
 
+/* The other neighbourhood collectives, persistent, on the same engine (MPI Advance offers
+ * its persistent neighbourhood collectives as drop-in replacements of the MPI calls,
+ * section 2.2; their meaning is the MPI standard's).  Each derives per-edge counts and
+ * displacements on the device from the graph, then behaves as gbx_neighbor_alltoallv_init
+ * with user-packed buffers and no global indices (so the standard form runs; the other info
+ * keys apply as there).  `count` / `sendcount` are in elements.
+ *   neighbor_alltoall:   rank r sends `count` elements to its j-th out-neighbour from element
+ *                        j*count of its send region; rank d receives `count` elements from its
+ *                        i-th in-neighbour at element i*count of its receive region.
+ *   neighbor_allgather:  rank r sends its elements [0, count) to every out-neighbour; rank d
+ *                        receives them from in-neighbour i at element i*count.
+ *   neighbor_allgatherv: rank r sends its elements [0, sendcount[r]) to every out-neighbour
+ *                        (sendcount: device int[P]); rank d receives recvcounts[i] elements from
+ *                        in-neighbour i at element rdispls[i] (recvcounts must equal the
+ *                        sender's count, else GBX_ERR_TRUNCATE).
+ * Errors as gbx_neighbor_alltoallv_init, plus GBX_ERR_UNSUPPORTED when a derived displacement
+ * exceeds the int32 range. */
+int gbx_neighbor_alltoall_init(const void *sendbuf, int64_t sendbuf_bytes, const int64_t *send_base,
+                               void *recvbuf, int64_t recvbuf_bytes, const int64_t *recv_base,
+                               int count, int64_t elem_size, int dtype, gbx_graph_t graph,
+                               const char *info, void *stream, gbx_request_t *request);
+int gbx_neighbor_allgather_init(const void *sendbuf, int64_t sendbuf_bytes, const int64_t *send_base,
+                                void *recvbuf, int64_t recvbuf_bytes, const int64_t *recv_base,
+                                int count, int64_t elem_size, int dtype, gbx_graph_t graph,
+                                const char *info, void *stream, gbx_request_t *request);
+int gbx_neighbor_allgatherv_init(const void *sendbuf, int64_t sendbuf_bytes, const int64_t *send_base,
+                                 const int *sendcount, void *recvbuf, int64_t recvbuf_bytes,
+                                 const int64_t *recv_base, const int *recvcounts, const int *rdispls,
+                                 int64_t elem_size, int dtype, gbx_graph_t graph,
+                                 const char *info, void *stream, gbx_request_t *request);
+
+/* Persistent all-to-all-v over the emulated communicator (MPIX_Alltoallv, section 2.1,
+ * Listing 2): rank r sends sendcounts[r*P + d] elements from element sdispls[r*P + d] of its
+ * send region to rank d, which stores them at element rdispls[d*P + r] of its receive region
+ * (recvcounts[d*P + r] must match).  All four arrays are device int[P*P], row-major by rank.
+ * The library builds the complete graph (every rank, itself included, in rank order) and
+ * frees it with the request.  Other arguments as gbx_neighbor_alltoallv_init. */
+int gbx_alltoallv_init(gbx_comm_t comm, const void *sendbuf, int64_t sendbuf_bytes,
+                       const int64_t *send_base, const int *sendcounts, const int *sdispls,
+                       void *recvbuf, int64_t recvbuf_bytes, const int64_t *recv_base,
+                       const int *recvcounts, const int *rdispls, int64_t elem_size, int dtype,
+                       const char *info, void *stream, gbx_request_t *request);
+
 /* Reverse exchange of a forward request: the transpose of its 0/1 map (the exchange is
  * linear), so that a halo exchange can be differentiated.  grad_recv has the forward
  * receive buffer's layout, grad_send the forward send buffer's.  Every source element

@@ -63,6 +63,14 @@ def lib():
                                         _vp, _vp, _i64, ctypes.c_int, _vp, _vp, _vp,
                                         ctypes.c_char_p, _vp, _pvp],
         "gbx_backward_init": [_vp, _vp, _vp, ctypes.c_int, ctypes.c_char_p, _vp, _pvp],
+        "gbx_neighbor_alltoall_init": [_vp, _i64, _vp, _vp, _i64, _vp, ctypes.c_int, _i64, ctypes.c_int, _vp,
+                                       ctypes.c_char_p, _vp, _pvp],
+        "gbx_neighbor_allgather_init": [_vp, _i64, _vp, _vp, _i64, _vp, ctypes.c_int, _i64, ctypes.c_int, _vp,
+                                        ctypes.c_char_p, _vp, _pvp],
+        "gbx_neighbor_allgatherv_init": [_vp, _i64, _vp, _vp, _vp, _i64, _vp, _vp, _vp, _i64, ctypes.c_int, _vp,
+                                         ctypes.c_char_p, _vp, _pvp],
+        "gbx_alltoallv_init": [_vp, _vp, _i64, _vp, _vp, _vp, _vp, _i64, _vp, _vp, _vp, _i64, ctypes.c_int,
+                               ctypes.c_char_p, _vp, _pvp],
         "gbx_start": [_vp],
         "gbx_wait": [_vp],
         "gbx_test": [_vp, ctypes.POINTER(ctypes.c_int)],
@@ -227,6 +235,51 @@ def backward_init(forward: Request, grad_recv, grad_send, accumulate: bool = Fal
                                    int(bool(accumulate)), info.encode() if info else None,
                                    _stream_handle(stream), ctypes.byref(h)), "backward_init")
     return Request(h, keep=(grad_recv, grad_send, forward))
+
+
+def neighbor_alltoall_init(sendbuf, send_base, recvbuf, recv_base, count: int, graph: DistGraph,
+                           elem_size: int, dtype: int = BYTES, info: str = "", stream=None) -> Request:
+    """MPI_Neighbor_alltoall, persistent (see include/gbx.h)."""
+    h = ctypes.c_void_p()
+    _check(lib().gbx_neighbor_alltoall_init(
+        _ptr(sendbuf), _nbytes(sendbuf), _ptr(send_base), _ptr(recvbuf), _nbytes(recvbuf), _ptr(recv_base),
+        int(count), int(elem_size), int(dtype), graph.handle, info.encode() if info else None,
+        _stream_handle(stream), ctypes.byref(h)), "neighbor_alltoall_init")
+    return Request(h, keep=(sendbuf, recvbuf, graph))
+
+
+def neighbor_allgather_init(sendbuf, send_base, recvbuf, recv_base, count: int, graph: DistGraph,
+                            elem_size: int, dtype: int = BYTES, info: str = "", stream=None) -> Request:
+    """MPI_Neighbor_allgather, persistent (see include/gbx.h)."""
+    h = ctypes.c_void_p()
+    _check(lib().gbx_neighbor_allgather_init(
+        _ptr(sendbuf), _nbytes(sendbuf), _ptr(send_base), _ptr(recvbuf), _nbytes(recvbuf), _ptr(recv_base),
+        int(count), int(elem_size), int(dtype), graph.handle, info.encode() if info else None,
+        _stream_handle(stream), ctypes.byref(h)), "neighbor_allgather_init")
+    return Request(h, keep=(sendbuf, recvbuf, graph))
+
+
+def neighbor_allgatherv_init(sendbuf, send_base, sendcount, recvbuf, recv_base, recvcounts, rdispls,
+                             graph: DistGraph, elem_size: int, dtype: int = BYTES, info: str = "",
+                             stream=None) -> Request:
+    """MPI_Neighbor_allgatherv, persistent (see include/gbx.h)."""
+    h = ctypes.c_void_p()
+    _check(lib().gbx_neighbor_allgatherv_init(
+        _ptr(sendbuf), _nbytes(sendbuf), _ptr(send_base), _ptr(sendcount), _ptr(recvbuf), _nbytes(recvbuf),
+        _ptr(recv_base), _ptr(recvcounts), _ptr(rdispls), int(elem_size), int(dtype), graph.handle,
+        info.encode() if info else None, _stream_handle(stream), ctypes.byref(h)), "neighbor_allgatherv_init")
+    return Request(h, keep=(sendbuf, recvbuf, graph))
+
+
+def alltoallv_init(comm: Comm, sendbuf, send_base, sendcounts, sdispls, recvbuf, recv_base, recvcounts,
+                   rdispls, elem_size: int, dtype: int = BYTES, info: str = "", stream=None) -> Request:
+    """MPIX_Alltoallv over the emulated communicator, persistent (P x P arrays, see include/gbx.h)."""
+    h = ctypes.c_void_p()
+    _check(lib().gbx_alltoallv_init(
+        comm.handle, _ptr(sendbuf), _nbytes(sendbuf), _ptr(send_base), _ptr(sendcounts), _ptr(sdispls),
+        _ptr(recvbuf), _nbytes(recvbuf), _ptr(recv_base), _ptr(recvcounts), _ptr(rdispls), int(elem_size),
+        int(dtype), info.encode() if info else None, _stream_handle(stream), ctypes.byref(h)), "alltoallv_init")
+    return Request(h, keep=(sendbuf, recvbuf, comm))
 
 
 def _handles(reqs: Sequence[Request]):

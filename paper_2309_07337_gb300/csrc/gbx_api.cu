@@ -628,7 +628,9 @@ static void destroy_request(gbx_request_s *req) {
     while (!req->batches.empty()) destroy_batch(req->batches.back());
     if (req->exec) cudaGraphExecDestroy(req->exec);
     if (req->done) cudaEventDestroy(req->done);
+    gbx_graph_s *g = req->owned_graph;
     delete req;
+    if (g) gbx_graph_free(&g);
 }
 
 static gbx_request_s *new_request(const Opts &o, void *stream) {

@@ -222,6 +222,7 @@ struct gbx_request_s {
     int timeout_ms;
     gbx_graph_s *graph;
     gbx_request_s *forward;  // backward: its forward request
+    gbx_graph_s *owned_graph;  // graph built for this request (dense all-to-all-v), freed with it
     cudaStream_t stream;
     cudaEvent_t done;
     cudaEvent_t *pending;    // event to wait on while active (own or a batch's)
