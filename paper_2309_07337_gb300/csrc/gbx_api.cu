@@ -418,7 +418,7 @@ static int tune_op(gbx_request_s *req, HostOp &op) {
     key.units = op.units; key.elem_size = req->elem_size;
     key.nseg = op.kind == 0 ? op.cd.nseg : 0;
     key.nterms = op.kind == 1 ? op.fd.nchunks : 0;
-    key.flat_ok = op.kind == 0 ? op.flat_ok + 2 * op.flat_only + 4 * (op.cd.flat == 3) : 0;
+    key.flat_ok = op.kind == 0 ? op.flat_ok + 2 * op.flat_only + 4 * ((op.cd.flat & 3) == 3) : 0;
     int blocks[4] = {128, 256, 512, 1024};
     if (!req->autotune || req->forced_block) {
         op.block = req->forced_block ? req->forced_block : 256;
@@ -443,22 +443,29 @@ static int tune_op(gbx_request_s *req, HostOp &op) {
             op.block = it->second.block;
             op.persistent = it->second.persistent;
             op.tuned_ms = it->second.ms;
-            if (op.kind == 0 && !op.flat_only) op.cd.flat = it->second.flat;
+            if (op.kind == 0) op.cd.flat = it->second.flat;
             if (op.kind == 0 && op.cd.flat) op.algo_bytes = op.algo_bytes_flat;
             return set_vec(req, op, it->second.vec);
         }
     }
     TuneVal best = {op.max_vec, 256, 1, 0, 1e30f};
-    const int nflat = (op.kind == 0 && op.flat_ok && !op.flat_only && req->forced_flat < 0) ? 2 : 1;
-    for (int fl = 0; fl < nflat; fl++) {
-        if (op.kind == 0 && !op.flat_only) op.cd.flat = nflat == 2 ? fl : (op.flat_ok && req->forced_flat > 0);
+    // candidate forms: segments, flat (gather or two-index), and the pipelined flat form
+    std::vector<int> forms;
+    if (op.kind == 1) forms.push_back(0);
+    else if (op.flat_only) { forms.push_back(op.cd.flat & 3); forms.push_back((op.cd.flat & 3) + 4); }
+    else if (op.flat_ok && req->forced_flat < 0) { forms.push_back(0); forms.push_back(1); forms.push_back(5); }
+    else if (op.flat_ok && req->forced_flat > 0) { forms.push_back(1); forms.push_back(5); }
+    else forms.push_back(0);
+    for (int form : forms) {
+        if (op.kind == 0) op.cd.flat = form;
+        const bool pipe = form >= 4;
         for (int vec = op.max_vec; vec >= op.min_vec; vec >>= 1) {
             GBX_TRY(set_vec(req, op, vec));
-            for (int bi = 0; bi < 4; bi++)
-                for (int pers = 1; pers >= 0; pers--) {
+            for (int bi = pipe ? 2 : 0; bi < 4; bi++)
+                for (int pers = 1; pers >= (pipe ? 1 : 0); pers--) {
                     float ms = 0;
                     GBX_TRY(time_op(req, op, blocks[bi], pers, 3, &ms));
-                    if (ms < best.ms) best = {vec, blocks[bi], pers, op.kind == 0 ? op.cd.flat : 0, ms};
+                    if (ms < best.ms) best = {vec, blocks[bi], pers, form, ms};
                 }
             if (vec == 1) break;
         }
@@ -466,7 +473,7 @@ static int tune_op(gbx_request_s *req, HostOp &op) {
     op.block = best.block;
     op.persistent = best.persistent;
     op.tuned_ms = best.ms;
-    if (op.kind == 0 && !op.flat_only) op.cd.flat = best.flat;
+    if (op.kind == 0) op.cd.flat = best.flat;
     if (op.kind == 0 && op.cd.flat) op.algo_bytes = op.algo_bytes_flat;
     GBX_TRY(set_vec(req, op, best.vec));
     std::lock_guard<std::mutex> lk(g_tune_mu);

@@ -166,6 +166,65 @@ __device__ __forceinline__ void copy_tile_flat2(const CopyDesc *__restrict__ d, 
         if ((int64_t)(u * B + threadIdx.x) < left) stv<VEC>(d->dst + doff[u], val[u]);
 }
 
+// Software-pipelined flat forms for a single-op persistent launch: the index loads of the
+// block's next tile are issued while the current tile's payload loads are in flight, so the
+// payload loads no longer wait for a full index round trip.  FORM 1: flat gather, 3: two-index.
+template <int VEC, int U, int FORM>
+__device__ __forceinline__ void flat_indices(const CopyDesc *__restrict__ d, int64_t t, uint32_t (&gi)[U],
+                                             int32_t (&gd)[U], int64_t (&e)[U], int64_t (&j)[U], bool (&ok)[U]) {
+    constexpr int B = GBX_TILE / U;
+    const int cpe = d->cpe, sh = d->cpe_shift;
+    const uint32_t magic = d->cpe_magic;
+    const int64_t e0 = __ldg(d->tile_e0 + t);
+    const uint32_t r0 = (uint32_t)(t * GBX_TILE - e0 * cpe);
+    const int64_t left = d->nchunks - t * GBX_TILE;
+#pragma unroll
+    for (int u = 0; u < U; u++) {
+        const uint32_t x = r0 + (uint32_t)(u * B) + threadIdx.x;
+        const uint32_t el = unit_of(x, cpe, sh, magic);
+        j[u] = (int64_t)(x - el * (uint32_t)cpe) * VEC;
+        e[u] = e0 + el;
+        ok[u] = (int64_t)(u * B + threadIdx.x) < left;
+        gi[u] = ok[u] ? (uint32_t)__ldg(d->flat_idx + e[u]) : 0u;
+        if (FORM == 3) gd[u] = ok[u] ? __ldg(d->flat_didx + e[u]) : 0;
+    }
+}
+
+template <int VEC, int U, int FORM>
+__device__ __forceinline__ void copy_flat_pipelined(const CopyDesc *__restrict__ d, int64_t ntiles) {
+    typedef typename VecT<VEC>::T V;
+    const int64_t s = d->elem_size;
+    int64_t t = blockIdx.x;
+    if (t >= ntiles) return;
+    uint32_t gi[U];
+    int32_t gd[U];
+    int64_t e[U], j[U];
+    bool ok[U];
+    flat_indices<VEC, U, FORM>(d, t, gi, gd, e, j, ok);
+    for (;;) {
+        const int64_t tn = t + gridDim.x;
+        V val[U];
+        int64_t doff[U];
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+            doff[u] = (FORM == 3 ? (int64_t)gd[u] * s : d->dst_flat0 + e[u] * s) + j[u];
+            if (ok[u]) {
+                const char *base = (gi[u] & GBX_FLAT_SRC2) ? d->src2 : d->src;
+                val[u] = ldv<VEC>(base + (int64_t)(gi[u] & ~GBX_FLAT_SRC2) * s + j[u]);
+            }
+        }
+        bool okc[U];
+#pragma unroll
+        for (int u = 0; u < U; u++) okc[u] = ok[u];
+        if (tn < ntiles) flat_indices<VEC, U, FORM>(d, tn, gi, gd, e, j, ok);
+#pragma unroll
+        for (int u = 0; u < U; u++)
+            if (okc[u]) stv<VEC>(d->dst + doff[u], val[u]);
+        if (tn >= ntiles) break;
+        t = tn;
+    }
+}
+
 template <int VEC, int U>
 __device__ __forceinline__ void copy_tile(const CopyDesc *__restrict__ d, int64_t t) {
     typedef typename VecT<VEC>::T V;
@@ -231,7 +290,7 @@ __device__ __forceinline__ void copy_tile(const CopyDesc *__restrict__ d, int64_
 #endif
 template <int VEC, int U>
 __device__ __forceinline__ void copy_tile_any(const CopyDesc *__restrict__ d, int64_t t, int flat) {
-    if (flat == 3) copy_tile_flat2<VEC, U>(d, t);
+    if ((flat & 3) == 3) copy_tile_flat2<VEC, U>(d, t);
     else if (flat) copy_tile_flat<VEC, U>(d, t);
     else copy_tile<VEC, U>(d, t);
 }
@@ -260,6 +319,17 @@ gbx_copy_kernel(const CopyDesc *const *__restrict__ ops, const int64_t *__restri
             }
         }
     }
+}
+
+// Pipelined flat forms (descriptor flat = 5: gather, 7: two-index), one op per launch,
+// persistent grid; launch bounds keep two full waves of threads resident (<= 32 registers).
+template <int VEC, int U, int FORM>
+__global__ void __launch_bounds__(GBX_TILE / U, 2 * U)
+gbx_copy_pipe_kernel(const CopyDesc *const *__restrict__ ops, const int64_t *__restrict__ prefix, int nops,
+                     int64_t total_tiles) {
+    (void)prefix;
+    (void)nops;
+    copy_flat_pipelined<VEC, U, FORM>(ops[0], total_tiles);
 }
 
 // ------------------------------------------------------------------------ fold
@@ -407,15 +477,23 @@ static CopyFn copy_fn_u(int block) {
     }
 }
 
+template <int VEC, int FORM>
+static CopyFn pipe_fn_u(int block) {
+    return block == 1024 ? gbx_copy_pipe_kernel<VEC, 1, FORM> : gbx_copy_pipe_kernel<VEC, 2, FORM>;
+}
+
 template <int VEC>
 static CopyFn copy_fn_v(int block, int flat) {
+    if (flat == 5) return pipe_fn_u<VEC, 1>(block);
+    if (flat == 7) return pipe_fn_u<VEC, 3>(block);
     if (flat == 1) return copy_fn_u<VEC, 1>(block);
     if (flat == 3) return copy_fn_u<VEC, 3>(block);
     if (flat == 0) return copy_fn_u<VEC, 0>(block);
     return copy_fn_u<VEC, 2>(block);
 }
 
-// flat: 0 segment form, 1 flat form, 3 two-index flat form, 2 decided per op (mixed launches)
+// flat: 0 segment form, 1 flat form, 3 two-index flat form, 2 decided per op (mixed launches),
+// 5 / 7 the pipelined flat forms (one op, persistent grid, block 512 or 1024)
 static CopyFn copy_fn(int vec, int block, int flat) {
     switch (vec) {
         case 16: return copy_fn_v<16>(block, flat);
@@ -462,7 +540,10 @@ static FoldFn fold_fn(int dtype, int vec, int block) {
 // Blocks of the mixed kernels never go below 256 threads (their unroll is capped at 4).
 int gbx_effective_block(int vec_class, int block) { return (vec_class == 0 && block < 256) ? 256 : block; }
 
+static int pipe_block(int flat, int block) { return (flat == 5 || flat == 7) && block < 512 ? 512 : block; }
+
 int gbx_occupancy(int kind, int dtype, int vec, int block, int flat) {
+    if (kind == 0) block = pipe_block(flat, block);
     const void *f = kind == 0 ? (const void *)copy_fn(vec, block, flat) : (const void *)fold_fn(dtype, vec, block);
     int n = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, f, gbx_effective_block(vec, block), 0);
@@ -477,6 +558,8 @@ static int clamp_grid(int grid, int64_t total_tiles) {
 cudaError_t gbx_launch_copy(const CopyDesc *const *ops, const int64_t *tile_prefix, int nops, int64_t total_tiles,
                             int vec, int flat, int block, int grid, cudaStream_t st) {
     if (total_tiles <= 0) return cudaSuccess;
+    if ((flat == 5 || flat == 7) && (nops > 1 || vec == 0)) flat -= 4;   // the pipelined kernels take one op
+    block = pipe_block(flat, block);
     CopyFn f = copy_fn(vec, block, flat);
     f<<<clamp_grid(grid, total_tiles), gbx_effective_block(vec, block), 0, st>>>(ops, tile_prefix, nops, total_tiles);
     return cudaGetLastError();

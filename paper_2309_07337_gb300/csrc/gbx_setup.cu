@@ -1144,7 +1144,7 @@ int gbx_validate_program(gbx_request_s *req, int64_t agg_bytes) {
             if (d.idx)
                 check_copy_idx_kernel<<<grid_of(d.nelem), SETUP_T, 0, st>>>(d.segs, d.nseg, d.nelem, d.idx,
                                                                             d.elem_size, bytes_of(d.src_role), err);
-            if (op.flat_ok && d.flat == 3)
+            if (op.flat_ok && (d.flat & 3) == 3)
                 check_flat2_kernel<<<grid_of(d.nelem), SETUP_T, 0, st>>>(d.flat_idx, d.flat_didx, d.nelem, d.elem_size,
                                                                          bytes_of(d.src_role),
                                                                          d.src2 ? bytes_of(d.src2_role) : 0,
