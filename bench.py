@@ -20,6 +20,12 @@ the SpMV halo (config 2) standard vs locality rates.
 
 --impl reference times the CPU oracle (the only reference this build has) on a bounded
 sample of the same workload: the exchanges into the first ranks' receive buffers.
+
+Two other modes print their own JSON line instead of the step's:
+  --sweep  message-size sweep of the stencil at P = 4096: block edge 8/16/32 points x 1..16
+           fp64 per point, standard and locality forms, cold L2;
+  --faces  the standard exchange per direction class (x, y, z faces; edges and corners) of
+           the 512^3 stencil, with each class's 128-byte-line DRAM floor.
 """
 from __future__ import annotations
 
@@ -59,6 +65,11 @@ def parse_args():
     a.add_argument("--no-e2e", action="store_true")
     a.add_argument("--no-cpu", action="store_true")
     a.add_argument("--edge", type=int, default=32, help="block edge (32 = the 512^3 workload)")
+    a.add_argument("--sweep", action="store_true",
+                   help="instead of the step: message-size sweep, comps 1..16 x block edge 8..32 at P=4096")
+    a.add_argument("--faces", action="store_true",
+                   help="instead of the step: standard exchange per face / edge+corner subset of the 512^3 "
+                        "stencil, with the 128-byte-line DRAM floor of each")
     return a.parse_args()
 
 
@@ -317,7 +328,7 @@ def run_ours(args):
     achieved = infos[0]["algo_bytes"] / (std_ms * 1e-3) / 1e9
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": profiled_traffic("gbx_copy_kernel_std_stencil512"),
-                "kernel": "gbx_copy_kernel (standard exchange, one launch per start)",
+                "kernel": "gbx_copy_pipe_kernel<16,1,1> (standard exchange, one launch per start)",
                 "peak_source": f"{peak_kind} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"}
     launches = sum(i["launches"] for i in infos) * K
 
@@ -384,6 +395,35 @@ def _time_loop(torch, fn, reps):
 
 def extras(gbx, torch, p, field, halo, grad_halo, grad_field, dp, ex_std, bwd):
     out = {}
+    # start -> wait latency on the L2-resident config 1 (2D 5-point halo, 3,072 elements)
+    q1 = pt.config1()
+    f1 = torch.from_numpy(pt.stencil_field(q1, pt.SEED + 1)).cuda()
+    lat = {"V": q1.volume, "E": q1.n_edges}
+    for name in ("standard", "locality"):
+        for mode in ("graph=1", "graph=0"):
+            h = torch.zeros(q1.recvbuf_bytes // 8, dtype=torch.float64, device="cuda")
+            ex = gbx.Exchange(q1, f1, h, name, info=mode)
+            wall, dev = [], []
+            for i in range(220):
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                torch.cuda.synchronize()
+                t = time.perf_counter()
+                e0.record()
+                ex.request.start()
+                e1.record()
+                ex.request.wait()
+                t = time.perf_counter() - t
+                e1.synchronize()
+                if i >= 20:
+                    wall.append(t * 1e6)
+                    dev.append(e0.elapsed_time(e1) * 1e3)
+            lat[f"{name}_{'graph' if mode == 'graph=1' else 'eager'}"] = {
+                "start_wait_us": statistics.median(wall), "device_us": statistics.median(dev),
+                "launches": ex.info()["launches"]}
+            del ex, h
+    lat["note"] = "L2-resident: latency instead of a fraction of HBM bandwidth; median of 200"
+    out["latency_cfg1"] = lat
     # fused forward + backward (one graph, fused level launches) vs plain
     plain_f = gbx.Exchange(p, field, halo, "standard", info="graph=0", dp=dp, graph=ex_std.graph)
     plain_b = gbx.backward_init(plain_f.request, grad_halo, grad_field, info="graph=0")
@@ -488,6 +528,7 @@ def extras(gbx, torch, p, field, halo, grad_halo, grad_field, dp, ex_std, bwd):
             ex.request.start()
             e1.record()
             ex.request.wait()
+            e1.synchronize()
             ts.append(e0.elapsed_time(e1))
         ms = statistics.median(ts)
         res[name] = {"ms": ms, "user_GBps": q.user_bytes() / (ms * 1e-3) / 1e9,
@@ -502,10 +543,140 @@ def extras(gbx, torch, p, field, halo, grad_halo, grad_field, dp, ex_std, bwd):
     return out
 
 
+def _cold_ms(torch, req, flush, reps=20, warm=3):
+    """Median CUDA-event time of start() with L2 flushed (a 256 MB write) before each rep."""
+    for _ in range(warm):
+        req.start()
+        req.wait()
+    ts = []
+    for _ in range(reps):
+        flush.fill_(1)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        req.start()
+        e1.record()
+        req.wait()
+        e1.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    return statistics.median(ts)
+
+
+def run_sweep(args):
+    """Message-size sweep of the 27-point stencil at P = 4096 (16^3 ranks, 64 per node):
+    block edge 8, 16, 32 points and 1, 2, 4, 8, 16 fp64 components per point; standard and
+    locality forms, cold L2, bytes of both forms compared."""
+    import torch
+    import paper_2309_07337_gb300 as gbx
+    peak, peak_kind = measured_peaks()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    gen = torch.Generator(device="cuda")
+    rows = []
+    for edge in (8, 16, 32):
+        for comps in (1, 2, 4, 8, 16):
+            p = pt.config5(edge=edge, comps=comps)
+            gen.manual_seed(pt.SEED + 5)
+            field = torch.rand(p.sendbuf_bytes // 8, dtype=torch.float64, device="cuda", generator=gen)
+            h1 = torch.zeros(p.recvbuf_bytes // 8, dtype=torch.float64, device="cuda")
+            h2 = torch.zeros_like(h1)
+            dp = gbx.DevicePattern(p)
+            a = gbx.Exchange(p, field, h1, "standard", dp=dp)
+            b = gbx.Exchange(p, field, h2, "locality", dp=dp, graph=a.graph)
+            row = {"edge": edge, "comps": comps, "elem_bytes": p.elem_size, "V": p.volume,
+                   "field_bytes": p.sendbuf_bytes, "user_bytes": 2 * p.volume * p.elem_size}
+            for name, ex in (("standard", a), ("locality", b)):
+                ms = _cold_ms(torch, ex.request, flush)
+                info = ex.info()
+                row[name] = {"ms": ms, "user_GBps": row["user_bytes"] / (ms * 1e-3) / 1e9,
+                             "algo_GBps": info["algo_bytes"] / (ms * 1e-3) / 1e9,
+                             "frac_of_measured_hbm": info["algo_bytes"] / (ms * 1e-3) / 1e9 / peak,
+                             "vec": info["vec_bytes"], "block": info["block"], "launches": info["launches"]}
+            row["identical"] = bool(torch.equal(h1.view(torch.uint8), h2.view(torch.uint8)))
+            rows.append(row)
+            print(json.dumps(row), file=sys.stderr)
+            del a, b, dp, field, h1, h2
+            torch.cuda.empty_cache()
+    print(json.dumps({"sweep": "stencil27_P4096_message_size", "peak_GBps": peak, "peak_kind": peak_kind,
+                      "l2": "flushed (256 MB write) before every repetition; median of 20", "rows": rows}))
+
+
+def line_floor(p):
+    """DRAM bytes a standard exchange of `p` cannot avoid when memory moves in 128-byte
+    lines: every 128-byte line holding a sent element is read once, the receive buffer is
+    written once, and the 4-byte source index of every element is read."""
+    sc = np.asarray(p.sendcounts, dtype=np.int64)
+    owner = np.repeat(np.arange(p.P), np.diff(np.asarray(p.out_ptr)))
+    V = int(sc.sum())
+    first = np.cumsum(sc) - sc
+    slot = np.repeat(np.asarray(p.sdispls, dtype=np.int64), sc) + (np.arange(V) - np.repeat(first, sc))
+    r = np.repeat(owner, sc)
+    el = slot if p.send_idx is None else np.asarray(p.send_idx)[np.asarray(p.send_slot_ptr)[r] + slot]
+    off = np.asarray(p.send_base)[r] + el.astype(np.int64) * p.elem_size
+    lines = np.unique(np.concatenate([off >> 7, (off + p.elem_size - 1) >> 7]))
+    return {"read_lines_bytes": int(len(lines)) * 128, "index_bytes": 4 * V, "write_bytes": V * p.elem_size,
+            "total": int(len(lines)) * 128 + 4 * V + V * p.elem_size}
+
+
+def run_faces(args):
+    """The standard exchange of the 512^3 27-point stencil restricted to one direction class
+    at a time (x faces: single 64-byte points 2 KB apart; y faces: rows of 32 points; z
+    faces: whole 32x32 planes; edges and corners), so that DRAM counters of each launch can
+    be set against its algorithmic bytes and its 128-byte-line floor."""
+    import torch
+    import paper_2309_07337_gb300 as gbx
+    peak, peak_kind = measured_peaks()
+    g = 16 * args.edge
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(pt.SEED + 5)
+    field = torch.rand(g ** 3 * 8, dtype=torch.float64, device="cuda", generator=gen)
+    dirs_all = [(a, b, c) for c in (-1, 0, 1) for b in (-1, 0, 1) for a in (-1, 0, 1) if (a, b, c) != (0, 0, 0)]
+    cases = [("all", None), ("x_faces", [(-1, 0, 0), (1, 0, 0)]), ("y_faces", [(0, -1, 0), (0, 1, 0)]),
+             ("z_faces", [(0, 0, -1), (0, 0, 1)]),
+             ("edges_corners", [d for d in dirs_all if sum(map(abs, d)) >= 2])]
+    rows = []
+    for name, dirs in cases:
+        p = pt.stencil((g, g, g), (16, 16, 16), ppn=64, comps=8, dtype="f64", neighbors="all", directions=dirs)
+        h = torch.zeros(p.recvbuf_bytes // 8, dtype=torch.float64, device="cuda")
+        ex = gbx.Exchange(p, field, h, "standard")
+        for _ in range(3):
+            ex.start()
+            ex.wait()
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_push(f"face_{name}")
+        ts = []
+        for _ in range(20):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            ex.start()
+            e1.record()
+            ex.wait()
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        torch.cuda.nvtx.range_pop()
+        ms = statistics.median(ts)
+        info = ex.info()
+        fl = line_floor(p)
+        row = {"case": name, "V": p.volume, "ms": ms, "algo_bytes": info["algo_bytes"],
+               "algo_GBps": info["algo_bytes"] / (ms * 1e-3) / 1e9, "floor_bytes": fl,
+               "floor_GBps": fl["total"] / (ms * 1e-3) / 1e9,
+               "floor_frac_of_measured_hbm": fl["total"] / (ms * 1e-3) / 1e9 / peak}
+        rows.append(row)
+        print(json.dumps(row), file=sys.stderr)
+        del ex, h
+        torch.cuda.empty_cache()
+    print(json.dumps({"faces": f"stencil27_{g}cube_P4096_c8_standard", "peak_GBps": peak, "peak_kind": peak_kind,
+                      "rows": rows}))
+
+
 def main():
     args = parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.sweep:
+        run_sweep(args)
+    elif args.faces:
+        run_faces(args)
     else:
         run_ours(args)
 
