@@ -12,7 +12,10 @@ follows, from "MPI Advance: Open-Source Message Passing Optimizations" (arXiv
   * section 2.2, last paragraph, and section 1: locality-aware aggregation with
     unique global indices, one message per node pair (orc_locality);
   * the reverse exchange (the transpose of the forward 0/1 map) in two fixed
-    summation orders (orc_backward).
+    summation orders (orc_backward);
+  * the neighbourhood all-to-all-w (section 2.2's neighbourhood collectives with one
+    datatype per edge, MPI standard meaning) and its reverse (orc_alltoallw,
+    orc_alltoallw_backward).
 
 Parity is pinned by tests/test_oracle_pins.py against brute-force global indexing,
 hand-worked golden cases, invariants and closed-form counts.  The backward's bit
@@ -67,6 +70,19 @@ class _Pattern(ctypes.Structure):
     ]
 
 
+class _WPattern(ctypes.Structure):
+    _fields_ = [
+        ("P", ctypes.c_int),
+        ("in_ptr", ctypes.c_void_p), ("sources", ctypes.c_void_p),
+        ("out_ptr", ctypes.c_void_p), ("dests", ctypes.c_void_p),
+        ("sendcounts", ctypes.c_void_p), ("sendtypes", ctypes.c_void_p), ("sdispls", ctypes.c_void_p),
+        ("recvcounts", ctypes.c_void_p), ("recvtypes", ctypes.c_void_p), ("rdispls", ctypes.c_void_p),
+        ("send_base", ctypes.c_void_p), ("recv_base", ctypes.c_void_p),
+        ("types", ctypes.c_void_p), ("ntypes", ctypes.c_int),
+        ("sendbuf_bytes", ctypes.c_int64), ("recvbuf_bytes", ctypes.c_int64),
+    ]
+
+
 def load(path: str | None = None):
     global _lib
     if path is not None:
@@ -84,8 +100,13 @@ def load(path: str | None = None):
     lib.orc_locality_stats.argtypes = [P, vp]
     lib.orc_locality_layout.argtypes = [P, vp, vp, vp, vp]
     lib.orc_backward.argtypes = [P, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, vp]
+    W = ctypes.POINTER(_WPattern)
+    lib.orc_alltoallw_validate.argtypes = [W]
+    lib.orc_alltoallw.argtypes = [W, vp, vp]
+    lib.orc_alltoallw_backward.argtypes = [W, ctypes.c_int, ctypes.c_int, vp, vp]
     for f in ("orc_match", "orc_validate", "orc_standard", "orc_locality",
-              "orc_locality_stats", "orc_locality_layout", "orc_backward"):
+              "orc_locality_stats", "orc_locality_layout", "orc_backward",
+              "orc_alltoallw_validate", "orc_alltoallw", "orc_alltoallw_backward"):
         getattr(lib, f).restype = ctypes.c_int
     if path is None:
         _lib = lib
@@ -224,6 +245,66 @@ def backward(p, grad_recv, grad_send=None, form=0, accumulate=False, dtype=None,
     dt = DTYPES[dtype or p.dtype]
     rc = lib.orc_backward(m.ref(), int(form), dt, int(bool(accumulate)), gr.ctypes.data,
                           out.ctypes.data)
+    if rc:
+        raise OracleError(rc)
+    return out
+
+
+class _WMarshalled:
+    """C view of an all-to-all-w problem (patterns.WPattern)."""
+
+    def __init__(self, w):
+        self.keep = {}
+        s = _WPattern()
+        s.P = int(w.P)
+        for name, dt in (("in_ptr", np.int32), ("sources", np.int32), ("out_ptr", np.int32),
+                         ("dests", np.int32), ("sendcounts", np.int32), ("sendtypes", np.int32),
+                         ("sdispls", np.int64), ("recvcounts", np.int32), ("recvtypes", np.int32),
+                         ("rdispls", np.int64), ("send_base", np.int64), ("recv_base", np.int64)):
+            a = _arr(getattr(w, name), dt)
+            self.keep[name] = a
+            setattr(s, name, a.ctypes.data if a is not None and a.size else None)
+        t = np.ascontiguousarray(np.asarray(w.types, dtype=np.int64).reshape(-1, 8))
+        self.keep["types"] = t
+        s.types = t.ctypes.data if t.size else None
+        s.ntypes = int(t.shape[0])
+        s.sendbuf_bytes = int(w.sendbuf_bytes)
+        s.recvbuf_bytes = int(w.recvbuf_bytes)
+        self.struct = s
+
+    def ref(self):
+        return ctypes.byref(self.struct)
+
+
+def alltoallw_validate(w, lib=None) -> int:
+    """Error code the all-to-all-w would raise (0 = valid)."""
+    lib = lib or load()
+    return lib.orc_alltoallw_validate(_WMarshalled(w).ref())
+
+
+def alltoallw(w, sendbuf, recvbuf=None, lib=None):
+    """Neighbourhood all-to-all-w; returns the receive bytes (a copy of recvbuf if
+    given, else zeros)."""
+    lib = lib or load()
+    m = _WMarshalled(w)
+    _, sb = _bytes_view(sendbuf)
+    out = np.zeros(int(w.recvbuf_bytes), dtype=np.uint8) if recvbuf is None else \
+        np.array(np.ascontiguousarray(recvbuf).view(np.uint8).reshape(-1), copy=True)
+    rc = lib.orc_alltoallw(m.ref(), sb.ctypes.data if sb.size else None, out.ctypes.data if out.size else None)
+    if rc:
+        raise OracleError(rc)
+    return out
+
+
+def alltoallw_backward(w, grad_recv, grad_send=None, accumulate=False, dtype=None, lib=None):
+    """Reverse all-to-all-w in the standard order; returns the new grad_send bytes."""
+    lib = lib or load()
+    m = _WMarshalled(w)
+    _, gr = _bytes_view(grad_recv)
+    out = np.zeros(int(w.sendbuf_bytes), dtype=np.uint8) if grad_send is None else \
+        np.array(np.ascontiguousarray(grad_send).view(np.uint8).reshape(-1), copy=True)
+    rc = lib.orc_alltoallw_backward(m.ref(), DTYPES[dtype or w.dtype], int(bool(accumulate)),
+                                    gr.ctypes.data if gr.size else None, out.ctypes.data if out.size else None)
     if rc:
         raise OracleError(rc)
     return out

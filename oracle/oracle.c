@@ -673,3 +673,214 @@ int orc_backward(const orc_pattern *pt, int form, int dtype, int accumulate,
     free(racc);
     return err;
 }
+
+/* ---------------------------------------------- neighbourhood all-to-all-w --- */
+
+/* MPI_Neighbor_alltoallw (the neighbourhood collectives of section 2.2 with one datatype
+ * per edge), with the MPI standard's meaning.  A datatype here is a block of `blocklen`
+ * bytes repeated over up to three strided levels (innermost first: count[0] blocks
+ * stride[0] bytes apart, count[1] such rows stride[1] apart, count[2] planes stride[2]
+ * apart), and `count` items of the type lie `extent` bytes apart: an hvector nested up to
+ * three times and resized to `extent`, lower bound 0.  The message of an edge is the
+ * sequence of bytes in type-map order (item, then level 2, level 1, level 0, then byte
+ * within the block); out-edge e of r to d sends sendcounts[e] items of its send type from
+ * byte sdispls[e] of r's region, in-edge i of d receives recvcounts[i] items of its
+ * receive type at byte rdispls[i] of d's region, and the two byte sequences must have the
+ * same length.  Errors, the smallest code winning: a bad type or type index -> ARG;
+ * unmatched edge or unequal lengths or a negative count -> TRUNCATE; a negative base or
+ * displacement, or a byte outside its buffer -> INDEX; a receive byte written twice ->
+ * OVERLAP. */
+typedef struct { int64_t blocklen, count[3], stride[3], extent; } orc_type;
+
+typedef struct {
+    int P;
+    const int *in_ptr, *sources, *out_ptr, *dests;
+    const int *sendcounts, *sendtypes;  /* one per out-edge */
+    const int64_t *sdispls;             /* bytes            */
+    const int *recvcounts, *recvtypes;  /* one per in-edge  */
+    const int64_t *rdispls;             /* bytes            */
+    const int64_t *send_base, *recv_base;
+    const orc_type *types;
+    int ntypes;
+    int64_t sendbuf_bytes, recvbuf_bytes;
+} orc_wpattern;
+
+#define ORC_TYPE_MAX_SIZE ((int64_t)1 << 31)
+
+static int64_t type_size(const orc_type *t) {
+    return t->blocklen * t->count[0] * t->count[1] * t->count[2];
+}
+
+static int type_valid(const orc_type *t) {
+    if (t->blocklen < 0 || t->extent < 0) return 0;
+    int64_t size = t->blocklen;
+    for (int l = 0; l < 3; l++) {
+        if (t->count[l] < 0 || t->stride[l] < 0) return 0;
+        if (t->count[l] > 0 && size > ORC_TYPE_MAX_SIZE / t->count[l]) return 0;
+        size *= t->count[l];
+    }
+    return size <= ORC_TYPE_MAX_SIZE;
+}
+
+/* Byte offset (from the message's displacement) of byte b of the message. */
+static int64_t type_byte(const orc_type *t, int64_t b) {
+    int64_t size = type_size(t);
+    int64_t item = b / size, w = b % size;
+    int64_t blk = w / t->blocklen, off = w % t->blocklen;
+    int64_t c0 = blk % t->count[0];
+    blk /= t->count[0];
+    int64_t c1 = blk % t->count[1];
+    int64_t c2 = blk / t->count[1];
+    return item * t->extent + c2 * t->stride[2] + c1 * t->stride[1] + c0 * t->stride[0] + off;
+}
+
+/* Matches the edges and checks everything; returns the smallest error code found. */
+static int w_prepare(const orc_wpattern *wp, int64_t **match_out) {
+    if (!wp || wp->P <= 0 || !wp->in_ptr || !wp->out_ptr || wp->ntypes < 0 || (wp->ntypes && !wp->types))
+        return ORC_ERR_ARG;
+    for (int k = 0; k < wp->ntypes; k++)
+        if (!type_valid(&wp->types[k])) return ORC_ERR_ARG;
+    orc_pattern g;
+    memset(&g, 0, sizeof(g));
+    g.P = wp->P;
+    g.ppn = 1;
+    g.in_ptr = wp->in_ptr; g.sources = wp->sources; g.out_ptr = wp->out_ptr; g.dests = wp->dests;
+    int64_t n_out = wp->out_ptr[wp->P] > 0 ? wp->out_ptr[wp->P] : 1;
+    int64_t *match = malloc(sizeof(int64_t) * n_out);
+    if (!match) return ORC_ERR_NOMEM;
+    int err = orc_match(&g, match);
+    if (err) { free(match); return err; }
+    if (wp->out_ptr[wp->P] > 0 && (!wp->sendcounts || !wp->sendtypes || !wp->sdispls || !wp->recvcounts ||
+                                   !wp->recvtypes || !wp->rdispls))
+        err = ORC_ERR_ARG;
+    if (!wp->send_base || !wp->recv_base) err = ORC_ERR_ARG;
+    if (err) { free(match); return err; }
+    for (int r = 0; r < wp->P; r++)
+        if (wp->send_base[r] < 0 || wp->recv_base[r] < 0) MIN_ERR(err, ORC_ERR_INDEX);
+    for (int r = 0; r < wp->P; r++)
+        for (int64_t e = wp->out_ptr[r]; e < wp->out_ptr[r + 1]; e++) {
+            int d = wp->dests[e];
+            int64_t i = match[e];
+            int ts = wp->sendtypes[e], tr = wp->recvtypes[i];
+            if (ts < 0 || ts >= wp->ntypes || tr < 0 || tr >= wp->ntypes) { MIN_ERR(err, ORC_ERR_ARG); continue; }
+            const orc_type *Ts = &wp->types[ts], *Tr = &wp->types[tr];
+            int64_t n = (int64_t)wp->sendcounts[e] * type_size(Ts);
+            if (wp->sendcounts[e] < 0 || wp->recvcounts[i] < 0 || n != (int64_t)wp->recvcounts[i] * type_size(Tr)) {
+                MIN_ERR(err, ORC_ERR_TRUNCATE);
+                continue;
+            }
+            if (wp->sdispls[e] < 0 || wp->rdispls[i] < 0) { MIN_ERR(err, ORC_ERR_INDEX); continue; }
+            if (wp->send_base[r] < 0 || wp->recv_base[d] < 0) continue;
+            for (int64_t b = 0; b < n; b++) {
+                int64_t sa = wp->send_base[r] + wp->sdispls[e] + type_byte(Ts, b);
+                int64_t da = wp->recv_base[d] + wp->rdispls[i] + type_byte(Tr, b);
+                if (sa >= wp->sendbuf_bytes || da >= wp->recvbuf_bytes) { MIN_ERR(err, ORC_ERR_INDEX); break; }
+            }
+        }
+    if (err == ORC_OK && wp->recvbuf_bytes > 0) {
+        uint8_t *seen = calloc((size_t)wp->recvbuf_bytes, 1);
+        if (!seen) { free(match); return ORC_ERR_NOMEM; }
+        for (int r = 0; r < wp->P && !err; r++)
+            for (int64_t e = wp->out_ptr[r]; e < wp->out_ptr[r + 1] && !err; e++) {
+                int d = wp->dests[e];
+                int64_t i = match[e];
+                const orc_type *Tr = &wp->types[wp->recvtypes[i]];
+                int64_t n = (int64_t)wp->recvcounts[i] * type_size(Tr);
+                for (int64_t b = 0; b < n; b++) {
+                    int64_t da = wp->recv_base[d] + wp->rdispls[i] + type_byte(Tr, b);
+                    if (seen[da]) { err = ORC_ERR_OVERLAP; break; }
+                    seen[da] = 1;
+                }
+            }
+        free(seen);
+    }
+    if (err) { free(match); return err; }
+    *match_out = match;
+    return ORC_OK;
+}
+
+int orc_alltoallw_validate(const orc_wpattern *wp) {
+    int64_t *match = NULL;
+    int err = w_prepare(wp, &match);
+    free(match);
+    return err;
+}
+
+/* The definition: every byte b of every message is copied from its send address to its
+ * receive address; receive bytes no message covers are untouched. */
+int orc_alltoallw(const orc_wpattern *wp, const uint8_t *sendbuf, uint8_t *recvbuf) {
+    int64_t *match = NULL;
+    int err = w_prepare(wp, &match);
+    if (err) return err;
+    for (int r = 0; r < wp->P; r++)
+        for (int64_t e = wp->out_ptr[r]; e < wp->out_ptr[r + 1]; e++) {
+            int d = wp->dests[e];
+            int64_t i = match[e];
+            const orc_type *Ts = &wp->types[wp->sendtypes[e]], *Tr = &wp->types[wp->recvtypes[i]];
+            int64_t n = (int64_t)wp->sendcounts[e] * type_size(Ts);
+            for (int64_t b = 0; b < n; b++)
+                recvbuf[wp->recv_base[d] + wp->rdispls[i] + type_byte(Tr, b)] =
+                    sendbuf[wp->send_base[r] + wp->sdispls[e] + type_byte(Ts, b)];
+        }
+    free(match);
+    return ORC_OK;
+}
+
+/* Reverse exchange of the all-to-all-w in the standard order: every payload element
+ * (4 or 8 bytes, aligned with the message byte sequence) of the send buffer receives the
+ * left-to-right sum of the gradients at the receive addresses it was copied to, ordered
+ * by (destination rank, receive address); accumulate adds the sum to the old value;
+ * elements no message reads are untouched.  Every block length, stride, extent, base and
+ * displacement must be a multiple of the payload size (else ARG), so that each payload
+ * element travels whole. */
+int orc_alltoallw_backward(const orc_wpattern *wp, int dtype, int accumulate, const uint8_t *grad_recv,
+                           uint8_t *grad_send) {
+    if (dtype != ORC_F32 && dtype != ORC_F64) return ORC_ERR_ARG;
+    int64_t dsz = dtype == ORC_F64 ? 8 : 4;
+    int64_t *match = NULL;
+    int err = w_prepare(wp, &match);
+    if (err) return err;
+    for (int k = 0; k < wp->ntypes; k++) {
+        const orc_type *t = &wp->types[k];
+        if (type_size(t) == 0) continue;
+        if (t->blocklen % dsz || t->stride[0] % dsz || t->stride[1] % dsz || t->stride[2] % dsz || t->extent % dsz)
+            err = ORC_ERR_ARG;
+    }
+    int64_t n_terms = 0;
+    for (int r = 0; r < wp->P && !err; r++) {
+        if (wp->send_base[r] % dsz || wp->recv_base[r] % dsz) err = ORC_ERR_ARG;
+        for (int64_t e = wp->out_ptr[r]; e < wp->out_ptr[r + 1]; e++) {
+            int64_t i = match[e];
+            if (wp->sdispls[e] % dsz || wp->rdispls[i] % dsz) err = ORC_ERR_ARG;
+            n_terms += (int64_t)wp->sendcounts[e] * type_size(&wp->types[wp->sendtypes[e]]) / dsz;
+        }
+    }
+    if (err) { free(match); return err; }
+    term_t *t = malloc(sizeof(term_t) * (n_terms ? n_terms : 1));
+    uint8_t *gacc = malloc((size_t)dsz), *racc = malloc((size_t)dsz);
+    if (!t || !gacc || !racc) { free(t); free(gacc); free(racc); free(match); return ORC_ERR_NOMEM; }
+    int64_t n = 0;
+    for (int r = 0; r < wp->P; r++)
+        for (int64_t e = wp->out_ptr[r]; e < wp->out_ptr[r + 1]; e++) {
+            int d = wp->dests[e];
+            int64_t i = match[e];
+            const orc_type *Ts = &wp->types[wp->sendtypes[e]], *Tr = &wp->types[wp->recvtypes[i]];
+            int64_t len = (int64_t)wp->sendcounts[e] * type_size(Ts);
+            for (int64_t b = 0; b < len; b += dsz) {
+                int64_t da = wp->recv_base[d] + wp->rdispls[i] + type_byte(Tr, b);
+                t[n].row = wp->send_base[r] + wp->sdispls[e] + type_byte(Ts, b);
+                t[n].group = 0;
+                t[n].o1 = d;
+                t[n].o2 = da;
+                t[n].val = grad_recv + da;
+                n++;
+            }
+        }
+    qsort(t, n, sizeof(term_t), cmp_term);
+    fold_rows(t, n, dtype, dsz, accumulate, grad_send, gacc, racc);
+    free(t);
+    free(gacc);
+    free(racc);
+    free(match);
+    return ORC_OK;
+}

@@ -584,3 +584,260 @@ def config3_torch(count=64, device="cuda"):
     return [spmv_halo_torch(s["n"], s["P"], s["ppn"], s["nnz"], s["seed"], s["dtype"], device=device,
                             name=f"cfg3_{j}_n{s['n']}_P{s['P']}_{s['dtype']}")
             for j, s in enumerate(batched_specs(count, SEED + 3))]
+
+
+# ------------------------------------------------- neighbourhood all-to-all-w ---
+
+# Datatype table columns: a block of `blocklen` bytes repeated over three strided levels
+# (innermost first), items `extent` bytes apart (an hvector nested up to three times and
+# resized, lower bound 0).
+TYPE_COLUMNS = ("blocklen", "count0", "count1", "count2", "stride0", "stride1", "stride2", "extent")
+
+
+def contiguous_type(nbytes: int) -> list:
+    """One item = `nbytes` contiguous bytes."""
+    return [nbytes, 1, 1, 1, nbytes, nbytes, nbytes, nbytes]
+
+
+@dataclasses.dataclass
+class WPattern:
+    """One neighbourhood all-to-all-w problem: per edge a count, a byte displacement and
+    a datatype (an index into `types`), on both sides."""
+
+    name: str
+    P: int
+    ppn: int
+    in_ptr: np.ndarray          # int32 [P+1]
+    sources: np.ndarray         # int32 [E]
+    out_ptr: np.ndarray         # int32 [P+1]
+    dests: np.ndarray           # int32 [E]
+    sendcounts: np.ndarray      # int32 [E] items, aligned with dests
+    sdispls: np.ndarray         # int64 [E] bytes from the rank's send region
+    sendtypes: np.ndarray       # int32 [E] rows of `types`
+    recvcounts: np.ndarray      # int32 [E] items, aligned with sources
+    rdispls: np.ndarray         # int64 [E] bytes from the rank's receive region
+    recvtypes: np.ndarray       # int32 [E]
+    types: np.ndarray           # int64 [ntypes, 8], columns TYPE_COLUMNS
+    send_base: np.ndarray       # int64 [P]
+    recv_base: np.ndarray       # int64 [P]
+    sendbuf_bytes: int
+    recvbuf_bytes: int
+    dtype: str                  # payload type for the backward: 'f64', 'f32' or 'bytes'
+    meta: dict = dataclasses.field(default_factory=dict)
+
+    @property
+    def n_edges(self) -> int:
+        return int(self.out_ptr[-1])
+
+    def type_sizes(self) -> np.ndarray:
+        t = self.types.astype(np.int64)
+        return t[:, 0] * t[:, 1] * t[:, 2] * t[:, 3]
+
+    def message_bytes(self) -> np.ndarray:
+        """Bytes of every out-edge's message."""
+        return self.sendcounts.astype(np.int64) * self.type_sizes()[self.sendtypes]
+
+    def user_bytes(self) -> int:
+        return 2 * int(self.message_bytes().sum())
+
+
+def w_from_v(p: Pattern, name=None) -> WPattern:
+    """The all-to-all-v problem `p` (packed send buffers, no send index list) written as
+    an all-to-all-w with one contiguous element type: counts unchanged, displacements in
+    bytes."""
+    assert p.send_idx is None, "a send index list has no all-to-all-w equivalent here"
+    s = int(p.elem_size)
+    E = int(p.out_ptr[-1])
+    return WPattern(
+        name=name or p.name + "_w", P=p.P, ppn=p.ppn, in_ptr=p.in_ptr.copy(), sources=p.sources.copy(),
+        out_ptr=p.out_ptr.copy(), dests=p.dests.copy(), sendcounts=p.sendcounts.copy(),
+        sdispls=p.sdispls.astype(np.int64) * s, sendtypes=np.zeros(E, np.int32),
+        recvcounts=p.recvcounts.copy(), rdispls=p.rdispls.astype(np.int64) * s,
+        recvtypes=np.zeros(E, np.int32), types=np.array([contiguous_type(s)], np.int64),
+        send_base=p.send_base.copy(), recv_base=p.recv_base.copy(), sendbuf_bytes=int(p.sendbuf_bytes),
+        recvbuf_bytes=int(p.recvbuf_bytes), dtype=p.dtype)
+
+
+def stencil_w(grid, ranks, ppn, comps=1, dtype="f64", neighbors="all", layout="soa", name=None) -> WPattern:
+    """The stencil halo exchange of `stencil(...)` with each message described by a
+    datatype over the rank's field block instead of a send index list.
+
+    layout 'aos': point-major field (a point's `comps` values together), the layout of
+    `stencil`; layout 'soa': component-major field (component c of all the rank's points,
+    then component c+1).  Every message is the boundary box facing its direction, sent
+    as z-planes (items) of y-rows (level 2) of x-runs (level 1) of the point's components
+    (level 0 for 'soa'; the block itself for 'aos'), i.e. in ascending local point order
+    with components innermost.  Receive side: the ghost points packed point-major, as in
+    `stencil`.  With the same values the receive buffer equals `stencil`'s."""
+    p = stencil(grid, ranks, ppn, comps=comps, dtype=dtype, neighbors=neighbors)
+    D = len(grid)
+    blk = [g // r for g, r in zip(grid, ranks)] + [1] * (3 - D)
+    rk = list(ranks) + [1] * (3 - D)
+    nx, ny, nz = blk
+    npts = nx * ny * nz
+    vb = 8 if dtype == "f64" else 4
+    esz = comps * vb
+
+    def coords(r):
+        return (r % rk[0], (r // rk[0]) % rk[1], r // (rk[0] * rk[1]))
+
+    E = p.n_edges
+    owner = np.repeat(np.arange(p.P), np.diff(p.out_ptr))
+    types, key_of = [contiguous_type(esz)], {}
+    sendtypes = np.zeros(E, np.int32)
+    sendcounts = np.zeros(E, np.int32)
+    sdispls = np.zeros(E, np.int64)
+    for e in range(E):
+        r, d = int(owner[e]), int(p.dests[e])
+        cr, cd = coords(r), coords(d)
+        box = []
+        for ax in range(3):
+            dd = cd[ax] - cr[ax]
+            n = blk[ax]
+            box.append((0, 1) if dd == -1 else (n - 1, 1) if dd == 1 else (0, n))
+        (x0, lx), (y0, ly), (z0, lz) = box
+        p0 = x0 + nx * (y0 + ny * z0)
+        if layout == "soa":
+            t = [vb, comps, lx, ly, npts * vb, vb, nx * vb, nx * ny * vb]
+            sdispls[e] = p0 * vb
+        else:
+            t = [esz, lx, ly, 1, esz, nx * esz, 0, nx * ny * esz]
+            sdispls[e] = p0 * esz
+        k = tuple(t)
+        if k not in key_of:
+            key_of[k] = len(types)
+            types.append(t)
+        sendtypes[e] = key_of[k]
+        sendcounts[e] = lz
+    return WPattern(
+        name=name or f"stencil{D}d_{layout}_{'x'.join(map(str, grid))}_P{p.P}_c{comps}", P=p.P, ppn=p.ppn,
+        in_ptr=p.in_ptr, sources=p.sources, out_ptr=p.out_ptr, dests=p.dests, sendcounts=sendcounts,
+        sdispls=sdispls, sendtypes=sendtypes, recvcounts=p.recvcounts.copy(),
+        rdispls=p.rdispls.astype(np.int64) * esz, recvtypes=np.zeros(E, np.int32),
+        types=np.array(types, np.int64), send_base=p.send_base.copy(), recv_base=p.recv_base.copy(),
+        sendbuf_bytes=int(p.sendbuf_bytes), recvbuf_bytes=int(p.recvbuf_bytes), dtype=dtype,
+        meta={"v_pattern": p, "layout": layout, "block": tuple(blk[:D]), "comps": comps})
+
+
+def soa_from_aos(field: np.ndarray, P: int, npts: int, comps: int) -> np.ndarray:
+    """Component-major copy of a point-major field of P equal rank blocks."""
+    return np.ascontiguousarray(field.reshape(P, npts, comps).transpose(0, 2, 1)).reshape(-1)
+
+
+def _divisors(n):
+    return [k for k in range(1, n + 1) if n % k == 0]
+
+
+def _random_type(rng, k_el, es, overlap_ok):
+    """A datatype of k_el elements of es bytes; returns (row, span of one item).  Without
+    overlap_ok no byte appears twice in one item or across items."""
+    bl = int(rng.choice(_divisors(k_el)))
+    rest = k_el // bl
+    c = []
+    for _ in range(2):
+        f = int(rng.choice(_divisors(rest)))
+        c.append(f)
+        rest //= f
+    c.append(rest)
+    rng.shuffle(c)
+    # nesting by stride magnitude: a random level order, each level stepping over the
+    # span of the ones inside it (plus a gap), so blocks never collide
+    order = rng.permutation(3)
+    stride = [0, 0, 0]
+    span = bl * es
+    for lv in order:
+        st = span + int(rng.integers(0, 3)) * es
+        if overlap_ok and rng.random() < 0.2:
+            st = int(rng.integers(0, span + 1)) // es * es
+        stride[lv] = st
+        span = span + (c[lv] - 1) * st
+    ext = span + int(rng.integers(0, 3)) * es
+    if overlap_ok and rng.random() < 0.2:
+        ext = int(rng.integers(0, span + 1)) // es * es
+    return [bl * es, c[0], c[1], c[2], stride[0], stride[1], stride[2], ext], span
+
+
+def random_wpattern(seed: int, P=None, dtype=None, es=None, max_deg=5, max_items=4, max_el=12) -> WPattern:
+    """Random valid all-to-all-w for fuzzing: multigraph and self edges, empty messages,
+    send and receive datatypes of different shapes (levels nested in random order, gaps,
+    overlapping reads on the send side), receive messages in random order with gaps.
+    For f32/f64 every offset is a multiple of the payload size."""
+    rng = np.random.default_rng(seed)
+    P = int(P if P is not None else rng.integers(1, 25))
+    ppn = int(rng.choice([1, 2, 4, max(P, 1)]))
+    dtype = dtype or str(rng.choice(["bytes", "f32", "f64"]))
+    if es is None:
+        es = int(rng.choice([1, 2, 3, 8])) if dtype == "bytes" else (4 if dtype == "f32" else 8) * int(rng.choice([1, 2]))
+    outs = [[int(rng.integers(0, P)) for _ in range(int(rng.integers(0, max_deg + 1)))] for _ in range(P)]
+    types = []
+    out_src, out_dst, scount, stype, sdisp, n_el = [], [], [], [], [], []
+    send_need = np.zeros(P, np.int64)
+    for r in range(P):
+        for d in outs[r]:
+            n = int(rng.integers(0, max_items + 1)) * int(rng.integers(1, max_el + 1)) if rng.random() > 0.1 else 0
+            k_s = int(rng.choice(_divisors(n))) if n > 0 else int(rng.integers(1, 4))
+            row, span = _random_type(rng, k_s, es, overlap_ok=True)
+            ns = n // k_s if n > 0 else 0
+            types.append(row)
+            disp = int(rng.integers(0, 6)) * es
+            out_src.append(r); out_dst.append(d); scount.append(ns); stype.append(len(types) - 1)
+            sdisp.append(disp); n_el.append(n)
+            if ns > 0:
+                send_need[r] = max(send_need[r], disp + (ns - 1) * row[7] + span)
+    E = len(out_src)
+    send_base = np.zeros(P, np.int64)
+    off = int(rng.integers(0, 3)) * es
+    for r in range(P):
+        send_base[r] = off
+        off += int(send_need[r]) + int(rng.integers(0, 3)) * es
+    sendbuf_bytes = off
+    # in-lists: shuffled, each sender's listings in their order
+    ins = [[] for _ in range(P)]
+    for e in range(E):
+        ins[out_dst[e]].append(e)
+    in_src, rcount, rtype, rdisp, recv_size = [], [], [], [], np.zeros(P, np.int64)
+    for d in range(P):
+        lst = ins[d]
+        keys = rng.random(len(lst))
+        by_sender = {}
+        for i, e in enumerate(lst):
+            by_sender.setdefault(out_src[e], []).append(i)
+        for idxs in by_sender.values():
+            keys[idxs] = np.sort(keys[idxs])
+        lst = [lst[i] for i in np.argsort(keys, kind="stable")]
+        rows = []
+        for e in lst:
+            n = n_el[e]
+            k_r = int(rng.choice(_divisors(n))) if n > 0 else int(rng.integers(1, 4))
+            row, span = _random_type(rng, k_r, es, overlap_ok=False)
+            nr = n // k_r if n > 0 else 0
+            types.append(row)
+            rows.append((e, nr, len(types) - 1, (nr - 1) * row[7] + span if nr > 0 else 0))
+        place = rng.permutation(len(rows))
+        pos = 0
+        disp = [0] * len(rows)
+        for i in place:
+            pos += int(rng.integers(0, 3)) * es
+            disp[i] = pos
+            pos += rows[i][3]
+        recv_size[d] = pos + int(rng.integers(0, 3)) * es
+        for (e, nr, t, _), dp in zip(rows, disp):
+            in_src.append(out_src[e]); rcount.append(nr); rtype.append(t); rdisp.append(dp)
+    recv_base = np.zeros(P, np.int64)
+    off = int(rng.integers(0, 3)) * es
+    for d in range(P):
+        recv_base[d] = off
+        off += int(recv_size[d]) + int(rng.integers(0, 3)) * es
+    in_cnt = np.bincount(np.array([out_dst[e] for d in range(P) for e in ins[d]], np.int64), minlength=P) \
+        if E else np.zeros(P, np.int64)
+    out_cnt = np.bincount(np.array(out_src, np.int64), minlength=P) if E else np.zeros(P, np.int64)
+    types.append(contiguous_type(es))     # an unused row
+    return WPattern(
+        name=f"randw{seed}_P{P}_{dtype}_es{es}", P=P, ppn=ppn,
+        in_ptr=_ptr_from_counts(in_cnt).astype(np.int32), sources=np.array(in_src, np.int32),
+        out_ptr=_ptr_from_counts(out_cnt).astype(np.int32), dests=np.array(out_dst, np.int32),
+        sendcounts=np.array(scount, np.int32), sdispls=np.array(sdisp, np.int64),
+        sendtypes=np.array(stype, np.int32), recvcounts=np.array(rcount, np.int32),
+        rdispls=np.array(rdisp, np.int64), recvtypes=np.array(rtype, np.int32), types=np.array(types, np.int64),
+        send_base=send_base, recv_base=recv_base, sendbuf_bytes=int(sendbuf_bytes), recvbuf_bytes=int(off),
+        dtype=dtype)

@@ -444,7 +444,157 @@ def check_error_codes(lib):
     assert st["U"] == 4
 
 
-ALL_CHECKS = [check_golden_forward, check_golden_multigraph_truncate, check_golden_locality,
+# -------------------------------------------------------- all-to-all-w ----
+
+def load_wgolden(name):
+    with open(os.path.join(GOLDEN, name)) as f:
+        g = json.load(f)
+    w = pt.WPattern(
+        name=name, P=g["P"], ppn=1, in_ptr=np.array(g["in_ptr"], np.int32), sources=np.array(g["sources"], np.int32),
+        out_ptr=np.array(g["out_ptr"], np.int32), dests=np.array(g["dests"], np.int32),
+        sendcounts=np.array(g["sendcounts"], np.int32), sdispls=np.array(g["sdispls"], np.int64),
+        sendtypes=np.array(g["sendtypes"], np.int32), recvcounts=np.array(g["recvcounts"], np.int32),
+        rdispls=np.array(g["rdispls"], np.int64), recvtypes=np.array(g["recvtypes"], np.int32),
+        types=np.array(g["types"], np.int64), send_base=np.array(g["send_base"], np.int64),
+        recv_base=np.array(g["recv_base"], np.int64), sendbuf_bytes=g["sendbuf_bytes"],
+        recvbuf_bytes=g["recvbuf_bytes"], dtype="bytes")
+    return w, g
+
+
+def apply_change(w, change):
+    q = pt.WPattern(**{k: (v.copy() if isinstance(v, np.ndarray) else v) for k, v in w.__dict__.items()})
+    for k, v in change.items():
+        if k == "types_row":
+            q.types[v[0]] = v[1]
+        else:
+            setattr(q, k, np.array(v, dtype=getattr(w, k).dtype))
+    return q
+
+
+def check_w_golden(lib):
+    w, g = load_wgolden("alltoallw_vector.json")
+    sb = np.array(g["send_values"], np.uint8)
+    got = oracle.alltoallw(w, sb, np.array(g["recv_init"], np.uint8), lib=lib)
+    assert got.tolist() == g["expected_recv"], got.tolist()
+    for case in g["error_cases"]:
+        assert oracle.alltoallw_validate(apply_change(w, case["change"]), lib=lib) == case["expected"], case
+
+
+def w_brute(w, sendbuf, recv_init):
+    """The all-to-all-w written as nested loops over each type map (item, level 2,
+    level 1, level 0, byte), paired by the t-th occurrence rule read off the lists."""
+    out = np.array(recv_init, dtype=np.uint8, copy=True)
+    T = w.types
+    occ_in = {}
+    for d in range(w.P):
+        for i in range(w.in_ptr[d], w.in_ptr[d + 1]):
+            occ_in.setdefault((int(w.sources[i]), d), []).append(i)
+    seen = {}
+
+    def offsets(t, count):
+        bl, c0, c1, c2, s0, s1, s2, ext = (int(x) for x in T[t])
+        res = []
+        for it in range(count):
+            for k2 in range(c2):
+                for k1 in range(c1):
+                    for k0 in range(c0):
+                        for b in range(bl):
+                            res.append(it * ext + k2 * s2 + k1 * s1 + k0 * s0 + b)
+        return res
+    for r in range(w.P):
+        for e in range(w.out_ptr[r], w.out_ptr[r + 1]):
+            d = int(w.dests[e])
+            n = seen.get((r, d), 0)
+            seen[(r, d)] = n + 1
+            i = occ_in[(r, d)][n]
+            so = offsets(w.sendtypes[e], int(w.sendcounts[e]))
+            ro = offsets(w.recvtypes[i], int(w.recvcounts[i]))
+            assert len(so) == len(ro)
+            for a, b in zip(so, ro):
+                out[w.recv_base[d] + w.rdispls[i] + b] = sendbuf[w.send_base[r] + w.sdispls[e] + a]
+    return out
+
+
+def check_w_bruteforce_random(lib):
+    for seed in range(12):
+        w = pt.random_wpattern(seed, max_deg=3, max_items=3, max_el=6)
+        sb = pt.random_bytes(w.sendbuf_bytes, seed)
+        init = pt.random_bytes(w.recvbuf_bytes, seed + 100)
+        got = oracle.alltoallw(w, sb, init, lib=lib)
+        assert np.array_equal(got, w_brute(w, sb, init)), w.name
+        # idempotent, and the bytes received are the bytes sent
+        assert np.array_equal(oracle.alltoallw(w, sb, got, lib=lib), got)
+        assert int(w.message_bytes().sum()) == int((w.recvcounts.astype(np.int64) *
+                                                    w.type_sizes()[w.recvtypes]).sum())
+
+
+def check_w_reduces_to_v(lib):
+    """With one contiguous element type the all-to-all-w is the all-to-all-v."""
+    for seed in (1, 4, 9, 17, 23):
+        p = pt.random_pattern(seed, indexed=False)
+        w = pt.w_from_v(p)
+        sb = pt.random_bytes(p.sendbuf_bytes, seed)
+        init = pt.random_bytes(p.recvbuf_bytes, seed + 1)
+        assert np.array_equal(oracle.alltoallw(w, sb, init, lib=lib), oracle.standard(p, sb, init, lib=lib))
+        bad = pt.random_pattern(seed, indexed=False)
+        if len(bad.recvcounts):
+            bad.recvcounts = bad.recvcounts.copy()
+            bad.recvcounts[0] += 1
+            assert oracle.alltoallw_validate(pt.w_from_v(bad), lib=lib) == oracle.validate(bad, lib=lib)
+
+
+def check_w_stencil_bruteforce(lib):
+    """A stencil halo through datatypes over the point-major and the component-major
+    field equals the global grid read at the ghost coordinates."""
+    for grid, ranks, ppn, comps in (((12, 8, 8), (3, 2, 2), 4, 3), ((16, 12), (4, 3), 4, 2)):
+        for layout in ("aos", "soa"):
+            w = pt.stencil_w(grid, ranks, ppn, comps=comps, dtype="f64", layout=layout)
+            p = w.meta["v_pattern"]
+            x = pt.stencil_field(p, 13)
+            npts = int(np.prod(p.meta["blk"]))
+            xs = x if layout == "aos" else pt.soa_from_aos(x, p.P, npts, comps)
+            got = as_values(oracle.alltoallw(w, xs, lib=lib), np.float64).reshape(-1, comps)
+            exp = ghost_expected(p, x)
+            for r in range(p.P):
+                lo = p.recv_base[r] // p.elem_size
+                assert np.array_equal(got[lo: lo + len(exp[r])], exp[r]), (grid, layout, r)
+
+
+def w_forward_map(w, lib):
+    """Source payload element of every receive payload element (-1 if none), from the
+    forward on element ids (the forward is pinned by the checks above)."""
+    vt = np.float64 if w.dtype == "f64" else np.float32
+    n_send, n_recv = w.sendbuf_bytes // vt().itemsize, w.recvbuf_bytes // vt().itemsize
+    ids = np.arange(n_send, dtype=vt)
+    got = as_values(oracle.alltoallw(w, ids, np.full(n_recv, -1, vt), lib=lib), vt)
+    return got.astype(np.int64), vt
+
+
+def check_w_adjoint(lib):
+    """Backward == transpose of the forward map, exactly on integer-valued gradients;
+    accumulate adds; elements no message reads are untouched."""
+    for seed in range(20, 32):
+        w = pt.random_wpattern(seed, dtype="f64" if seed % 2 else "f32")
+        src, vt = w_forward_map(w, lib)
+        rng = np.random.default_rng(seed)
+        g = rng.integers(-8, 9, size=len(src)).astype(vt)
+        old = rng.integers(-8, 9, size=w.sendbuf_bytes // vt().itemsize).astype(vt)
+        ref = np.zeros(len(old), np.float64)
+        hit = np.zeros(len(old), bool)
+        ok = src >= 0
+        np.add.at(ref, src[ok], g[ok].astype(np.float64))
+        hit[src[ok]] = True
+        got = as_values(oracle.alltoallw_backward(w, g, old, lib=lib), vt)
+        assert np.array_equal(got[hit], ref[hit].astype(vt)), w.name
+        assert np.array_equal(got[~hit], old[~hit]), w.name
+        acc = as_values(oracle.alltoallw_backward(w, g, old, accumulate=True, lib=lib), vt)
+        assert np.array_equal(acc[hit], (old[hit] + ref[hit]).astype(vt)), w.name
+        assert np.array_equal(acc[~hit], old[~hit]), w.name
+
+
+ALL_CHECKS = [check_w_golden, check_w_bruteforce_random, check_w_reduces_to_v,
+              check_w_stencil_bruteforce, check_w_adjoint,
+              check_golden_forward, check_golden_multigraph_truncate, check_golden_locality,
               check_golden_backward_order, check_bruteforce_stencil, check_bruteforce_spmv,
               check_permutation_invariance, check_idempotent_and_untouched,
               check_closed_forms_small, check_adjoint_dense, check_accumulate_and_untouched,

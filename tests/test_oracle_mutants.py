@@ -34,6 +34,19 @@ MUTANTS = [
     ("node_blocked_groups_lost", "t1[n].group = L.u[q].b;", "t1[n].group = 0;"),
     ("overlap_unchecked", "if (rr[x].lo < rr[x - 1].hi)", "if (0)"),
     ("count_mismatch_unchecked", "if (pt->recvcounts[i] != cnt || cnt < 0)", "if (cnt < 0)"),
+    ("w_level_strides_swapped", "c1 * t->stride[1] + c0 * t->stride[0] + off",
+     "c1 * t->stride[0] + c0 * t->stride[1] + off"),
+    ("w_extent_ignored", "return item * t->extent + c2", "return item * type_size(t) + c2"),
+    ("w_level_digits_reversed",
+     "int64_t c0 = blk % t->count[0];\n    blk /= t->count[0];\n    int64_t c1 = blk % t->count[1];\n"
+     "    int64_t c2 = blk / t->count[1];",
+     "int64_t c2 = blk % t->count[2];\n    blk /= t->count[2];\n    int64_t c1 = blk % t->count[1];\n"
+     "    int64_t c0 = blk / t->count[1];"),
+    ("w_recv_through_send_type", "recvbuf[wp->recv_base[d] + wp->rdispls[i] + type_byte(Tr, b)] =",
+     "recvbuf[wp->recv_base[d] + wp->rdispls[i] + type_byte(Ts, b)] ="),
+    ("w_overlap_unchecked", "if (seen[da]) { err = ORC_ERR_OVERLAP; break; }", "if (0) { err = ORC_ERR_OVERLAP; break; }"),
+    ("w_length_unchecked", "n != (int64_t)wp->recvcounts[i] * type_size(Tr)", "0"),
+    ("w_backward_wrong_base", "t[n].val = grad_recv + da;", "t[n].val = grad_recv + (da - wp->recv_base[d]);"),
     ("dedup_by_gidx_only", "if (p->a != q->a) return p->a < q->a ? -1 : 1;\n    if (p->b != q->b) return p->b < q->b ? -1 : 1;\n    if (p->gidx",
      "if (0) return 0;\n    if (0) return 0;\n    if (p->gidx"),
 ]
