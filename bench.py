@@ -508,6 +508,32 @@ def extras(gbx, torch, p, field, halo, grad_halo, grad_field, dp, ex_std, bwd):
                            "plain": "eager launches, start+wait per exchange",
                            "fused": "startall of forward+backward: one CUDA graph"}
     del f_graph, b_graph, f_plain, b_plain
+    # the same stencil exchange through per-edge datatypes (neighbourhood all-to-all-w) over the
+    # point-major field and over a component-major copy of it, L2 flushed between repetitions
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    wres = {"standard_v_ms": _cold_ms(torch, ex_std.request, flush)}
+    for layout in ("aos", "soa"):
+        w = pt.stencil_w(tuple(p.meta["grid"]), tuple(p.meta["ranks"]), p.ppn, comps=p.meta["comps"],
+                         layout=layout)
+        npts = int(np.prod(p.meta["blk"]))
+        xs = field if layout == "aos" else \
+            field.view(p.P, npts, p.meta["comps"]).transpose(1, 2).contiguous().view(-1)
+        hw = torch.zeros_like(halo)
+        ew = gbx.WExchange(w, xs, hw)
+        ms = _cold_ms(torch, ew.request, flush)
+        ew.start()
+        ew.wait()
+        ex_std.request.start()
+        ex_std.request.wait()
+        info = ew.info()
+        wres[layout] = {"ms": ms, "user_GBps": w.user_bytes() / (ms * 1e-3) / 1e9,
+                        "algo_GBps": info["algo_bytes"] / (ms * 1e-3) / 1e9, "unit_bytes": info["elem_size"],
+                        "units": info["V"], "launches": info["launches"],
+                        "identical_to_index_list_exchange": bool(torch.equal(hw, halo))}
+        del ew, hw, xs
+        torch.cuda.empty_cache()
+    wres["l2"] = "flushed (256 MB write) before every repetition; median of 20"
+    out["alltoallw_cfg5"] = wres
     # SpMV halo (config 2), standard vs locality, L2 flushed between repetitions
     q = pt.config2()
     xs = torch.randn(q.meta["n"], device="cuda", dtype=torch.float64)
@@ -516,7 +542,6 @@ def extras(gbx, torch, p, field, halo, grad_halo, grad_field, dp, ex_std, bwd):
     dq = gbx.DevicePattern(q)
     a = gbx.Exchange(q, xs, r1, "standard", dp=dq)
     b = gbx.Exchange(q, xs, r2, "locality", dp=dq, graph=a.graph)
-    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     res = {}
     for name, ex in (("standard", a), ("locality", b)):
         ts = []

@@ -229,6 +229,54 @@ int gbx_neighbor_allgatherv_init(const void *sendbuf, int64_t sendbuf_bytes, con
                                  int64_t elem_size, int dtype, gbx_graph_t graph,
                                  const char *info, void *stream, gbx_request_t *request);
 
+/* Datatype of gbx_neighbor_alltoallw_init: a block of `blocklen` bytes repeated over three
+ * strided levels, innermost first (count[0] blocks stride[0] bytes apart form a row,
+ * count[1] rows stride[1] apart a plane, count[2] planes stride[2] apart an item), and
+ * consecutive items `extent` bytes apart.  This is an MPI hvector nested up to three times
+ * and resized to `extent`, with lower bound 0 (MPI_Type_create_subarray of a 3D block is one
+ * such type).  Size of one item = blocklen * count[0] * count[1] * count[2] bytes; its type
+ * map lists item by item, level 2, level 1, level 0, then the block's bytes in order.
+ * Every field must be >= 0 and the size at most 2^31 bytes (else GBX_ERR_ARG); an unused
+ * level has count 1. */
+typedef struct {
+    int64_t blocklen;
+    int64_t count[3];
+    int64_t stride[3];
+    int64_t extent;
+} gbx_datatype_t;
+
+/* Persistent neighbourhood all-to-all-w (MPI_Neighbor_alltoallw: the neighbourhood
+ * collectives of section 2.2 with one datatype per edge; meaning of the MPI standard).
+ * Out-edge j of rank r sends sendcounts[j] items of datatype types[sendtypes[j]], starting
+ * sdispls[j] BYTES into r's send region (send_base[r]); in-edge i of rank d receives
+ * recvcounts[i] items of types[recvtypes[i]] starting rdispls[i] bytes into d's receive
+ * region.  Matched edges (the t-th listing rule of gbx_dist_graph_create_adjacent) must
+ * carry the same number of bytes; the k-th byte of the send type map lands on the k-th byte
+ * of the receive type map.  Receive bytes no message covers are untouched.
+ *   sendcounts, sendtypes: device int[E] aligned with the destinations; sdispls: device
+ *   int64[E];  recvcounts, recvtypes: device int[E] aligned with the sources; rdispls:
+ *   device int64[E];  send_base, recv_base: device int64[P];  types: HOST array of
+ *   `ntypes` datatypes, copied at init;  dtype: payload type for a backward request
+ *   (GBX_BYTES / F32 / F64).
+ * The exchange runs as the standard form (info algorithm=standard or absent; other values
+ * give GBX_ERR_UNSUPPORTED) over units of u bytes, u the largest power of two <= 16
+ * dividing every block length, stride and extent of the table and every base and
+ * displacement.  gbx_backward_init accepts the request when u is a multiple of the payload
+ * size: each payload element then receives the sum of the gradients at the receive
+ * elements it was copied to, in (destination rank, receive address) order.
+ * Errors, the smallest code winning: GBX_ERR_ARG (null argument, bad datatype or datatype
+ * index), GBX_ERR_RANK / GBX_ERR_TRUNCATE (unmatched edges, unequal byte counts, negative
+ * counts), GBX_ERR_INDEX (negative base or displacement, a byte outside its buffer),
+ * GBX_ERR_OVERLAP (a receive byte written twice), GBX_ERR_UNSUPPORTED (more than 2^31
+ * units in a rank's send region or in total, or P and the receive buffer too large to key
+ * in 64 bits).  Nothing is launched on error. */
+int gbx_neighbor_alltoallw_init(const void *sendbuf, int64_t sendbuf_bytes, const int64_t *send_base,
+                                const int *sendcounts, const int64_t *sdispls, const int *sendtypes,
+                                void *recvbuf, int64_t recvbuf_bytes, const int64_t *recv_base,
+                                const int *recvcounts, const int64_t *rdispls, const int *recvtypes,
+                                const gbx_datatype_t *types, int ntypes, int dtype, gbx_graph_t graph,
+                                const char *info, void *stream, gbx_request_t *request);
+
 /* Persistent all-to-all-v over the emulated communicator (MPIX_Alltoallv, section 2.1,
  * Listing 2): rank r sends sendcounts[r*P + d] elements from element sdispls[r*P + d] of its
  * send region to rank d, which stores them at element rdispls[d*P + r] of its receive region

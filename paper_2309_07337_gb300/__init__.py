@@ -71,6 +71,8 @@ def lib():
                                          ctypes.c_char_p, _vp, _pvp],
         "gbx_alltoallv_init": [_vp, _vp, _i64, _vp, _vp, _vp, _vp, _i64, _vp, _vp, _vp, _i64, ctypes.c_int,
                                ctypes.c_char_p, _vp, _pvp],
+        "gbx_neighbor_alltoallw_init": [_vp, _i64, _vp, _vp, _vp, _vp, _vp, _i64, _vp, _vp, _vp, _vp,
+                                        _vp, ctypes.c_int, ctypes.c_int, _vp, ctypes.c_char_p, _vp, _pvp],
         "gbx_start": [_vp],
         "gbx_wait": [_vp],
         "gbx_test": [_vp, ctypes.POINTER(ctypes.c_int)],
@@ -282,6 +284,42 @@ def alltoallv_init(comm: Comm, sendbuf, send_base, sendcounts, sdispls, recvbuf,
     return Request(h, keep=(sendbuf, recvbuf, comm))
 
 
+class Datatype(ctypes.Structure):
+    """gbx_datatype_t: a block of `blocklen` bytes over three strided levels (innermost
+    first), items `extent` bytes apart; all in bytes (see include/gbx.h)."""
+    _fields_ = [("blocklen", ctypes.c_int64), ("count", ctypes.c_int64 * 3), ("stride", ctypes.c_int64 * 3),
+                ("extent", ctypes.c_int64)]
+
+
+def datatype_table(rows):
+    """ctypes array of Datatype from rows (blocklen, count0, count1, count2, stride0,
+    stride1, stride2, extent)."""
+    rows = [tuple(int(x) for x in r) for r in rows]
+    arr = (Datatype * max(len(rows), 1))()
+    for k, r in enumerate(rows):
+        arr[k].blocklen = r[0]
+        arr[k].count[:] = r[1:4]
+        arr[k].stride[:] = r[4:7]
+        arr[k].extent = r[7]
+    return arr, len(rows)
+
+
+def neighbor_alltoallw_init(sendbuf, send_base, sendcounts, sdispls, sendtypes, recvbuf, recv_base, recvcounts,
+                            rdispls, recvtypes, types, graph: DistGraph, dtype: int = BYTES, info: str = "",
+                            stream=None) -> Request:
+    """MPI_Neighbor_alltoallw, persistent: per-edge datatypes, byte displacements (see
+    include/gbx.h).  `types`: rows (blocklen, count0, count1, count2, stride0, stride1,
+    stride2, extent), copied at init; the per-edge arrays are device tensors."""
+    arr, n = datatype_table(types)
+    h = ctypes.c_void_p()
+    _check(lib().gbx_neighbor_alltoallw_init(
+        _ptr(sendbuf), _nbytes(sendbuf), _ptr(send_base), _ptr(sendcounts), _ptr(sdispls), _ptr(sendtypes),
+        _ptr(recvbuf), _nbytes(recvbuf), _ptr(recv_base), _ptr(recvcounts), _ptr(rdispls), _ptr(recvtypes),
+        ctypes.cast(arr, ctypes.c_void_p), int(n), int(dtype), graph.handle, info.encode() if info else None,
+        _stream_handle(stream), ctypes.byref(h)), "neighbor_alltoallw_init")
+    return Request(h, keep=(sendbuf, recvbuf, graph))
+
+
 def _handles(reqs: Sequence[Request]):
     arr = (ctypes.c_void_p * len(reqs))(*[r.handle.value for r in reqs])
     return arr
@@ -334,6 +372,47 @@ class Exchange:
             dp.rdispls, self.graph, p.elem_size, DTYPE_CODES[p.dtype],
             send_slot_ptr=dp.send_slot_ptr, send_idx=dp.send_idx, recv_slot_ptr=dp.recv_slot_ptr,
             global_sidx=dp.global_sidx, global_ridx=dp.global_ridx, info=full, stream=stream)
+
+    def start(self):
+        self.request.start()
+
+    def wait(self):
+        self.request.wait()
+
+    def info(self):
+        return self.request.info()
+
+
+class DeviceWPattern:
+    """A patterns.WPattern's per-edge and per-rank arrays uploaded to the GPU."""
+
+    FIELDS = (("in_ptr", "int32"), ("sources", "int32"), ("out_ptr", "int32"), ("dests", "int32"),
+              ("sendcounts", "int32"), ("sdispls", "int64"), ("sendtypes", "int32"),
+              ("recvcounts", "int32"), ("rdispls", "int64"), ("recvtypes", "int32"),
+              ("send_base", "int64"), ("recv_base", "int64"))
+
+    def __init__(self, w, device="cuda"):
+        import numpy as np
+        import torch
+        self.w = w
+        for name, dt in self.FIELDS:
+            setattr(self, name, torch.from_numpy(np.ascontiguousarray(getattr(w, name), dtype=dt)).to(device))
+
+
+class WExchange:
+    """Communicator + graph + persistent all-to-all-w request for one WPattern."""
+
+    def __init__(self, w, sendbuf, recvbuf, info="", dw: DeviceWPattern = None, stream=None,
+                 graph: DistGraph = None):
+        self.w = w
+        self.dw = dw or DeviceWPattern(w)
+        self.comm = graph.comm if graph is not None else Comm(w.P, w.ppn)
+        self.graph = graph or DistGraph(self.comm, self.dw.in_ptr, self.dw.sources, self.dw.out_ptr,
+                                        self.dw.dests, stream)
+        d = self.dw
+        self.request = neighbor_alltoallw_init(
+            sendbuf, d.send_base, d.sendcounts, d.sdispls, d.sendtypes, recvbuf, d.recv_base, d.recvcounts,
+            d.rdispls, d.recvtypes, w.types, self.graph, DTYPE_CODES[w.dtype], info=info, stream=stream)
 
     def start(self):
         self.request.start()

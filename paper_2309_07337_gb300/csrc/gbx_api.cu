@@ -738,6 +738,40 @@ extern "C" int gbx_neighbor_alltoallv_init(const void *sendbuf, int64_t sendbuf_
     return GBX_SUCCESS;
 }
 
+extern "C" int gbx_neighbor_alltoallw_init(const void *sendbuf, int64_t sendbuf_bytes, const int64_t *send_base,
+                                           const int *sendcounts, const int64_t *sdispls, const int *sendtypes,
+                                           void *recvbuf, int64_t recvbuf_bytes, const int64_t *recv_base,
+                                           const int *recvcounts, const int64_t *rdispls, const int *recvtypes,
+                                           const gbx_datatype_t *types, int ntypes, int dtype, gbx_graph_t graph,
+                                           const char *info, void *stream, gbx_request_t *request) {
+    if (!request) return GBX_ERR_ARG;
+    *request = nullptr;
+    if (!graph || sendbuf_bytes < 0 || recvbuf_bytes < 0 || ntypes < 0 || (ntypes > 0 && !types)) return GBX_ERR_ARG;
+    if (dtype != GBX_BYTES && dtype != GBX_F32 && dtype != GBX_F64) return GBX_ERR_ARG;
+    if ((sendbuf_bytes > 0 && !sendbuf) || (recvbuf_bytes > 0 && !recvbuf)) return GBX_ERR_ARG;
+    if (!send_base || !recv_base) return GBX_ERR_ARG;
+    if (graph->E > 0 && (!sendcounts || !sdispls || !sendtypes || !recvcounts || !rdispls || !recvtypes))
+        return GBX_ERR_ARG;
+    Opts o = parse_info(info);
+    if (!o.ok) return GBX_ERR_ARG;
+    if (o.algorithm != GBX_ALG_STANDARD || o.algorithm_auto) return GBX_ERR_UNSUPPORTED;
+    gbx_request_s *req = new_request(o, stream);
+    if (!req->done) { destroy_request(req); return GBX_ERR_CUDA; }
+    req->kind = 0;
+    req->graph = graph;
+    req->src = (const char *)sendbuf;
+    req->dst = (char *)recvbuf;
+    req->src_bytes = sendbuf_bytes;
+    req->dst_bytes = recvbuf_bytes;
+    req->dtype = dtype;
+    int rc = gbx_setup_alltoallw(req, send_base, sendcounts, sdispls, sendtypes, recv_base, recvcounts, rdispls,
+                                 recvtypes, types, ntypes);
+    if (rc == GBX_SUCCESS) rc = finalize(req);
+    if (rc != GBX_SUCCESS) { destroy_request(req); return rc; }
+    *request = req;
+    return GBX_SUCCESS;
+}
+
 extern "C" int gbx_backward_init(gbx_request_t forward, const void *grad_recv, void *grad_send, int accumulate,
                                  const char *info, void *stream, gbx_request_t *request) {
     if (!request) return GBX_ERR_ARG;

@@ -264,6 +264,9 @@ int gbx_setup_forward(gbx_request_s *req, const int64_t *send_base, const int *s
                       const int64_t *recv_slot_ptr, const int64_t *global_sidx,
                       const int64_t *global_ridx, int want_locality);
 int gbx_setup_backward(gbx_request_s *bwd, int accumulate);
+int gbx_setup_alltoallw(gbx_request_s *req, const int64_t *send_base, const int *sendcounts, const int64_t *sdispls,
+                        const int *sendtypes, const int64_t *recv_base, const int *recvcounts, const int64_t *rdispls,
+                        const int *recvtypes, const gbx_datatype_t *types, int ntypes);
 int gbx_graph_setup(gbx_graph_s *g, int64_t n_in, const int *in_ptr, const int *sources,
                     int64_t n_out, const int *out_ptr, const int *dests, cudaStream_t st);
 int gbx_make_copy_op(gbx_request_s *req, int level, const char *src, int src_role, char *dst,
