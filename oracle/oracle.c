@@ -25,7 +25,9 @@
  *    send_idx[q] of r's region instead of element q.
  *  * Section 2.2, last paragraph: the locality-aware variant takes a unique global index
  *    for every value sent and received, so that one value crosses a given pair of nodes
- *    only once.
+ *    only once.  When the caller gives none, a value is named by its source element (its
+ *    byte offset in the send buffer): distinct elements stay distinct, and an element
+ *    sent to several ranks of one node still crosses that node pair once.
  *  * Section 1: locality-aware aggregation sends inter-node traffic as one aggregated
  *    message per pair of nodes.  The steps followed here (the paper cites but does not
  *    print them): intra-node blocks are copied directly; every inter-node value is
@@ -339,7 +341,7 @@ static void loc_free(loc_t *L) {
 /* Builds the deduplicated aggregate layout and the statistics. */
 static int loc_build(const orc_pattern *pt, const uint8_t *sendbuf, loc_t *L) {
     memset(L, 0, sizeof(*L));
-    if (!pt || !pt->global_sidx) return ORC_ERR_ARG;
+    if (!pt) return ORC_ERR_ARG;
     int err = prepare(pt, &L->match);
     if (err) return err;
     int64_t s = pt->elem_size;
@@ -363,10 +365,11 @@ static int loc_build(const orc_pattern *pt, const uint8_t *sendbuf, loc_t *L) {
             for (int64_t k = 0; k < pt->sendcounts[e]; k++) {
                 xrec_t *x = &L->x[n++];
                 int64_t q = pt->sdispls[e] + k;
-                x->gidx = pt->global_sidx[pt->send_slot_ptr[r] + q];
+                x->src_off = pt->send_base[r] + send_elem(pt, r, q) * s;
+                /* without global indices a value is named by its source element */
+                x->gidx = pt->global_sidx ? pt->global_sidx[pt->send_slot_ptr[r] + q] : x->src_off;
                 x->a = node_of(pt, r); x->b = node_of(pt, d); x->r = r; x->d = d;
                 x->e = e; x->k = k;
-                x->src_off = pt->send_base[r] + send_elem(pt, r, q) * s;
                 x->p = pt->rdispls[i] + k;
                 x->recv_off = pt->recv_base[d] + x->p * s;
             }

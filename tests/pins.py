@@ -444,6 +444,40 @@ def check_error_codes(lib):
     assert st["U"] == 4
 
 
+# ------------------------------------------- locality without global indices ----
+
+def check_locality_names_values_by_source_element(lib):
+    """Without global indices a value is its source element: for generator patterns whose
+    indices name source elements, dropping them changes no byte, no statistic and no
+    aggregate layout; an element sent to every rank of a node crosses the node pair once."""
+    for seed in (2, 5, 7, 12, 19, 33):
+        p = pt.random_pattern(seed, indexed=bool(seed % 2))
+        if p.global_sidx is None:
+            continue
+        q = types.SimpleNamespace(**{k: getattr(p, k) for k in p.__dataclass_fields__})
+        q.global_sidx = q.global_ridx = None
+        if p.send_idx is None:
+            q.send_slot_ptr = None
+        x = pt.random_bytes(p.sendbuf_bytes, seed)
+        a, sa = oracle.locality(p, x, lib=lib)
+        b, sb = oracle.locality(q, x, lib=lib)
+        assert np.array_equal(a, b) and sa == sb, (seed, sa, sb)
+        la, lb = oracle.locality_layout(p, lib=lib), oracle.locality_layout(q, lib=lib)
+        assert all(np.array_equal(la[j], lb[j]) for j in (0, 1, 3)), seed
+    # rank 0 sends its elements 0..2 to every rank of node 1 (ranks 4..7), ppn 4
+    star = types.SimpleNamespace(
+        P=8, ppn=4, in_ptr=np.array([0, 0, 0, 0, 0, 1, 2, 3, 4], np.int32), sources=np.zeros(4, np.int32),
+        out_ptr=np.array([0, 4, 4, 4, 4, 4, 4, 4, 4], np.int32), dests=np.array([4, 5, 6, 7], np.int32),
+        sendcounts=np.full(4, 3, np.int32), sdispls=np.zeros(4, np.int32), recvcounts=np.full(4, 3, np.int32),
+        rdispls=np.zeros(4, np.int32), send_base=np.zeros(8, np.int64), recv_base=np.arange(8, dtype=np.int64) * 24,
+        send_slot_ptr=None, send_idx=None, recv_slot_ptr=None, global_sidx=None, global_ridx=None,
+        elem_size=8, sendbuf_bytes=24, recvbuf_bytes=192)
+    x = np.array([1.5, -2.0, 4.25])
+    got, st = oracle.locality(star, x, lib=lib)
+    assert st["V"] == 12 and st["V_inter"] == 12 and st["U"] == 3 and st["node_pairs"] == 1, st
+    assert np.array_equal(as_values(got, np.float64)[12:], np.tile(x, 4))
+
+
 # -------------------------------------------------------- all-to-all-w ----
 
 def load_wgolden(name):
@@ -592,7 +626,7 @@ def check_w_adjoint(lib):
         assert np.array_equal(acc[~hit], old[~hit]), w.name
 
 
-ALL_CHECKS = [check_w_golden, check_w_bruteforce_random, check_w_reduces_to_v,
+ALL_CHECKS = [check_locality_names_values_by_source_element, check_w_golden, check_w_bruteforce_random, check_w_reduces_to_v,
               check_w_stencil_bruteforce, check_w_adjoint,
               check_golden_forward, check_golden_multigraph_truncate, check_golden_locality,
               check_golden_backward_order, check_bruteforce_stencil, check_bruteforce_spmv,

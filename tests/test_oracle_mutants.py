@@ -47,6 +47,8 @@ MUTANTS = [
     ("w_overlap_unchecked", "if (seen[da]) { err = ORC_ERR_OVERLAP; break; }", "if (0) { err = ORC_ERR_OVERLAP; break; }"),
     ("w_length_unchecked", "n != (int64_t)wp->recvcounts[i] * type_size(Tr)", "0"),
     ("w_backward_wrong_base", "t[n].val = grad_recv + da;", "t[n].val = grad_recv + (da - wp->recv_base[d]);"),
+    ("values_named_by_send_slot", "pt->global_sidx[pt->send_slot_ptr[r] + q] : x->src_off;",
+     "pt->global_sidx[pt->send_slot_ptr[r] + q] : q;"),
     ("dedup_by_gidx_only", "if (p->a != q->a) return p->a < q->a ? -1 : 1;\n    if (p->b != q->b) return p->b < q->b ? -1 : 1;\n    if (p->gidx",
      "if (0) return 0;\n    if (0) return 0;\n    if (p->gidx"),
 ]
