@@ -393,6 +393,58 @@ def _time_loop(torch, fn, reps):
     return (time.perf_counter() - t) / reps * 1e3
 
 
+def _dense_and_allgather(gbx, torch, p5, flush):
+    res = {}
+    P, ppn, c, s = 1024, 32, 4, 64
+    r = np.arange(P, dtype=np.int64)
+    sd = np.tile(r * c, P)                       # sdispls[r*P + d] = d*c
+    rd = np.tile(r * c, P)                       # rdispls[d*P + src] = src*c
+    cnt = np.full(P * P, c, np.int32)
+    t32 = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.int32)).cuda()
+    base = torch.from_numpy(r * P * c * s).cuda()
+    comm = gbx.Comm(P, ppn)
+    send = torch.randint(0, 256, (P * P * c * s,), dtype=torch.uint8, device="cuda")
+    recvs = {}
+    for alg in ("standard", "locality"):
+        recvs[alg] = torch.zeros_like(send)
+        req = gbx.alltoallv_init(comm, send, base, t32(cnt), t32(sd), recvs[alg], base, t32(cnt), t32(rd), s,
+                                 gbx.BYTES, info=f"algorithm={alg}")
+        ms = _cold_ms(torch, req, flush)
+        info = req.info()
+        res[alg] = {"ms": ms, "user_GBps": 2 * P * P * c * s / (ms * 1e-3) / 1e9,
+                    "algo_GBps": info["algo_bytes"] / (ms * 1e-3) / 1e9, "launches": info["launches"],
+                    "U": info["U"], "node_pairs": info["node_pairs"]}
+        del req
+    res["identical"] = bool(torch.equal(recvs["standard"], recvs["locality"]))
+    res["workload"] = f"P={P}, {ppn} per node, {c} points of {s} bytes per rank pair"
+    del recvs, send
+    # neighbourhood allgather on the stencil graph
+    dq = gbx.DevicePattern(p5)
+    g = gbx.DistGraph(gbx.Comm(p5.P, p5.ppn), dq.in_ptr, dq.sources, dq.out_ptr, dq.dests)
+    n, es = 128, 64
+    deg_in = np.diff(p5.in_ptr)
+    sbase = torch.from_numpy(np.arange(p5.P, dtype=np.int64) * n * es).cuda()
+    rbase = torch.from_numpy(np.concatenate([[0], np.cumsum(deg_in)[:-1]]).astype(np.int64) * n * es).cuda()
+    send = torch.randint(0, 256, (p5.P * n * es,), dtype=torch.uint8, device="cuda")
+    ag = {}
+    outs = {}
+    for alg in ("standard", "locality"):
+        outs[alg] = torch.zeros(int(deg_in.sum()) * n * es, dtype=torch.uint8, device="cuda")
+        req = gbx.neighbor_allgather_init(send, sbase, outs[alg], rbase, n, g, es, info=f"algorithm={alg}")
+        ms = _cold_ms(torch, req, flush)
+        info = req.info()
+        ag[alg] = {"ms": ms, "user_GBps": 2 * info["V"] * es / (ms * 1e-3) / 1e9,
+                   "algo_GBps": info["algo_bytes"] / (ms * 1e-3) / 1e9, "V": info["V"], "V_inter": info["V_inter"],
+                   "U": info["U"], "launches": info["launches"]}
+        del req
+    ag["identical"] = bool(torch.equal(outs["standard"], outs["locality"]))
+    ag["workload"] = f"27-point stencil graph P={p5.P}, {p5.ppn} per node, {n} points of {es} bytes per rank"
+    res["allgather_stencil"] = ag
+    del outs, send, g, dq
+    torch.cuda.empty_cache()
+    return res
+
+
 def extras(gbx, torch, p, field, halo, grad_halo, grad_field, dp, ex_std, bwd):
     out = {}
     # start -> wait latency on the L2-resident config 1 (2D 5-point halo, 3,072 elements)
@@ -534,6 +586,11 @@ def extras(gbx, torch, p, field, halo, grad_halo, grad_field, dp, ex_std, bwd):
         torch.cuda.empty_cache()
     wres["l2"] = "flushed (256 MB write) before every repetition; median of 20"
     out["alltoallw_cfg5"] = wres
+    # dense all-to-all-v over the emulated communicator (P = 1024, 32 per node, 4 points of
+    # 64 bytes per rank pair) and the neighbourhood allgather on the stencil graph (128 points
+    # of 64 bytes per rank to each of its neighbours): standard vs locality-aware form, whose
+    # values are named by their source elements (an allgathered point crosses a node pair once)
+    out["alltoallv_dense"] = _dense_and_allgather(gbx, torch, p, flush)
     # SpMV halo (config 2), standard vs locality, L2 flushed between repetitions
     q = pt.config2()
     xs = torch.randn(q.meta["n"], device="cuda", dtype=torch.float64)

@@ -160,8 +160,11 @@ int gbx_graph_free(gbx_graph_t *graph);
  *   elem_size                  bytes per element (any positive size)
  *   dtype                      GBX_BYTES, GBX_F32 or GBX_F64; only the backward uses it
  *   global_sidx, global_ridx   unique global index of every send / receive slot (int64;
- *                              section 2.2, last paragraph).  global_sidx is required by
- *                              the locality form; global_ridx is optional and, when
+ *                              section 2.2, last paragraph), or NULL.  The locality form
+ *                              aggregates by it; without it a value is named by its
+ *                              source element (its byte offset in the send buffer), so an
+ *                              element sent to several ranks of one remote node crosses
+ *                              that node pair once.  global_ridx is optional and, when
  *                              given, must equal the paired send index (GBX_ERR_GIDX).
  *                              The same global index sent by two ranks of one node to
  *                              the same remote node must carry identical bytes: it is
@@ -169,7 +172,7 @@ int gbx_graph_free(gbx_graph_t *graph);
  *   graph, info, stream, request
  *   info: "key=value;..." with
  *       algorithm=standard|locality|auto   (default standard; auto times both and keeps
- *                                          the faster; needs global_sidx)
+ *                                          the faster)
  *       graph=0|1          capture the start sequence in a CUDA graph (default 1)
  *       autotune=0|1       time candidate kernel shapes at init (default 1)
  *       vec=V block=B      force the move kernel's vector width / block size
@@ -202,8 +205,9 @@ int gbx_neighbor_alltoallv_init(const void *sendbuf, int64_t sendbuf_bytes,
  * its persistent neighbourhood collectives as drop-in replacements of the MPI calls,
  * section 2.2; their meaning is the MPI standard's).  Each derives per-edge counts and
  * displacements on the device from the graph, then behaves as gbx_neighbor_alltoallv_init
- * with user-packed buffers and no global indices (so the standard form runs; the other info
- * keys apply as there).  `count` / `sendcount` are in elements.
+ * with user-packed buffers and no global indices (info keys apply as there; with
+ * algorithm=locality a value is named by its source element, so the allgathers send each
+ * element once per remote node).  `count` / `sendcount` are in elements.
  *   neighbor_alltoall:   rank r sends `count` elements to its j-th out-neighbour from element
  *                        j*count of its send region; rank d receives `count` elements from its
  *                        i-th in-neighbour at element i*count of its receive region.
@@ -282,7 +286,9 @@ int gbx_neighbor_alltoallw_init(const void *sendbuf, int64_t sendbuf_bytes, cons
  * send region to rank d, which stores them at element rdispls[d*P + r] of its receive region
  * (recvcounts[d*P + r] must match).  All four arrays are device int[P*P], row-major by rank.
  * The library builds the complete graph (every rank, itself included, in rank order) and
- * frees it with the request.  Other arguments as gbx_neighbor_alltoallv_init. */
+ * frees it with the request.  Other arguments as gbx_neighbor_alltoallv_init; with
+ * info algorithm=locality the dense traffic takes the locality-aware form (one aggregate
+ * per node pair, values named by their source elements). */
 int gbx_alltoallv_init(gbx_comm_t comm, const void *sendbuf, int64_t sendbuf_bytes,
                        const int64_t *send_base, const int *sendcounts, const int *sdispls,
                        void *recvbuf, int64_t recvbuf_bytes, const int64_t *recv_base,

@@ -701,7 +701,6 @@ extern "C" int gbx_neighbor_alltoallv_init(const void *sendbuf, int64_t sendbuf_
     if (global_ridx && (!recv_slot_ptr || !global_sidx)) return GBX_ERR_ARG;
     Opts o = parse_info(info);
     if (!o.ok) return GBX_ERR_ARG;
-    if ((o.algorithm == GBX_ALG_LOCALITY || o.algorithm_auto) && !global_sidx) return GBX_ERR_ARG;
 
     auto build = [&](int locality, gbx_request_s **out) -> int {
         gbx_request_s *req = new_request(o, stream);

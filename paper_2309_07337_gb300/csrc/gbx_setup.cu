@@ -322,7 +322,14 @@ __device__ __forceinline__ void inter_elem(const FwdArgs &a, const int64_t *w0, 
     const int64_t q = seg_of_inedge[i];
     const int r = a.out_owner[e], d = a.in_owner[i];
     *v = segv0[q] + k;
-    *g = a.global_sidx[a.send_slot_ptr[r] + a.sdispls[e] + k];
+    const int64_t slot = a.sdispls[e] + k;
+    if (a.global_sidx) {
+        *g = a.global_sidx[a.send_slot_ptr[r] + slot];
+    } else {
+        // no global indices: a value is named by its source element (its byte offset)
+        const int64_t el = a.send_idx ? (int64_t)a.send_idx[a.send_slot_ptr[r] + slot] : slot;
+        *g = a.send_base[r] + el * a.s;
+    }
     *pair = (int64_t)(r / a.ppn) * a.nnodes + (d / a.ppn);
 }
 
@@ -640,7 +647,6 @@ int gbx_setup_forward(gbx_request_s *req, const int64_t *send_base, const int *s
 
     // ------------------------------------------------------------ locality form
     req->algorithm = GBX_ALG_LOCALITY;
-    if (!global_sidx || !send_slot_ptr) return GBX_ERR_ARG;
     Seg *seg0 = nullptr, *seg3 = nullptr;
     GBX_TRY(req->mem.get(&seg0, n0));
     GBX_TRY(req->mem.get(&seg3, n3));

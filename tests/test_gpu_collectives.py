@@ -77,6 +77,17 @@ def test_neighbor_alltoall_and_allgather(seed, kind):
     r.start()
     r.wait()
     assert_bytes_equal(recv.cpu().numpy(), want, f"{kind} seed {seed}")
+    # locality-aware form: values named by their source elements, so an allgather sends each
+    # element once per remote node; same bytes, the oracle's statistics
+    recv2 = torch.from_numpy(init.copy()).cuda()
+    r2 = f(send, sb, recv2, rb, count, g, s, info="algorithm=locality")
+    r2.start()
+    r2.wait()
+    assert_bytes_equal(recv2.cpu().numpy(), want, f"{kind} seed {seed} locality")
+    st = oracle.locality_stats(q)
+    i = r2.info()
+    assert {k: i[k] for k in ("U", "node_pairs", "V_inter", "msgs_step1", "msgs_step3")} == \
+        {k: st[k] for k in ("U", "node_pairs", "V_inter", "msgs_step1", "msgs_step3")}
     del out_owner, in_owner
 
 
@@ -161,3 +172,53 @@ def test_dense_alltoallv(P, ppn):
     b.start()
     b.wait()
     assert_bytes_equal(gx.cpu().numpy(), oracle.backward(p, g.cpu().numpy(), form=0), f"alltoallv backward P={P}")
+
+    # locality-aware dense traffic: one aggregate per node pair; the reverse follows the
+    # three steps (node-blocked order)
+    recv2 = torch.zeros_like(recv)
+    r2 = gbx.alltoallv_init(comm, send, torch.from_numpy(p.send_base).cuda(), t32(p.sendcounts), t32(p.sdispls),
+                            recv2, torch.from_numpy(p.recv_base).cuda(), t32(p.recvcounts), t32(p.rdispls), s,
+                            gbx.F64, info="algorithm=locality")
+    r2.start()
+    r2.wait()
+    assert_bytes_equal(recv2.cpu().numpy(), want, f"alltoallv locality P={P}")
+    st = oracle.locality_stats(p)
+    assert r2.info()["U"] == st["U"] and r2.info()["node_pairs"] == st["node_pairs"]
+    gx2 = torch.zeros_like(send)
+    b2 = gbx.backward_init(r2, g, gx2)
+    b2.start()
+    b2.wait()
+    assert_bytes_equal(gx2.cpu().numpy(), oracle.backward(p, g.cpu().numpy(), form=1),
+                       f"alltoallv locality backward P={P}")
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_locality_without_global_indices(seed):
+    """Index-list exchanges given no global indices: the locality form names values by
+    their source elements (repeated elements are aggregated once per node pair)."""
+    p = pt.random_pattern(700 + seed, dtype="f64" if seed % 2 else "f32")
+    q = pt.Pattern(**{k: getattr(p, k) for k in p.__dataclass_fields__})
+    q.global_sidx = q.global_ridx = None
+    if q.send_idx is None:
+        q.send_slot_ptr = None
+    rng = np.random.default_rng(seed)
+    vt = np.float64 if p.dtype == "f64" else np.float32
+    x = rng.standard_normal(p.sendbuf_bytes // np.dtype(vt).itemsize).astype(vt)
+    want, st = oracle.locality(q, x)
+    dq = gbx.DevicePattern(q)
+    send = torch.from_numpy(x).cuda()
+    recv = torch.zeros(max(p.recvbuf_bytes, 1) // np.dtype(vt).itemsize, dtype=send.dtype, device="cuda")
+    recv = recv[: p.recvbuf_bytes // np.dtype(vt).itemsize]
+    ex = gbx.Exchange(q, send, recv, "locality", dp=dq)
+    ex.start()
+    ex.wait()
+    assert_bytes_equal(recv.cpu().numpy(), want, q.name)
+    i = ex.info()
+    for k in ("U", "node_pairs", "V_direct", "V_inter", "msgs_step1", "msgs_step3"):
+        assert i[k] == st[k], (k, i[k], st[k])
+    g = rng.standard_normal(len(recv)).astype(vt)
+    gx = torch.zeros_like(send)
+    b = gbx.backward_init(ex.request, torch.from_numpy(g).cuda(), gx)
+    b.start()
+    b.wait()
+    assert_bytes_equal(gx.cpu().numpy(), oracle.backward(q, g, form=1), q.name + " backward")
