@@ -15,7 +15,10 @@ follows, from "MPI Advance: Open-Source Message Passing Optimizations" (arXiv
     summation orders (orc_backward);
   * the neighbourhood all-to-all-w (section 2.2's neighbourhood collectives with one
     datatype per edge, MPI standard meaning) and its reverse (orc_alltoallw,
-    orc_alltoallw_backward).
+    orc_alltoallw_backward);
+  * the partitioned (early-bird) exchange of section 2.3: the state after a subset of
+    send partitions has moved, and which receive partitions have arrived
+    (orc_standard_partial, orc_arrived).
 
 Parity is pinned by tests/test_oracle_pins.py against brute-force global indexing,
 hand-worked golden cases, invariants and closed-form counts.  The backward's bit
@@ -104,6 +107,10 @@ def load(path: str | None = None):
     lib.orc_alltoallw_validate.argtypes = [W]
     lib.orc_alltoallw.argtypes = [W, vp, vp]
     lib.orc_alltoallw_backward.argtypes = [W, ctypes.c_int, ctypes.c_int, vp, vp]
+    lib.orc_standard_partial.argtypes = [P, ctypes.c_int, vp, vp, vp, vp]
+    lib.orc_arrived.argtypes = [P, ctypes.c_int, vp, vp, ctypes.c_int, vp, vp]
+    for f in ("orc_standard_partial", "orc_arrived"):
+        getattr(lib, f).restype = ctypes.c_int
     for f in ("orc_match", "orc_validate", "orc_standard", "orc_locality",
               "orc_locality_stats", "orc_locality_layout", "orc_backward",
               "orc_alltoallw_validate", "orc_alltoallw", "orc_alltoallw_backward"):
@@ -305,6 +312,38 @@ def alltoallw_backward(w, grad_recv, grad_send=None, accumulate=False, dtype=Non
         np.array(np.ascontiguousarray(grad_send).view(np.uint8).reshape(-1), copy=True)
     rc = lib.orc_alltoallw_backward(m.ref(), DTYPES[dtype or w.dtype], int(bool(accumulate)),
                                     gr.ctypes.data if gr.size else None, out.ctypes.data if out.size else None)
+    if rc:
+        raise OracleError(rc)
+    return out
+
+
+def standard_partial(p, part_ptr, ready, sendbuf, recvbuf=None, lib=None):
+    """Standard exchange restricted to elements whose source lies in a ready send
+    partition (part_ptr: byte boundaries, ready: one flag per partition)."""
+    lib = lib or load()
+    m = _Marshalled(p)
+    _, sb = _bytes_view(sendbuf)
+    out = np.zeros(int(p.recvbuf_bytes), dtype=np.uint8) if recvbuf is None else \
+        np.array(np.ascontiguousarray(recvbuf).view(np.uint8).reshape(-1), copy=True)
+    pp = np.ascontiguousarray(part_ptr, dtype=np.int64)
+    rd = np.ascontiguousarray(ready, dtype=np.uint8)
+    rc = lib.orc_standard_partial(m.ref(), len(pp) - 1, pp.ctypes.data, rd.ctypes.data,
+                                  sb.ctypes.data if sb.size else None, out.ctypes.data if out.size else None)
+    if rc:
+        raise OracleError(rc)
+    return out
+
+
+def arrived(p, part_ptr, ready, rpart_ptr, lib=None):
+    """Per receive partition: 1 when all of its values come from ready send partitions."""
+    lib = lib or load()
+    m = _Marshalled(p)
+    pp = np.ascontiguousarray(part_ptr, dtype=np.int64)
+    rpp = np.ascontiguousarray(rpart_ptr, dtype=np.int64)
+    rd = np.ascontiguousarray(ready, dtype=np.uint8)
+    out = np.zeros(len(rpp) - 1, dtype=np.uint8)
+    rc = lib.orc_arrived(m.ref(), len(pp) - 1, pp.ctypes.data, rd.ctypes.data, len(rpp) - 1, rpp.ctypes.data,
+                         out.ctypes.data)
     if rc:
         raise OracleError(rc)
     return out

@@ -887,3 +887,99 @@ int orc_alltoallw_backward(const orc_wpattern *wp, int dtype, int accumulate, co
     free(match);
     return ORC_OK;
 }
+
+/* ------------------------------------------------------ partitioned exchange --- */
+
+/* Partitioned communication (section 2.3): a persistent exchange whose send buffer is cut
+ * into partitions that the producer marks ready one by one; each ready partition's data
+ * may move before the rest of the buffer exists ("early-bird"), and a receive partition
+ * is complete once every value landing in it has arrived.  Partition p of the send buffer
+ * is the byte range [part_ptr[p], part_ptr[p+1]); the pointers start at 0, never decrease
+ * and end at the buffer's size, and no element may straddle a boundary (else ARG).  The
+ * same holds for receive partitions over the receive buffer. */
+static int check_parts(int n, const int64_t *ptr, int64_t bytes) {
+    if (n < 1 || !ptr || ptr[0] != 0 || ptr[n] != bytes) return ORC_ERR_ARG;
+    for (int p = 0; p < n; p++)
+        if (ptr[p + 1] < ptr[p]) return ORC_ERR_ARG;
+    return ORC_OK;
+}
+
+/* The partition holding bytes [off, off + s), or -1 when they straddle a boundary. */
+static int part_of(int n, const int64_t *ptr, int64_t off, int64_t s) {
+    for (int p = 0; p < n; p++)
+        if (ptr[p] <= off && off < ptr[p + 1]) return off + s <= ptr[p + 1] ? p : -1;
+    return -1;
+}
+
+/* Every element's (send partition, receive partition); -1 entries make the call fail. */
+static int part_scan(const orc_pattern *pt, const int64_t *match, int npart, const int64_t *part_ptr, int nrpart,
+                     const int64_t *rpart_ptr, int *sp, int *rp) {
+    int64_t s = pt->elem_size, n = 0;
+    for (int r = 0; r < pt->P; r++)
+        for (int64_t e = pt->out_ptr[r]; e < pt->out_ptr[r + 1]; e++) {
+            int d = pt->dests[e];
+            int64_t i = match[e];
+            for (int64_t k = 0; k < pt->sendcounts[e]; k++, n++) {
+                int64_t src = pt->send_base[r] + send_elem(pt, r, pt->sdispls[e] + k) * s;
+                int64_t dst = pt->recv_base[d] + (pt->rdispls[i] + k) * s;
+                sp[n] = part_of(npart, part_ptr, src, s);
+                rp[n] = rpart_ptr ? part_of(nrpart, rpart_ptr, dst, s) : 0;
+                if (sp[n] < 0 || rp[n] < 0) return ORC_ERR_ARG;
+            }
+        }
+    return ORC_OK;
+}
+
+/* The exchange after the partitions with ready[p] != 0 have moved: a receive element is
+ * written when its source element lies in a ready partition, else left as it was. */
+int orc_standard_partial(const orc_pattern *pt, int npart, const int64_t *part_ptr, const uint8_t *ready,
+                         const uint8_t *sendbuf, uint8_t *recvbuf) {
+    int64_t *match = NULL;
+    int err = prepare(pt, &match);
+    if (err) return err;
+    if (check_parts(npart, part_ptr, pt->sendbuf_bytes)) { free(match); return ORC_ERR_ARG; }
+    int64_t V = 0;
+    for (int64_t e = 0; e < pt->out_ptr[pt->P]; e++) V += pt->sendcounts[e];
+    int *sp = malloc(sizeof(int) * (V ? V : 1)), *rp = malloc(sizeof(int) * (V ? V : 1));
+    if (!sp || !rp) { free(sp); free(rp); free(match); return ORC_ERR_NOMEM; }
+    err = part_scan(pt, match, npart, part_ptr, 0, NULL, sp, rp);
+    int64_t s = pt->elem_size, n = 0;
+    for (int r = 0; r < pt->P && !err; r++)
+        for (int64_t e = pt->out_ptr[r]; e < pt->out_ptr[r + 1]; e++) {
+            int d = pt->dests[e];
+            int64_t i = match[e];
+            for (int64_t k = 0; k < pt->sendcounts[e]; k++, n++) {
+                if (!ready[sp[n]]) continue;
+                int64_t src = pt->send_base[r] + send_elem(pt, r, pt->sdispls[e] + k) * s;
+                int64_t dst = pt->recv_base[d] + (pt->rdispls[i] + k) * s;
+                memcpy(recvbuf + dst, sendbuf + src, (size_t)s);
+            }
+        }
+    free(sp); free(rp); free(match);
+    return err;
+}
+
+/* arrived[j] = 1 when every element received into receive partition j comes from a ready
+ * send partition (a partition that receives nothing has arrived). */
+int orc_arrived(const orc_pattern *pt, int npart, const int64_t *part_ptr, const uint8_t *ready, int nrpart,
+                const int64_t *rpart_ptr, uint8_t *arrived) {
+    int64_t *match = NULL;
+    int err = prepare(pt, &match);
+    if (err) return err;
+    if (check_parts(npart, part_ptr, pt->sendbuf_bytes) || check_parts(nrpart, rpart_ptr, pt->recvbuf_bytes)) {
+        free(match);
+        return ORC_ERR_ARG;
+    }
+    int64_t V = 0;
+    for (int64_t e = 0; e < pt->out_ptr[pt->P]; e++) V += pt->sendcounts[e];
+    int *sp = malloc(sizeof(int) * (V ? V : 1)), *rp = malloc(sizeof(int) * (V ? V : 1));
+    if (!sp || !rp) { free(sp); free(rp); free(match); return ORC_ERR_NOMEM; }
+    err = part_scan(pt, match, npart, part_ptr, nrpart, rpart_ptr, sp, rp);
+    if (!err) {
+        for (int j = 0; j < nrpart; j++) arrived[j] = 1;
+        for (int64_t n = 0; n < V; n++)
+            if (!ready[sp[n]]) arrived[rp[n]] = 0;
+    }
+    free(sp); free(rp); free(match);
+    return err;
+}

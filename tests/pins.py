@@ -478,6 +478,73 @@ def check_locality_names_values_by_source_element(lib):
     assert np.array_equal(as_values(got, np.float64)[12:], np.tile(x, 4))
 
 
+# ---------------------------------------------------- partitioned exchange ----
+
+def ghost_sources(p):
+    """Byte offset of the source point of every receive element of a stencil pattern, per
+    rank, read from the global grid assembled from each point's own offset."""
+    npts = int(np.prod(p.meta["blk"]))
+    comps = p.meta["comps"]
+    offs = p.send_base[:, None] + np.arange(npts)[None, :] * p.elem_size
+    ids = np.repeat(offs.reshape(-1, 1), comps, axis=1).astype(np.float64).reshape(-1)
+    return [g[:, 0].astype(np.int64) for g in ghost_expected(p, ids)]
+
+
+def _cuts(rng, n_elems, s, n):
+    """n partitions of a buffer of n_elems elements of s bytes, cut at element boundaries
+    (some possibly empty)."""
+    c = np.sort(rng.integers(0, n_elems + 1, size=n - 1)) * s
+    return np.concatenate([[0], c, [n_elems * s]]).astype(np.int64)
+
+
+def check_partitioned_bruteforce(lib):
+    """Only the elements whose source point lies in a ready send partition have moved; a
+    receive partition has arrived when all its elements have; all partitions ready is the
+    whole exchange; the order in which partitions move does not matter."""
+    rng = np.random.default_rng(23)
+    for grid, ranks, comps, dt in (((12, 8), (3, 2), 2, "f64"), ((8, 8, 8), (2, 2, 2), 1, "f32")):
+        p = pt.stencil(grid, ranks, ppn=2, comps=comps, dtype=dt, neighbors="all")
+        vt = np.float64 if dt == "f64" else np.float32
+        x = pt.stencil_field(p, 3)
+        xb = x.view(np.uint8)
+        src = ghost_sources(p)
+        full = oracle.standard(p, x, lib=lib)
+        init = pt.random_bytes(p.recvbuf_bytes, 4)
+        s = p.elem_size
+        for trial in range(6):
+            n, nr = int(rng.integers(1, 7)), int(rng.integers(1, 5))
+            cuts = _cuts(rng, p.sendbuf_bytes // s, s, n)
+            rcuts = _cuts(rng, p.recvbuf_bytes // s, s, nr)
+            ready = rng.integers(0, 2, size=n).astype(np.uint8)
+            part = lambda off, c: int(np.searchsorted(c, off, side="right") - 1)
+            want = init.copy()
+            arr = np.ones(nr, np.uint8)
+            for r in range(p.P):
+                for k, so in enumerate(src[r]):
+                    ro = int(p.recv_base[r]) + k * s
+                    if ready[part(so, cuts)]:
+                        want[ro: ro + s] = xb[so: so + s]
+                    else:
+                        arr[part(ro, rcuts)] = 0
+            got = oracle.standard_partial(p, cuts, ready, x, init, lib=lib)
+            assert np.array_equal(got, want), (grid, trial)
+            assert np.array_equal(oracle.arrived(p, cuts, ready, rcuts, lib=lib), arr), (grid, trial)
+            rest = 1 - ready
+            both = oracle.standard_partial(p, cuts, rest, x, got, lib=lib)
+            assert np.array_equal(both, oracle.standard(p, x, init, lib=lib)), (grid, trial)
+            assert oracle.arrived(p, cuts, np.ones(n, np.uint8), rcuts, lib=lib).all()
+        assert np.array_equal(oracle.standard_partial(p, [0, p.sendbuf_bytes], [1], x, lib=lib), full)
+        # a boundary inside an element that is sent, and malformed pointers, are errors
+        sent = int(src[0][0])
+        for bad in ([0, sent + 1, p.sendbuf_bytes], [0, p.sendbuf_bytes - s], [s, p.sendbuf_bytes],
+                    [0, 3 * s, 2 * s, p.sendbuf_bytes]):
+            try:
+                oracle.standard_partial(p, bad, np.ones(len(bad) - 1, np.uint8), x, lib=lib)
+                raise AssertionError(f"accepted partition pointers {bad}")
+            except oracle.OracleError as e:
+                assert e.code == oracle.ERR_ARG
+
+
 # -------------------------------------------------------- all-to-all-w ----
 
 def load_wgolden(name):
@@ -626,7 +693,7 @@ def check_w_adjoint(lib):
         assert np.array_equal(acc[~hit], old[~hit]), w.name
 
 
-ALL_CHECKS = [check_locality_names_values_by_source_element, check_w_golden, check_w_bruteforce_random, check_w_reduces_to_v,
+ALL_CHECKS = [check_partitioned_bruteforce, check_locality_names_values_by_source_element, check_w_golden, check_w_bruteforce_random, check_w_reduces_to_v,
               check_w_stencil_bruteforce, check_w_adjoint,
               check_golden_forward, check_golden_multigraph_truncate, check_golden_locality,
               check_golden_backward_order, check_bruteforce_stencil, check_bruteforce_spmv,

@@ -49,6 +49,10 @@ MUTANTS = [
     ("w_backward_wrong_base", "t[n].val = grad_recv + da;", "t[n].val = grad_recv + (da - wp->recv_base[d]);"),
     ("values_named_by_send_slot", "pt->global_sidx[pt->send_slot_ptr[r] + q] : x->src_off;",
      "pt->global_sidx[pt->send_slot_ptr[r] + q] : q;"),
+    ("partition_by_receive_offset", "sp[n] = part_of(npart, part_ptr, src, s);",
+     "sp[n] = part_of(npart, part_ptr, dst < pt->sendbuf_bytes ? dst : 0, s);"),
+    ("partition_straddle_accepted", "return off + s <= ptr[p + 1] ? p : -1;", "return p;"),
+    ("arrival_ignores_readiness", "if (!ready[sp[n]]) arrived[rp[n]] = 0;", "(void)0;"),
     ("dedup_by_gidx_only", "if (p->a != q->a) return p->a < q->a ? -1 : 1;\n    if (p->b != q->b) return p->b < q->b ? -1 : 1;\n    if (p->gidx",
      "if (0) return 0;\n    if (0) return 0;\n    if (p->gidx"),
 ]
