@@ -62,6 +62,9 @@ extern "C" {
                                     device-side validation (a library bug); nothing ran    */
 #define GBX_ERR_OVERLAP     13   /* two receive blocks write the same bytes              */
 #define GBX_ERR_LIMIT       14   /* beyond the fixed capacity of gbx_neighbor_alltoallv_noalloc */
+#define GBX_ERR_STATE       15   /* call not allowed in the request's current state (partitioned:
+                                    pready before start or twice in one epoch, a wait or an
+                                    arrival wait before the partitions it needs were marked) */
 
 /* payload types: only the backward (which adds) needs to know them */
 #define GBX_BYTES 0
@@ -78,7 +81,7 @@ typedef struct gbx_request_s *gbx_request_t;
 
 /* What a request does per start; filled by gbx_request_get_info. */
 typedef struct {
-    int kind;               /* 0 forward exchange, 1 backward (reverse) exchange       */
+    int kind;               /* 0 forward exchange, 1 backward (reverse) exchange, 2 partitioned */
     int algorithm;          /* GBX_ALG_*                                              */
     int levels;             /* dependent kernel phases per start (1 or 3)             */
     int launches;           /* kernels per start                                      */
@@ -232,6 +235,43 @@ int gbx_neighbor_allgatherv_init(const void *sendbuf, int64_t sendbuf_bytes, con
                                  const int64_t *recv_base, const int *recvcounts, const int *rdispls,
                                  int64_t elem_size, int dtype, gbx_graph_t graph,
                                  const char *info, void *stream, gbx_request_t *request);
+
+/* Persistent partitioned exchange (section 2.3: partitioned communication lets marked
+ * portions of a buffer move before the whole message is complete -- early-bird transfer --
+ * and lets the receiver use completed portions early).  Built on a standard-form forward
+ * request `forward` (from gbx_neighbor_alltoallv_init, the derived collectives or
+ * gbx_neighbor_alltoallw_init; the locality form gives GBX_ERR_UNSUPPORTED), which must
+ * outlive it and keeps working on its own.
+ *   part_ptr[npart+1]    HOST byte boundaries of the send partitions over the forward's
+ *                        send buffer: part_ptr[0] = 0, non-decreasing, part_ptr[npart] =
+ *                        sendbuf_bytes; element bytes the exchange reads may not straddle a
+ *                        boundary (GBX_ERR_ARG otherwise).  1 <= npart <= 1024.
+ *   rpart_ptr[nrpart+1]  HOST byte boundaries of the receive partitions over the receive
+ *                        buffer, same rules.  1 <= nrpart <= 1024.
+ * Each send partition's elements (those whose source lies in it) get their own move
+ * program, built, validated, tuned and captured at init.  Use, per epoch:
+ *   gbx_start(req)                       opens an epoch (no data moves yet);
+ *   gbx_pready(req, p, stream)           partition p is ready: its moves are enqueued on
+ *                                        `stream` (NULL = the request's stream), ordered
+ *                                        after the producer's work already on that stream;
+ *   gbx_parrived(req, j, &flag)          flag = 1 once every value of receive partition j
+ *                                        has landed (host query, no blocking);
+ *   gbx_parrived_stream(req, j, stream)  `stream` waits (on the device) until receive
+ *                                        partition j has landed; every send partition
+ *                                        feeding j must have been marked (GBX_ERR_STATE);
+ *   gbx_wait / gbx_test / gbx_wait_stream   complete the epoch; every partition must have
+ *                                        been marked (GBX_ERR_STATE otherwise; the epoch
+ *                                        stays open).
+ * Nothing waits on the device for a flag: readiness is stream order, so a partition
+ * produced by a kernel on stream A moves right after it when marked on A.  gbx_startall
+ * and gbx_start_host do not take partitioned requests (GBX_ERR_UNSUPPORTED);
+ * gbx_request_bind rebinds every partition's program. */
+int gbx_partitioned_init(gbx_request_t forward, int npart, const int64_t *part_ptr, int nrpart,
+                         const int64_t *rpart_ptr, const char *info, void *stream,
+                         gbx_request_t *request);
+int gbx_pready(gbx_request_t request, int partition, void *stream);
+int gbx_parrived(gbx_request_t request, int rpartition, int *flag);
+int gbx_parrived_stream(gbx_request_t request, int rpartition, void *stream);
 
 /* Datatype of gbx_neighbor_alltoallw_init: a block of `blocklen` bytes repeated over three
  * strided levels, innermost first (count[0] blocks stride[0] bytes apart form a row,

@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(_HERE, "libgbx.so")
 
 SUCCESS, ERR_ARG, ERR_RANK, ERR_TRUNCATE, ERR_INDEX, ERR_DUP, ERR_GIDX = 0, 1, 2, 3, 4, 5, 6
 ERR_ACTIVE, ERR_TIMEOUT, ERR_CUDA, ERR_NOMEM, ERR_UNSUPPORTED, ERR_INTERNAL, ERR_OVERLAP = 7, 8, 9, 10, 11, 12, 13
-ERR_LIMIT = 14
+ERR_LIMIT, ERR_STATE = 14, 15
 BYTES, F32, F64 = 0, 1, 2
 ALG_STANDARD, ALG_LOCALITY = 0, 1
 DTYPE_CODES = {"bytes": BYTES, "f32": F32, "f64": F64}
@@ -71,6 +71,10 @@ def lib():
                                          ctypes.c_char_p, _vp, _pvp],
         "gbx_alltoallv_init": [_vp, _vp, _i64, _vp, _vp, _vp, _vp, _i64, _vp, _vp, _vp, _i64, ctypes.c_int,
                                ctypes.c_char_p, _vp, _pvp],
+        "gbx_partitioned_init": [_vp, ctypes.c_int, _vp, ctypes.c_int, _vp, ctypes.c_char_p, _vp, _pvp],
+        "gbx_pready": [_vp, ctypes.c_int, _vp],
+        "gbx_parrived": [_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int)],
+        "gbx_parrived_stream": [_vp, ctypes.c_int, _vp],
         "gbx_neighbor_alltoallw_init": [_vp, _i64, _vp, _vp, _vp, _vp, _vp, _i64, _vp, _vp, _vp, _vp,
                                         _vp, ctypes.c_int, ctypes.c_int, _vp, ctypes.c_char_p, _vp, _pvp],
         "gbx_start": [_vp],
@@ -187,6 +191,20 @@ class Request:
 
     def wait_stream(self, stream=None):
         _check(lib().gbx_wait_stream(self.handle, _stream_handle(stream)), "wait_stream")
+
+    def pready(self, partition: int, stream=None):
+        """Partitioned request: partition `partition` of the send buffer is ready; its
+        moves are enqueued on `stream` (default: the request's)."""
+        _check(lib().gbx_pready(self.handle, int(partition), _stream_handle(stream)), "pready")
+
+    def parrived(self, rpartition: int) -> bool:
+        f = ctypes.c_int(0)
+        _check(lib().gbx_parrived(self.handle, int(rpartition), ctypes.byref(f)), "parrived")
+        return bool(f.value)
+
+    def parrived_stream(self, rpartition: int, stream=None):
+        """`stream` waits on the device until receive partition `rpartition` has landed."""
+        _check(lib().gbx_parrived_stream(self.handle, int(rpartition), _stream_handle(stream)), "parrived_stream")
 
     def bind(self, src=None, dst=None):
         _check(lib().gbx_request_bind(self.handle, _ptr(src), _ptr(dst)), "bind")
@@ -318,6 +336,22 @@ def neighbor_alltoallw_init(sendbuf, send_base, sendcounts, sdispls, sendtypes, 
         ctypes.cast(arr, ctypes.c_void_p), int(n), int(dtype), graph.handle, info.encode() if info else None,
         _stream_handle(stream), ctypes.byref(h)), "neighbor_alltoallw_init")
     return Request(h, keep=(sendbuf, recvbuf, graph))
+
+
+def partitioned_init(forward: Request, part_ptr, rpart_ptr, info: str = "", stream=None) -> Request:
+    """Partitioned (early-bird) exchange over a standard-form forward request: send
+    partitions = byte ranges part_ptr[k]..part_ptr[k+1] of its send buffer, receive
+    partitions likewise over its receive buffer (host integer sequences; see include/gbx.h).
+    Use start(), pready(k, stream) per ready partition, parrived(j) / parrived_stream(j),
+    then wait()."""
+    import numpy as np
+    pp = np.ascontiguousarray(part_ptr, dtype=np.int64)
+    rp = np.ascontiguousarray(rpart_ptr, dtype=np.int64)
+    h = ctypes.c_void_p()
+    _check(lib().gbx_partitioned_init(forward.handle, len(pp) - 1, pp.ctypes.data, len(rp) - 1, rp.ctypes.data,
+                                      info.encode() if info else None, _stream_handle(stream), ctypes.byref(h)),
+           "partitioned_init")
+    return Request(h, keep=(forward,))
 
 
 def _handles(reqs: Sequence[Request]):

@@ -38,6 +38,7 @@ extern "C" const char *gbx_error_string(int code) {
         case GBX_ERR_OVERLAP: return "receive blocks overlap";
         case GBX_ERR_INTERNAL: return "internal error: a generated move program failed validation";
         case GBX_ERR_LIMIT: return "size beyond the fixed scratch of the allocation-free exchange";
+        case GBX_ERR_STATE: return "call not allowed in the request's current state";
         default: return "unknown error";
     }
 }
@@ -628,6 +629,15 @@ static void destroy_batch(Batch *b) {
 
 static void destroy_request(gbx_request_s *req) {
     if (!req) return;
+    if (req->kind == 2) {
+        for (size_t k = 0; k < req->part_ev.size(); k++) {
+            if (req->part_ready[k]) cudaEventSynchronize(req->part_ev[k]);
+            cudaEventDestroy(req->part_ev[k]);
+        }
+        for (gbx_request_s *c : req->parts) destroy_request(c);
+        req->parts.clear();
+        req->active = 0;
+    }
     if (req->active) {
         cudaEvent_t ev = req->pending ? *req->pending : req->done;
         cudaEventSynchronize(ev);
@@ -771,6 +781,142 @@ extern "C" int gbx_neighbor_alltoallw_init(const void *sendbuf, int64_t sendbuf_
     return GBX_SUCCESS;
 }
 
+// ------------------------------------------------------------ partitioned
+static int check_part_ptr(int n, const int64_t *ptr, int64_t bytes) {
+    if (n < 1 || n > 1024 || !ptr || ptr[0] != 0 || ptr[n] != bytes) return GBX_ERR_ARG;
+    for (int k = 0; k < n; k++)
+        if (ptr[k + 1] < ptr[k]) return GBX_ERR_ARG;
+    return GBX_SUCCESS;
+}
+
+extern "C" int gbx_partitioned_init(gbx_request_t forward, int npart, const int64_t *part_ptr, int nrpart,
+                                    const int64_t *rpart_ptr, const char *info, void *stream,
+                                    gbx_request_t *request) {
+    if (!request) return GBX_ERR_ARG;
+    *request = nullptr;
+    if (!forward || forward->kind != 0) return GBX_ERR_ARG;
+    if (forward->algorithm != GBX_ALG_STANDARD) return GBX_ERR_UNSUPPORTED;
+    GBX_TRY(check_part_ptr(npart, part_ptr, forward->src_bytes));
+    GBX_TRY(check_part_ptr(nrpart, rpart_ptr, forward->dst_bytes));
+    Opts o = parse_info(info);
+    if (!o.ok) return GBX_ERR_ARG;
+    gbx_request_s *req = new_request(o, stream);
+    if (!req->done) { destroy_request(req); return GBX_ERR_CUDA; }
+    req->kind = 2;
+    req->forward = forward;
+    req->graph = forward->graph;
+    req->src = forward->src;
+    req->dst = forward->dst;
+    req->src_bytes = forward->src_bytes;
+    req->dst_bytes = forward->dst_bytes;
+    req->elem_size = forward->elem_size;
+    req->dtype = forward->dtype;
+    req->align = forward->align;
+    req->algorithm = GBX_ALG_STANDARD;
+    req->npart = npart;
+    req->nrpart = nrpart;
+    req->part_ready.assign(npart, 0);
+    PartPlan plan;
+    int rc = gbx_setup_partitions(req, forward, npart, part_ptr, nrpart, rpart_ptr, &plan);
+    const int64_t s = forward->elem_size;
+    int64_t algo = 0;
+    int launches = 0;
+    for (int k = 0; k < npart && rc == GBX_SUCCESS; k++) {
+        const int64_t n = plan.elem_off[k + 1] - plan.elem_off[k];
+        if (n == 0) { req->parts.push_back(nullptr); continue; }
+        gbx_request_s *c = new_request(o, stream);
+        req->parts.push_back(c);
+        if (!c->done) { rc = GBX_ERR_CUDA; break; }
+        c->kind = 0;
+        c->graph = forward->graph;
+        c->src = forward->src;
+        c->dst = forward->dst;
+        c->src_bytes = forward->src_bytes;
+        c->dst_bytes = forward->dst_bytes;
+        c->elem_size = s;
+        c->dtype = forward->dtype;
+        c->align = forward->align;
+        c->algorithm = GBX_ALG_STANDARD;
+        const int64_t ns = plan.seg_off[k + 1] - plan.seg_off[k];
+        rc = gbx_make_copy_op(c, 0, c->src, ROLE_SRC, c->dst, ROLE_DST, plan.segs + plan.seg_off[k], ns,
+                              plan.idx + plan.elem_off[k], n, n, 2 * n * s + 4 * n + ns * (int64_t)sizeof(Seg));
+        if (rc == GBX_SUCCESS) rc = finalize(c);
+        if (rc == GBX_SUCCESS) {
+            c->info.V = n;
+            c->info.elem_size = s;
+            c->info.user_bytes = 2 * n * s;
+            algo += c->info.algo_bytes;
+            launches += c->info.launches;
+        }
+    }
+    for (int k = 0; k < npart && rc == GBX_SUCCESS; k++) {
+        cudaEvent_t ev;
+        if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) { rc = GBX_ERR_CUDA; break; }
+        req->part_ev.push_back(ev);
+    }
+    if (rc != GBX_SUCCESS) {
+        req->part_ready.assign(req->part_ev.size(), 0);
+        destroy_request(req);
+        return rc;
+    }
+    req->feed = plan.feed;
+    gbx_request_info_t &I = req->info;
+    I = forward->info;
+    I.kind = 2;
+    I.levels = 1;
+    I.launches = launches;
+    I.algo_bytes = algo;
+    *request = req;
+    return GBX_SUCCESS;
+}
+
+extern "C" int gbx_pready(gbx_request_t req, int p, void *stream) {
+    if (!req || req->kind != 2 || p < 0 || p >= req->npart) return GBX_ERR_ARG;
+    if (!req->active || req->part_ready[p]) return GBX_ERR_STATE;
+    cudaStream_t st = stream ? (cudaStream_t)stream : req->stream;
+    gbx_request_s *c = req->parts[p];
+    if (c) {
+        if (c->use_graph && c->exec) GBX_CUDA_TRY(cudaGraphLaunch(c->exec, st));
+        else GBX_CUDA_TRY(enqueue_levels(c->launches, st));
+    }
+    GBX_CUDA_TRY(cudaEventRecord(req->part_ev[p], st));
+    req->part_ready[p] = 1;
+    req->nready++;
+    return GBX_SUCCESS;
+}
+
+static bool feeds(const gbx_request_s *req, int j, int k) {
+    const int words = (req->npart + 31) / 32;
+    return (req->feed[(size_t)j * words + (k >> 5)] >> (k & 31)) & 1u;
+}
+
+extern "C" int gbx_parrived(gbx_request_t req, int j, int *flag) {
+    if (!req || req->kind != 2 || j < 0 || j >= req->nrpart || !flag) return GBX_ERR_ARG;
+    if (!req->active) return GBX_ERR_STATE;
+    *flag = 1;
+    for (int k = 0; k < req->npart; k++) {
+        if (!feeds(req, j, k)) continue;
+        if (!req->part_ready[k]) { *flag = 0; return GBX_SUCCESS; }
+        cudaError_t e = cudaEventQuery(req->part_ev[k]);
+        if (e == cudaErrorNotReady) { *flag = 0; return GBX_SUCCESS; }
+        if (e != cudaSuccess) {
+            gbx_note_cuda_error(e, "event query", __FILE__, __LINE__);
+            return GBX_ERR_CUDA;
+        }
+    }
+    return GBX_SUCCESS;
+}
+
+extern "C" int gbx_parrived_stream(gbx_request_t req, int j, void *stream) {
+    if (!req || req->kind != 2 || j < 0 || j >= req->nrpart) return GBX_ERR_ARG;
+    if (!req->active) return GBX_ERR_STATE;
+    for (int k = 0; k < req->npart; k++)
+        if (feeds(req, j, k) && !req->part_ready[k]) return GBX_ERR_STATE;
+    for (int k = 0; k < req->npart; k++)
+        if (feeds(req, j, k)) GBX_CUDA_TRY(cudaStreamWaitEvent((cudaStream_t)stream, req->part_ev[k], 0));
+    return GBX_SUCCESS;
+}
+
 extern "C" int gbx_backward_init(gbx_request_t forward, const void *grad_recv, void *grad_send, int accumulate,
                                  const char *info, void *stream, gbx_request_t *request) {
     if (!request) return GBX_ERR_ARG;
@@ -818,15 +964,42 @@ static int enqueue_start(gbx_request_s *req) {
 extern "C" int gbx_start(gbx_request_t req) {
     if (!req) return GBX_ERR_ARG;
     if (req->active) return GBX_ERR_ACTIVE;
+    if (req->kind == 2) {   // partitioned: open an epoch; data moves at gbx_pready
+        std::fill(req->part_ready.begin(), req->part_ready.end(), 0);
+        req->nready = 0;
+        req->active = 1;
+        return GBX_SUCCESS;
+    }
     return enqueue_start(req);
 }
 
 static cudaEvent_t pending_event(gbx_request_s *req) { return req->pending ? *req->pending : req->done; }
 
+// partitioned: 1 when every marked partition's moves are done (0 if still running)
+static int parts_done(gbx_request_s *req, int *flag) {
+    *flag = 1;
+    for (int k = 0; k < req->npart; k++) {
+        if (!req->part_ready[k]) continue;
+        cudaError_t e = cudaEventQuery(req->part_ev[k]);
+        if (e == cudaErrorNotReady) { *flag = 0; return GBX_SUCCESS; }
+        if (e != cudaSuccess) {
+            gbx_note_cuda_error(e, "event query", __FILE__, __LINE__);
+            return GBX_ERR_CUDA;
+        }
+    }
+    return GBX_SUCCESS;
+}
+
 extern "C" int gbx_test(gbx_request_t req, int *flag) {
     if (!req || !flag) return GBX_ERR_ARG;
     *flag = 1;
     if (!req->active) return GBX_SUCCESS;
+    if (req->kind == 2) {
+        if (req->nready < req->npart) { *flag = 0; return GBX_ERR_STATE; }
+        GBX_TRY(parts_done(req, flag));
+        if (*flag) req->active = 0;
+        return GBX_SUCCESS;
+    }
     cudaError_t e = cudaEventQuery(pending_event(req));
     if (e == cudaErrorNotReady) { *flag = 0; return GBX_SUCCESS; }
     if (e != cudaSuccess) {
@@ -857,6 +1030,13 @@ extern "C" int gbx_wait(gbx_request_t req) {
 extern "C" int gbx_wait_stream(gbx_request_t req, void *stream) {
     if (!req) return GBX_ERR_ARG;
     if (!req->active) return GBX_SUCCESS;
+    if (req->kind == 2) {
+        if (req->nready < req->npart) return GBX_ERR_STATE;
+        for (int k = 0; k < req->npart; k++)
+            GBX_CUDA_TRY(cudaStreamWaitEvent((cudaStream_t)stream, req->part_ev[k], 0));
+        req->active = 0;
+        return GBX_SUCCESS;
+    }
     GBX_CUDA_TRY(cudaStreamWaitEvent((cudaStream_t)stream, pending_event(req), 0));
     req->active = 0;
     req->pending = nullptr;
@@ -873,6 +1053,7 @@ extern "C" int gbx_startall(int count, gbx_request_t *reqs) {
     if (count <= 0 || !reqs) return GBX_ERR_ARG;
     for (int i = 0; i < count; i++) {
         if (!reqs[i]) return GBX_ERR_ARG;
+        if (reqs[i]->kind == 2) return GBX_ERR_UNSUPPORTED;
         if (reqs[i]->active) return GBX_ERR_ACTIVE;
         for (int j = 0; j < i; j++) if (reqs[j] == reqs[i]) return GBX_ERR_ARG;
     }
@@ -914,6 +1095,13 @@ extern "C" int gbx_startall(int count, gbx_request_t *reqs) {
 extern "C" int gbx_request_bind(gbx_request_t req, const void *src, void *dst) {
     if (!req) return GBX_ERR_ARG;
     if (req->active) return GBX_ERR_ACTIVE;
+    if (req->kind == 2) {
+        for (gbx_request_s *c : req->parts)
+            if (c) GBX_TRY(gbx_request_bind(c, src, dst));
+        if (src) req->src = (const char *)src;
+        if (dst) req->dst = (char *)dst;
+        return GBX_SUCCESS;
+    }
     const char *ns = src ? (const char *)src : req->src;
     char *nd = dst ? (char *)dst : req->dst;
     for (HostOp &op : req->ops) {
@@ -937,6 +1125,7 @@ extern "C" int gbx_request_bind(gbx_request_t req, const void *src, void *dst) {
 
 extern "C" int gbx_start_host(gbx_request_t req, const void *host_src, void *host_dst) {
     if (!req || (req->src_bytes > 0 && !host_src) || (req->dst_bytes > 0 && !host_dst)) return GBX_ERR_ARG;
+    if (req->kind == 2) return GBX_ERR_UNSUPPORTED;
     if (req->active) return GBX_ERR_ACTIVE;
     if (req->src_bytes > 0)
         GBX_CUDA_TRY(cudaMemcpyAsync((void *)req->src, host_src, req->src_bytes, cudaMemcpyHostToDevice, req->stream));

@@ -255,6 +255,22 @@ struct gbx_request_s {
     int64_t npairs;
     char *agg;               // locality scratch: send aggregate | receive aggregate
     std::vector<Batch *> batches;
+    // partitioned requests (kind 2): one standard-form child per non-empty send partition
+    int npart = 0, nrpart = 0;
+    std::vector<gbx_request_s *> parts;
+    std::vector<cudaEvent_t> part_ev;
+    std::vector<char> part_ready;
+    int nready = 0;
+    std::vector<uint32_t> feed;  // nrpart rows of ceil(npart / 32) words: send partitions feeding each
+};
+
+// Device part of a partitioned request: every forward element keyed by its send
+// partition, cut into receive-contiguous runs of one source rank per partition.
+struct PartPlan {
+    Seg *segs = nullptr;          // all partitions' segments, partition by partition
+    int32_t *idx = nullptr;       // per element, in partition order: source element in its rank's region
+    std::vector<int64_t> elem_off, seg_off;   // npart + 1 each
+    std::vector<uint32_t> feed;
 };
 
 // Internal steps shared by the C ABI translation unit.
@@ -264,6 +280,8 @@ int gbx_setup_forward(gbx_request_s *req, const int64_t *send_base, const int *s
                       const int64_t *recv_slot_ptr, const int64_t *global_sidx,
                       const int64_t *global_ridx, int want_locality);
 int gbx_setup_backward(gbx_request_s *bwd, int accumulate);
+int gbx_setup_partitions(gbx_request_s *parent, const gbx_request_s *f, int npart, const int64_t *part_ptr,
+                         int nrpart, const int64_t *rpart_ptr, PartPlan *plan);
 int gbx_setup_alltoallw(gbx_request_s *req, const int64_t *send_base, const int *sendcounts, const int64_t *sdispls,
                         const int *sendtypes, const int64_t *recv_base, const int *recvcounts, const int64_t *rdispls,
                         const int *recvtypes, const gbx_datatype_t *types, int ntypes);
