@@ -15,7 +15,8 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "libgbx.so")
 SOURCES = ["gbx_prims.cu", "gbx_move.cu", "gbx_setup.cu", "gbx_api.cu", "gbx_variants.cu", "gbx_alltoallw.cu", "gbx_partition.cu", "gbx_noalloc.cu"]
-HEADERS = [os.path.join(CSRC, "gbx_internal.cuh"), os.path.join(ROOT, "include", "gbx.h")]
+HEADERS = [os.path.join(CSRC, "gbx_internal.cuh"), os.path.join(CSRC, "gbx_device.cuh"),
+           os.path.join(ROOT, "include", "gbx.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -24,67 +24,7 @@
 
 #include "../../include/gbx.h"
 
-#define GBX_TILE 1024                    // chunks per tile (block * unroll)
-#define GBX_TERM_GROUP (1ull << 63)      // fold term: first term of a group
-#define GBX_TERM_BUFB (1ull << 62)       // fold term: reads buffer B (else A)
-#define GBX_TERM_MASK ((1ull << 62) - 1)
-// fold row record: a = output byte offset | GBX_ROW_SINGLE; b = the row's only term when
-// GBX_ROW_SINGLE is set, else (first term index << 24) | term count
-#define GBX_ROW_SINGLE (1ull << 63)
-#define GBX_ROW_CNT_BITS 24
-
-#define GBX_ERR_NONE 0x7fffffff          // device error word: "no error yet"
-
-// Buffer roles of an op's pointers (for re-binding).
-enum { ROLE_SRC = 0, ROLE_DST = 1, ROLE_AGG = 2, ROLE_NONE = 3 };
-
-struct Seg {
-    int64_t v0;       // first element of the segment in the op's element space
-    int64_t dst_off;  // byte offset of the segment's first destination element
-    int64_t src_off;  // byte offset of the source base (contiguous: of the first element)
-    int64_t idx_off;  // >= 0: element k reads index idx[idx_off + k]; < 0: contiguous
-};
-
-struct CopyDesc {
-    const char *src;
-    char *dst;
-    const Seg *segs;
-    const int32_t *idx;
-    const int64_t *tile_seg;  // ntiles + 1: segment holding each tile's first element
-    const int64_t *tile_e0;   // ntiles: first element of each tile
-    int64_t nseg, nelem, nchunks, ntiles, elem_size;
-    int32_t vec, cpe, cpe_shift;  // chunks per element; log2 of it, or -1
-    uint32_t cpe_magic;           // ceil(2^32 / cpe) when cpe is not a power of two
-    int32_t src_role, dst_role;
-    // flat form (when set): destinations are one contiguous run from dst_flat0 and element
-    // e reads source element flat_idx[e]; no segment search
-    int32_t flat;
-    const int32_t *flat_idx;
-    int64_t dst_flat0;
-    // flat form with two sources: an index with bit 31 set reads src2 (e.g. the receive
-    // aggregate) instead of src
-    const char *src2;
-    int32_t src2_role;
-    // two-index flat form (flat == 3): element e also writes destination element flat_didx[e]
-    const int32_t *flat_didx;
-};
-#define GBX_FLAT_SRC2 0x80000000u
-
-struct FoldDesc {
-    char *out;
-    const char *bufA;
-    const char *bufB;
-    const int64_t *row_ptr;   // nrows + 1 (setup and validation)
-    const int64_t *row_out;   // byte offset of each row's output element (setup and validation)
-    const longlong2 *rec;     // nrows packed row records (the kernel's view)
-    const int64_t *terms;     // byte offset | GBX_TERM_GROUP | GBX_TERM_BUFB
-    const int64_t *tile_e0;   // ntiles: first row of each tile
-    int64_t nrows, nchunks, ntiles, elem_size;
-    int32_t vec, cpe, cpe_shift;
-    uint32_t cpe_magic;
-    int32_t dtype, accumulate;
-    int32_t out_role, a_role, b_role;
-};
+#include "gbx_device.cuh"
 
 // ----------------------------------------------------------------------------- util
 #define GBX_CUDA_TRY(expr)                                  \
