@@ -487,8 +487,47 @@ static int tune_op(gbx_request_s *req, HostOp &op) {
 // (payload type, vector width) for folds, so every launch runs a specialised kernel.  For a
 // batch the ops of all its requests are pooled, so each launch covers every pattern of its
 // class (the generic width-dispatching kernels stay available but are not needed).
+// Times a pooled launch in every block size and grid mode with CUDA events and keeps the
+// fastest (the moved bytes do not depend on the shape).
+static int tune_launch(LevelLaunch &L, cudaStream_t st) {
+    cudaEvent_t a, b;
+    GBX_CUDA_TRY(cudaEventCreate(&a));
+    GBX_CUDA_TRY(cudaEventCreate(&b));
+    const int blocks[4] = {128, 256, 512, 1024};
+    float best = 1e30f;
+    int bb = L.block, bg = L.grid;
+    cudaError_t e = cudaSuccess;
+    for (int bi = 0; bi < 4 && e == cudaSuccess; bi++)
+        for (int pers = 1; pers >= 0 && e == cudaSuccess; pers--) {
+            const int blk = gbx_effective_block(L.vec, blocks[bi]);
+            const int grid = grid_for(L.kind, L.dtype, L.vec, L.flat, blk, pers, L.total_tiles);
+            e = launch_list(L.kind, L.dtype, L.vec, L.flat, L.d_ops, L.d_prefix, L.nops, L.total_tiles, blk, grid, st);
+            float t = 1e30f;
+            for (int r = 0; r < 3 && e == cudaSuccess; r++) {
+                cudaEventRecord(a, st);
+                e = launch_list(L.kind, L.dtype, L.vec, L.flat, L.d_ops, L.d_prefix, L.nops, L.total_tiles, blk,
+                                grid, st);
+                cudaEventRecord(b, st);
+                if (e == cudaSuccess) e = cudaEventSynchronize(b);
+                float x = 0;
+                if (e == cudaSuccess) cudaEventElapsedTime(&x, a, b);
+                t = std::min(t, x);
+            }
+            if (t < best) { best = t; bb = blk; bg = grid; }
+        }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    if (e != cudaSuccess) {
+        gbx_note_cuda_error(e, "tuning a pooled launch", __FILE__, __LINE__);
+        return GBX_ERR_CUDA;
+    }
+    L.block = bb;
+    L.grid = bg;
+    return GBX_SUCCESS;
+}
+
 static int build_levels(DevPool &mem, const std::vector<HostOp *> &ops, const std::vector<int> &dtypes,
-                        std::vector<LevelLaunch> &out, int batch, cudaStream_t st) {
+                        std::vector<LevelLaunch> &out, int batch, cudaStream_t st, int tune = 0) {
     int nlev = 0;
     for (HostOp *op : ops) nlev = std::max(nlev, op->level + 1);
     for (int lv = 0; lv < nlev; lv++)
@@ -499,9 +538,13 @@ static int build_levels(DevPool &mem, const std::vector<HostOp *> &ops, const st
                 HostOp *op = ops[i];
                 if (op->level != lv || op->kind != kind || op_tiles(*op) <= 0) continue;
                 // every launch is specialised: ops are grouped by (form, vector width) for copies
-                // and (payload type, vector width) for folds; a batch fuses all patterns of a class
+                // and (payload type, vector width) for folds; a batch fuses all patterns of a
+                // class, with every copy that has the flat form in one flat launch whatever form
+                // it was tuned to alone (fewer, larger launches)
+                const int form = !batch ? op_flat(*op)
+                                        : (op->flat_ok ? ((op_flat(*op) & 3) == 3 ? 3 : 1) : 0);
                 std::pair<int, int> k = kind ? std::make_pair(dtypes[i], op_vec(*op))
-                                             : std::make_pair(op_flat(*op), op_vec(*op));
+                                             : std::make_pair(form, op_vec(*op));
                 size_t g = 0;
                 while (g < keys.size() && keys[g] != k) g++;
                 if (g == keys.size()) { keys.push_back(k); groups.emplace_back(); }
@@ -512,11 +555,13 @@ static int build_levels(DevPool &mem, const std::vector<HostOp *> &ops, const st
                 L.kind = kind;
                 L.nops = (int)groups[g].size();
                 // common payload type, vector width and form, or 0 / 2 (= mixed)
-                int dt = dtypes[groups[g][0]], vec = op_vec(*ops[groups[g][0]]), fl = op_flat(*ops[groups[g][0]]);
+                int dt = dtypes[groups[g][0]], vec = op_vec(*ops[groups[g][0]]);
+                // (a pooled class of one op keeps the form it was tuned to, pipelined included)
+                int fl = kind ? 0 : (groups[g].size() == 1 ? op_flat(*ops[groups[g][0]]) : keys[g].first);
                 for (size_t i : groups[g]) {
                     if (dtypes[i] != dt) dt = -1;
                     if (op_vec(*ops[i]) != vec) vec = 0;
-                    if (op_flat(*ops[i]) != fl) fl = 2;
+                    if (!batch && op_flat(*ops[i]) != fl) fl = 2;
                 }
                 if (dt < 0 && kind == 1) vec = 0;
                 L.dtype = dt < 0 ? GBX_F32 : dt;
@@ -540,6 +585,9 @@ static int build_levels(DevPool &mem, const std::vector<HostOp *> &ops, const st
                                              cudaMemcpyHostToDevice, st));
                 GBX_CUDA_TRY(cudaMemcpyAsync(L.d_prefix, pre.data(), sizeof(int64_t) * pre.size(),
                                              cudaMemcpyHostToDevice, st));
+                // a pooled copy launch of a batch is tuned as a whole (copies only: a trial
+                // writes the bytes the real launch writes next; folds keep their op's shape)
+                if (batch && kind == 0 && L.nops > 1 && tune) GBX_TRY(tune_launch(L, st));
                 out.push_back(L);
             }
         }
@@ -1069,7 +1117,9 @@ extern "C" int gbx_startall(int count, gbx_request_t *reqs) {
         std::vector<int> dts;
         for (gbx_request_s *r : key)
             for (HostOp &op : r->ops) { ops.push_back(&op); dts.push_back(r->dtype); }
-        int rc = build_levels(b->mem, ops, dts, b->launches, 1, st);
+        int tune = 1;
+        for (gbx_request_s *r : key) tune &= r->autotune && !r->forced_block;
+        int rc = build_levels(b->mem, ops, dts, b->launches, 1, st, tune);
         if (rc == GBX_SUCCESS && cudaEventCreateWithFlags(&b->done, cudaEventDisableTiming) != cudaSuccess)
             rc = GBX_ERR_CUDA;
         if (rc == GBX_SUCCESS && !b->launches.empty()) rc = capture(b->launches, &b->exec);
