@@ -48,9 +48,9 @@ extern "C" {
 #define GBX_ERR_RANK         2   /* neighbour rank outside [0, P)                        */
 #define GBX_ERR_TRUNCATE     3   /* unmatched edge, or paired counts differ (MPI_ERR_TRUNCATE) */
 #define GBX_ERR_INDEX        4   /* displacement, slot or element index out of range     */
-#define GBX_ERR_DUP          5   /* reserved: one global index with different bytes; the
-                                    library never reads payload at init, so only the CPU
-                                    oracle reports it                                     */
+#define GBX_ERR_DUP          5   /* one global index carried by different bytes into one
+                                    node pair; found at init only with info check_dup=1
+                                    (the library otherwise never reads payload at init)    */
 #define GBX_ERR_GIDX         6   /* a receive global index differs from the matched send index */
 #define GBX_ERR_ACTIVE       7   /* start on a request already started                  */
 #define GBX_ERR_TIMEOUT      8   /* wait gave up after the request's timeout; the request
@@ -187,8 +187,11 @@ int gbx_graph_free(gbx_graph_t *graph);
  *       piece=N            run copies in ascending source order, in pieces of <= N elements
  *                          (default 0: receive order)
  *       timeout_ms=T       limit of gbx_wait (default 60000)
+ *       check_dup=0|1      locality form: at init, compare the bytes of every element that
+ *                          shares a (node pair, global index) value with the value's
+ *                          representative in the send buffer as bound then (default 0)
  * Errors: GBX_ERR_ARG, _TRUNCATE, _INDEX, _GIDX, _OVERLAP (receive blocks must not
- * overlap), _NOMEM, _CUDA.  Validation and map building run as device kernels; the
+ * overlap), _DUP (with check_dup=1), _NOMEM, _CUDA.  Validation and map building run as device kernels; the
  * call blocks on `stream` to read their status.  The autotuner's trial launches write
  * the bound receive buffer (with the correct result for the send data present then).
  * Element bytes are copied exactly; no value is converted. */

@@ -51,6 +51,7 @@ struct Opts {
     int algorithm_auto = 0;
     int graph = 1, autotune = 1, vec = 0, block = 0, timeout_ms = 60000, min_run = 4, piece = 0, flat = -1;
     int split = 1, split_order = 0;
+    int check_dup = 0;
     bool ok = true;
 };
 
@@ -83,6 +84,7 @@ static Opts parse_info(const char *info) {
         else if (k == "flat") o.flat = atoi(v.c_str()) != 0;
         else if (k == "single_split") o.split = atoi(v.c_str()) != 0;
         else if (k == "split_order") o.split_order = v == "source" ? 1 : v == "dest" ? 0 : -1;
+        else if (k == "check_dup") o.check_dup = atoi(v.c_str()) != 0;
         else o.ok = false;
     }
     if (o.vec && !(o.vec == 1 || o.vec == 2 || o.vec == 4 || o.vec == 8 || o.vec == 16)) o.ok = false;
@@ -714,6 +716,7 @@ static gbx_request_s *new_request(const Opts &o, void *stream) {
     req->no_combine = o.flat == 0;
     req->no_single_split = !o.split;
     req->split_order = o.split_order;
+    req->check_dup = o.check_dup;
     if (cudaEventCreateWithFlags(&req->done, cudaEventDisableTiming) != cudaSuccess) {
         cudaGetLastError();
         req->done = nullptr;

@@ -159,6 +159,7 @@ struct gbx_request_s {
     int no_combine;          // locality form: keep direct copies and redistribution apart
     int no_single_split;     // keep single-term fold rows in the fold
     int split_order;         // single-term rows as copies: 0 in row (destination) order, 1 in source order
+    int check_dup;           // locality form: compare every deduplicated value's bytes with its representative's at init
     int timeout_ms;
     gbx_graph_s *graph;
     gbx_request_s *forward;  // backward: its forward request

@@ -502,6 +502,26 @@ __global__ void loc_final_index_kernel(const int64_t *segv0, int64_t nseg, const
 }
 
 // --------------------------------------------------------------- forward driver
+// -------------------------------------------------------------- debug checks
+// GBX_ERR_DUP when an inter-node element's bytes differ from those of the representative of
+// its (node pair, global index) value (read from the send buffer at init).
+__global__ void dup_check_kernel(const char *src, const int64_t *segv0, int64_t nseg, const int *seg_src,
+                                 const int64_t *send_base, const int32_t *srcel, const int64_t *val_pos,
+                                 const int64_t *rep_off, int64_t V, int64_t s, int *err) {
+    FOR_EACH(v, V) {
+        const int64_t q = val_pos[v];
+        if (q < 0) continue;
+        const int64_t off = send_base[seg_src[upper_index(segv0, nseg, v)]] + (int64_t)srcel[v] * s;
+        const int64_t ro = rep_off[q];
+        if (off == ro) continue;
+        for (int64_t b = 0; b < s; b++)
+            if (src[off + b] != src[ro + b]) {
+                set_err(err, GBX_ERR_DUP);
+                break;
+            }
+    }
+}
+
 int gbx_setup_forward(gbx_request_s *req, const int64_t *send_base, const int *sendcounts, const int *sdispls,
                       const int64_t *send_slot_ptr, const int *send_idx, const int64_t *recv_base,
                       const int *recvcounts, const int *rdispls, const int64_t *recv_slot_ptr,
@@ -772,6 +792,13 @@ int gbx_setup_forward(gbx_request_s *req, const int64_t *send_base, const int *s
         seg03_kernel<<<grid_of(nseg), SETUP_T, 0, st>>>(req->segs_std, f_intra, v_intra, p_intra, v_inter, p_inter,
                                                         nseg, U * s, seg0, seg3);
         GBX_CUDA_TRY(cudaGetLastError());
+    }
+    if (req->check_dup && U > 0) {
+        // the debug check: one global index per node pair must carry one value
+        dup_check_kernel<<<grid_of(V), SETUP_T, 0, st>>>(req->src, segv0, nseg, seg_src, req->send_base_copy,
+                                                         req->srcel, req->val_pos, req->agg_rep_off, V, s, err);
+        GBX_CUDA_TRY(cudaGetLastError());
+        GBX_TRY(read_err_stage(err, st));
     }
     req->U = U;
     req->npairs = npairs;

@@ -311,3 +311,52 @@ def test_accumulating_backward_init_leaves_gradient_untouched():
         b.start()
         b.wait()
         assert_bytes_equal(gs.cpu().numpy(), oracle.backward(p, g, old, form=form, accumulate=True), alg)
+
+
+def _dup_pattern(seed):
+    """A random pattern in which one inter-node send slot is given the global index of
+    another slot of the same node pair that reads different bytes (receive indices
+    dropped), so the locality form would send the first slot's value for both."""
+    p = pt.random_pattern(seed, indexed=True, P=24, ppn=4)
+    x = pt.random_bytes(p.sendbuf_bytes, seed)
+    owner = np.repeat(np.arange(p.P), np.diff(p.out_ptr))
+    seen = {}
+    for e in range(len(p.dests)):
+        r, d = int(owner[e]), int(p.dests[e])
+        if r // p.ppn == d // p.ppn:
+            continue
+        for k in range(int(p.sendcounts[e])):
+            slot = int(p.send_slot_ptr[r] + p.sdispls[e] + k)
+            off = int(p.send_base[r] + p.send_idx[slot] * p.elem_size)
+            key = (r // p.ppn, d // p.ppn)
+            if key in seen:
+                s0, o0 = seen[key]
+                if o0 != off and not np.array_equal(x[o0:o0 + p.elem_size], x[off:off + p.elem_size]):
+                    q = pt.Pattern(**{k_: getattr(p, k_) for k_ in p.__dataclass_fields__})
+                    q.global_sidx = p.global_sidx.copy()
+                    q.global_sidx[slot] = p.global_sidx[s0]
+                    q.global_ridx = None
+                    q.recv_slot_ptr = None
+                    return q, x
+            else:
+                seen[key] = (slot, off)
+    return None, None
+
+
+@pytest.mark.parametrize("seed", [3, 8, 21])
+def test_check_dup_reports_conflicting_global_indices(seed):
+    q, x = _dup_pattern(seed)
+    if q is None:
+        pytest.skip("no inter-node pair with two distinct slots")
+    with pytest.raises(oracle.OracleError) as oe:
+        oracle.locality(q, x)
+    assert oe.value.code == gbx.ERR_DUP
+    with pytest.raises(gbx.GbxError) as e:
+        forward(q, x, "locality", info="check_dup=1")
+    assert e.value.code == gbx.ERR_DUP
+    forward(q, x, "locality")            # without the debug check init does not read the payload
+    # consistent indices pass the check and change nothing
+    p = pt.config5(edge=4, comps=2)
+    xs = payload(p, 1)
+    got, _ = forward(p, xs, "locality", info="check_dup=1")
+    assert_bytes_equal(got, oracle.standard(p, xs), "check_dup on a valid pattern")
