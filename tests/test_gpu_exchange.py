@@ -360,3 +360,65 @@ def test_check_dup_reports_conflicting_global_indices(seed):
     xs = payload(p, 1)
     got, _ = forward(p, xs, "locality", info="check_dup=1")
     assert_bytes_equal(got, oracle.standard(p, xs), "check_dup on a valid pattern")
+
+
+def test_config5_full_512cube_backward():
+    """The backward of the full 512^3 exchange, both forms, against the oracle bit for bit
+    (fp64 gradients; each form in its own fixed summation order)."""
+    p = pt.config5()
+    x = pt.stencil_field(p, pt.SEED + 5)
+    g = grad_payload(p, 77)
+    for alg, form in (("standard", 0), ("locality", 1)):
+        _, ex = forward(p, x, alg)
+        got, b = backward(ex, g)
+        assert_bytes_equal(got, oracle.backward(p, g, form=form), f"full backward {alg}")
+        del ex, b
+        torch.cuda.empty_cache()
+
+
+def _explicit(P, ppn, out_lists, in_lists, s, send_base, recv_base, sendbuf_bytes, recvbuf_bytes, dtype="bytes"):
+    """Pattern from per-rank lists: out_lists[r] = [(d, count, sdispl)], in_lists[d] = [(r, count, rdispl)]."""
+    def csr(lists):
+        return np.concatenate([[0], np.cumsum([len(l) for l in lists])]).astype(np.int32)
+    flat = lambda lists, j: np.array([t[j] for l in lists for t in l], np.int32)
+    return pt.Pattern(name="explicit", P=P, ppn=ppn, in_ptr=csr(in_lists), sources=flat(in_lists, 0),
+                      out_ptr=csr(out_lists), dests=flat(out_lists, 0), sendcounts=flat(out_lists, 1),
+                      sdispls=flat(out_lists, 2), recvcounts=flat(in_lists, 1), rdispls=flat(in_lists, 2),
+                      elem_size=s, dtype=dtype, send_base=np.array(send_base, np.int64),
+                      recv_base=np.array(recv_base, np.int64), sendbuf_bytes=sendbuf_bytes,
+                      recvbuf_bytes=recvbuf_bytes)
+
+
+def _degenerate_cases():
+    # one rank sending to itself
+    yield "self", _explicit(1, 1, [[(0, 5, 0)]], [[(0, 5, 2)]], 8, [0], [0], 40, 64, "f64")
+    # a graph with no edges
+    yield "no_edges", _explicit(4, 2, [[], [], [], []], [[], [], [], []], 8, [0] * 4, [0] * 4, 8, 8)
+    # edges that all carry nothing
+    yield "zero_counts", _explicit(3, 1, [[(1, 0, 0)], [(2, 0, 3)], [(0, 0, 1)]],
+                                   [[(2, 0, 0)], [(0, 0, 1)], [(1, 0, 0)]], 4, [0, 8, 16], [0, 8, 16], 24, 24)
+    # one large element per message
+    yield "elem_4096", _explicit(2, 1, [[(1, 1, 0)], [(0, 1, 1)]], [[(1, 1, 0)], [(0, 1, 1)]], 4096,
+                                 [0, 8192], [0, 8192], 16384, 16384)
+    # one-byte elements at odd offsets, two nodes, a repeated neighbour
+    yield "bytes_odd", _explicit(4, 2, [[(3, 3, 1), (3, 2, 0)], [], [(0, 1, 2)], [(1, 4, 0)]],
+                                 [[(2, 1, 0)], [(3, 4, 3)], [], [(0, 3, 0), (0, 2, 5)]], 1,
+                                 [1, 7, 11, 13], [3, 5, 14, 17], 19, 27)
+
+
+@pytest.mark.parametrize("case", list(_degenerate_cases()), ids=lambda c: c[0])
+def test_degenerate_patterns(case):
+    _, p = case
+    assert oracle.validate(p) == 0
+    x = pt.random_bytes(p.sendbuf_bytes, 1) if p.dtype == "bytes" else payload(p, 1)
+    init = pt.random_bytes(p.recvbuf_bytes, 2)
+    want = oracle.standard(p, x, init)
+    for alg in ("standard", "locality"):
+        got, ex = forward(p, x, alg, recv_init=init)
+        assert_bytes_equal(got, want, f"{case[0]} {alg}")
+        ex.start()
+        ex.wait()
+        if p.dtype == "f64":
+            g = grad_payload(p, 3)
+            got, _ = backward(ex, g)
+            assert_bytes_equal(got, oracle.backward(p, g, form=0 if alg == "standard" else 1), f"{case[0]} bwd")
