@@ -187,6 +187,9 @@ int gbx_graph_free(gbx_graph_t *graph);
  *       piece=N            run copies in ascending source order, in pieces of <= N elements
  *                          (default 0: receive order)
  *       timeout_ms=T       limit of gbx_wait (default 60000)
+ *       bulk=0|1|2         offer the bulk form (contiguous pieces moved through shared memory
+ *                          by the bulk-copy engine) to the autotuner where every block is
+ *                          contiguous and 16-byte aligned (default 1; 2 forces it there)
  *       check_dup=0|1      locality form: at init, compare the bytes of every element that
  *                          shares a (node pair, global index) value with the value's
  *                          representative in the send buffer as bound then (default 0)
@@ -238,6 +241,11 @@ int gbx_neighbor_allgatherv_init(const void *sendbuf, int64_t sendbuf_bytes, con
                                  const int64_t *recv_base, const int *recvcounts, const int *rdispls,
                                  int64_t elem_size, int dtype, gbx_graph_t graph,
                                  const char *info, void *stream, gbx_request_t *request);
+
+/* Reads and clears the device status word of the move kernels: 1 when a bounded wait of
+ * the bulk-copy kernel gave up since the last call (the launch then left its pieces
+ * unfinished), else 0.  No counterpart in the paper. */
+int gbx_device_status(int *status);
 
 /* Persistent partitioned exchange (section 2.3: partitioned communication lets marked
  * portions of a buffer move before the whole message is complete -- early-bird transfer --

@@ -77,6 +77,7 @@ def lib():
         "gbx_parrived_stream": [_vp, ctypes.c_int, _vp],
         "gbx_neighbor_alltoallw_init": [_vp, _i64, _vp, _vp, _vp, _vp, _vp, _i64, _vp, _vp, _vp, _vp,
                                         _vp, ctypes.c_int, ctypes.c_int, _vp, ctypes.c_char_p, _vp, _pvp],
+        "gbx_device_status": [ctypes.POINTER(ctypes.c_int)],
         "gbx_start": [_vp],
         "gbx_wait": [_vp],
         "gbx_test": [_vp, ctypes.POINTER(ctypes.c_int)],
@@ -352,6 +353,13 @@ def partitioned_init(forward: Request, part_ptr, rpart_ptr, info: str = "", stre
                                       info.encode() if info else None, _stream_handle(stream), ctypes.byref(h)),
            "partitioned_init")
     return Request(h, keep=(forward,))
+
+
+def device_status() -> int:
+    """Reads and clears the move kernels' device status word (1 = a bounded wait gave up)."""
+    f = ctypes.c_int(0)
+    _check(lib().gbx_device_status(ctypes.byref(f)), "device_status")
+    return f.value
 
 
 def _handles(reqs: Sequence[Request]):

@@ -45,13 +45,18 @@ extern "C" const char *gbx_error_string(int code) {
 
 extern "C" int gbx_version(void) { return 100; }
 
+extern "C" int gbx_device_status(int *status) {
+    if (!status) return GBX_ERR_ARG;
+    return gbx_bulk_status_take(status);
+}
+
 // ------------------------------------------------------------------------ info
 struct Opts {
     int algorithm = GBX_ALG_STANDARD;
     int algorithm_auto = 0;
     int graph = 1, autotune = 1, vec = 0, block = 0, timeout_ms = 60000, min_run = 4, piece = 0, flat = -1;
     int split = 1, split_order = 0;
-    int check_dup = 0;
+    int check_dup = 0, bulk = 1;
     bool ok = true;
 };
 
@@ -85,11 +90,13 @@ static Opts parse_info(const char *info) {
         else if (k == "single_split") o.split = atoi(v.c_str()) != 0;
         else if (k == "split_order") o.split_order = v == "source" ? 1 : v == "dest" ? 0 : -1;
         else if (k == "check_dup") o.check_dup = atoi(v.c_str()) != 0;
+        else if (k == "bulk") o.bulk = atoi(v.c_str());
         else o.ok = false;
     }
     if (o.vec && !(o.vec == 1 || o.vec == 2 || o.vec == 4 || o.vec == 8 || o.vec == 16)) o.ok = false;
     if (o.block && !(o.block == 128 || o.block == 256 || o.block == 512 || o.block == 1024)) o.ok = false;
     if (o.timeout_ms <= 0 || o.min_run < 0 || o.piece < 0 || o.split_order < 0) o.ok = false;
+    if (o.bulk < 0 || o.bulk > 2) o.ok = false;
     return o;
 }
 
@@ -204,6 +211,13 @@ int gbx_make_copy_op(gbx_request_s *req, int level, const char *src, int src_rol
         d.dst_flat0 = op.flat_dst0;
         op.algo_bytes_flat = 2 * nelem * req->elem_size + 4 * nelem;
     }
+    if (req->allow_bulk) {
+        GBX_TRY(gbx_make_bulk(req, segs, nseg, nelem, &op.d_bulk, &op.nbulk, &op.bulk_ok));
+        d.bulk = op.d_bulk;
+        d.nbulk = op.nbulk;
+        op.algo_bytes_bulk = 2 * nelem * req->elem_size + op.nbulk * (int64_t)sizeof(BulkTask);
+    }
+    op.algo_bytes_seg = op.algo_bytes;
     req->ops.push_back(op);
     return GBX_SUCCESS;
 }
@@ -329,7 +343,9 @@ static int set_vec(gbx_request_s *req, HostOp &op, int vec) {
         d.vec = vec; d.cpe = cpe; d.cpe_shift = shift; d.cpe_magic = magic;
         d.nchunks = d.nelem * cpe;
         d.ntiles = ceil_div(d.nchunks, GBX_TILE);
-        if (op.flat_only)
+        if (d.flat == 8)   // bulk form: one "tile" per piece, no tile table
+            d.ntiles = d.nbulk;
+        else if (op.flat_only)
             GBX_TRY(gbx_build_tile_meta(nullptr, 0, cpe, d.ntiles, nullptr, op.d_tile_e0, req->stream));
         else
             GBX_TRY(gbx_build_tile_meta(d.segs, d.nseg, cpe, d.ntiles, op.d_tile_seg, op.d_tile_e0, req->stream));
@@ -414,6 +430,12 @@ static int time_op(gbx_request_s *req, HostOp &op, int block, int persistent, in
     return GBX_SUCCESS;
 }
 
+// algorithmic bytes of a copy in the form it runs in
+static void set_form_bytes(HostOp &op) {
+    if (op.kind != 0) return;
+    op.algo_bytes = op.cd.flat == 8 ? op.algo_bytes_bulk : op.cd.flat ? op.algo_bytes_flat : op.algo_bytes_seg;
+}
+
 static int tune_op(gbx_request_s *req, HostOp &op) {
     TuneKey key;
     memset(&key, 0, sizeof(key));
@@ -421,13 +443,14 @@ static int tune_op(gbx_request_s *req, HostOp &op) {
     key.units = op.units; key.elem_size = req->elem_size;
     key.nseg = op.kind == 0 ? op.cd.nseg : 0;
     key.nterms = op.kind == 1 ? op.fd.nchunks : 0;
-    key.flat_ok = op.kind == 0 ? op.flat_ok + 2 * op.flat_only + 4 * ((op.cd.flat & 3) == 3) : 0;
+    key.flat_ok = op.kind == 0 ? op.flat_ok + 2 * op.flat_only + 4 * ((op.cd.flat & 3) == 3) + 8 * op.bulk_ok : 0;
     int blocks[4] = {128, 256, 512, 1024};
     if (!req->autotune || req->forced_block) {
         op.block = req->forced_block ? req->forced_block : 256;
         op.persistent = 1;
         if (op.kind == 0 && !op.flat_only) op.cd.flat = op.flat_ok && req->forced_flat != 0;
-        if (op.kind == 0 && op.cd.flat) op.algo_bytes = op.algo_bytes_flat;
+        if (op.kind == 0 && op.bulk_ok && req->allow_bulk == 2) op.cd.flat = 8;
+        set_form_bytes(op);
         return set_vec(req, op, op.max_vec);
     }
     if (op.kind == 1 && op.fd.accumulate) {
@@ -447,7 +470,7 @@ static int tune_op(gbx_request_s *req, HostOp &op) {
             op.persistent = it->second.persistent;
             op.tuned_ms = it->second.ms;
             if (op.kind == 0) op.cd.flat = it->second.flat;
-            if (op.kind == 0 && op.cd.flat) op.algo_bytes = op.algo_bytes_flat;
+            set_form_bytes(op);
             return set_vec(req, op, it->second.vec);
         }
     }
@@ -459,12 +482,14 @@ static int tune_op(gbx_request_s *req, HostOp &op) {
     else if (op.flat_ok && req->forced_flat < 0) { forms.push_back(0); forms.push_back(1); forms.push_back(5); }
     else if (op.flat_ok && req->forced_flat > 0) { forms.push_back(1); forms.push_back(5); }
     else forms.push_back(0);
+    if (op.kind == 0 && op.bulk_ok && req->forced_flat != 1 && op.max_vec == 16) forms.push_back(8);
+    if (op.kind == 0 && op.bulk_ok && req->allow_bulk == 2) forms.assign(1, 8);   // forced where it applies
     for (int form : forms) {
         if (op.kind == 0) op.cd.flat = form;
-        const bool pipe = form >= 4;
-        for (int vec = op.max_vec; vec >= op.min_vec; vec >>= 1) {
+        const bool pipe = form >= 4 && form < 8, bulk = form == 8;
+        for (int vec = op.max_vec; vec >= (bulk ? 16 : op.min_vec); vec >>= 1) {
             GBX_TRY(set_vec(req, op, vec));
-            for (int bi = pipe ? 2 : 0; bi < 4; bi++)
+            for (int bi = pipe ? 2 : bulk ? 3 : 0; bi < 4; bi++)
                 for (int pers = 1; pers >= (pipe ? 1 : 0); pers--) {
                     float ms = 0;
                     GBX_TRY(time_op(req, op, blocks[bi], pers, 3, &ms));
@@ -477,7 +502,7 @@ static int tune_op(gbx_request_s *req, HostOp &op) {
     op.persistent = best.persistent;
     op.tuned_ms = best.ms;
     if (op.kind == 0) op.cd.flat = best.flat;
-    if (op.kind == 0 && op.cd.flat) op.algo_bytes = op.algo_bytes_flat;
+    set_form_bytes(op);
     GBX_TRY(set_vec(req, op, best.vec));
     std::lock_guard<std::mutex> lk(g_tune_mu);
     g_tune_cache[key] = best;
@@ -543,7 +568,7 @@ static int build_levels(DevPool &mem, const std::vector<HostOp *> &ops, const st
                 // and (payload type, vector width) for folds; a batch fuses all patterns of a
                 // class, with every copy that has the flat form in one flat launch whatever form
                 // it was tuned to alone (fewer, larger launches)
-                const int form = !batch ? op_flat(*op)
+                const int form = !batch || op_flat(*op) == 8 ? op_flat(*op)   // bulk ops pool only with bulk ops
                                         : (op->flat_ok ? ((op_flat(*op) & 3) == 3 ? 3 : 1) : 0);
                 std::pair<int, int> k = kind ? std::make_pair(dtypes[i], op_vec(*op))
                                              : std::make_pair(form, op_vec(*op));
@@ -717,6 +742,7 @@ static gbx_request_s *new_request(const Opts &o, void *stream) {
     req->no_single_split = !o.split;
     req->split_order = o.split_order;
     req->check_dup = o.check_dup;
+    req->allow_bulk = o.bulk;
     if (cudaEventCreateWithFlags(&req->done, cudaEventDisableTiming) != cudaSuccess) {
         cudaGetLastError();
         req->done = nullptr;

@@ -50,7 +50,18 @@ struct CopyDesc {
     int32_t src2_role;
     // two-index flat form (flat == 3): element e also writes destination element flat_didx[e]
     const int32_t *flat_didx;
+    // bulk form (flat == 8): contiguous pieces moved by the bulk-copy engine
+    const struct BulkTask *bulk;
+    int64_t nbulk;
 };
+
+// One piece of a bulk-form copy: len bytes (a multiple of 16, at most GBX_BULK_BYTES) from
+// byte src of the op's source to byte dst of its destination, both 16-byte aligned.
+struct BulkTask {
+    int64_t src, dst, len;
+};
+#define GBX_BULK_BYTES 32768             // bytes per bulk piece (one shared-memory stage)
+#define GBX_BULK_STAGES 4                // stages per CTA of the bulk kernel
 #define GBX_FLAT_SRC2 0x80000000u
 
 struct FoldDesc {

@@ -127,6 +127,11 @@ struct HostOp {
     int flat_ok;            // the flat form is available
     int flat_only;          // the op exists only in flat form (cd.flat is 1 or 3)
     int64_t algo_bytes_flat;
+    int64_t algo_bytes_bulk;
+    int64_t algo_bytes_seg;   // the segment form's
+    int bulk_ok;            // every segment is contiguous on both sides and 16-byte aligned
+    BulkTask *d_bulk;       // its pieces for the bulk form
+    int64_t nbulk;
     void **d_self;          // one-entry descriptor list for launching the op alone
     int64_t *d_self_prefix; // {0, ntiles}
 };
@@ -160,6 +165,7 @@ struct gbx_request_s {
     int no_single_split;     // keep single-term fold rows in the fold
     int split_order;         // single-term rows as copies: 0 in row (destination) order, 1 in source order
     int check_dup;           // locality form: compare every deduplicated value's bytes with its representative's at init
+    int allow_bulk;          // offer the bulk form to the autotuner where it applies
     int timeout_ms;
     gbx_graph_s *graph;
     gbx_request_s *forward;  // backward: its forward request
@@ -242,6 +248,10 @@ int gbx_split_single_rows(gbx_request_s *req, const int64_t *row_ptr, const int6
 int gbx_sort_pairs_by_source(gbx_request_s *req, int32_t *gs, int32_t *gd, int64_t n);
 int gbx_make_flat2_op(gbx_request_s *req, int level, const char *src, int src_role, const char *src2, int src2_role,
                       char *dst, int dst_role, const int32_t *gs, const int32_t *gd, int64_t nelem);
+int gbx_make_bulk(gbx_request_s *req, const Seg *segs, int64_t nseg, int64_t nelem, BulkTask **out, int64_t *n,
+                  int *ok);
+int gbx_bulk_prepare(void);
+int gbx_bulk_status_take(int *status);
 int gbx_make_flat(gbx_request_s *req, const Seg *segs, int64_t nseg, const int32_t *idx, int64_t nelem,
                   int32_t **flat_idx, int64_t *dst0, int *ok);
 int gbx_order_by_source(gbx_request_s *req, const Seg *segs, int64_t nseg, const int32_t *idx, int64_t nelem,

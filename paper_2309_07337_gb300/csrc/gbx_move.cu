@@ -332,6 +332,126 @@ gbx_copy_pipe_kernel(const CopyDesc *const *__restrict__ ops, const int64_t *__r
     copy_flat_pipelined<VEC, U, FORM>(ops[0], total_tiles);
 }
 
+// ------------------------------------------------------------------------ bulk
+// Bulk form: contiguous pieces moved through shared memory by the bulk-copy engine.  One
+// thread per CTA drives a ring of GBX_BULK_STAGES buffers: a piece is loaded with
+// cp.async.bulk (completion counted on the stage's mbarrier), stored back with a bulk store,
+// and a stage is refilled once the store before it has read it, so several pieces per CTA
+// are always in flight.  Every mbarrier wait is bounded: a wait that gives up sets
+// gbx_bulk_status, waits (bounded again) for the stage loads still in flight and for the
+// stores, and leaves the kernel.
+__device__ int gbx_bulk_status;
+
+__device__ __forceinline__ bool bulk_wait(uint32_t bar, uint32_t parity) {
+    for (int it = 0; it < (1 << 22); it++) {
+        uint32_t done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+            : "=r"(done)
+            : "r"(bar), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+__global__ void __launch_bounds__(32) gbx_bulk_kernel(const CopyDesc *const *__restrict__ ops,
+                                                      const int64_t *__restrict__ prefix, int nops,
+                                                      int64_t ntasks) {
+    extern __shared__ __align__(128) unsigned char gbx_bulk_smem[];
+    __shared__ __align__(8) uint64_t bar[GBX_BULK_STAGES];
+    if (threadIdx.x != 0) return;
+    constexpr int S = GBX_BULK_STAGES;
+    const uint32_t sbuf = (uint32_t)__cvta_generic_to_shared(gbx_bulk_smem);
+    const uint32_t sbar = (uint32_t)__cvta_generic_to_shared(bar);
+    for (int q = 0; q < S; q++) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(sbar + 8 * q) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    char *dst_of[S];
+    uint32_t len_of[S], parity[S];
+    bool pend[S];
+#pragma unroll
+    for (int q = 0; q < S; q++) {
+        parity[q] = 0;
+        pend[q] = false;
+        dst_of[q] = nullptr;
+        len_of[q] = 0;
+    }
+    auto load = [&](int q, int64_t t) {
+        const int op = nops > 1 ? find_op(prefix, nops, t) : 0;
+        const CopyDesc *d = ops[op];
+        const BulkTask k = d->bulk[t - (nops > 1 ? __ldg(prefix + op) : 0)];
+        const uint32_t b = sbar + 8 * q, len = (uint32_t)k.len;
+        // pieces were validated at init; a piece that is not a whole number of aligned 16-byte
+        // units within one stage is recorded and skipped
+        if (k.len <= 0 || k.len > GBX_BULK_BYTES || ((k.len | k.src | k.dst |
+                                                      (int64_t)(uintptr_t)d->src | (int64_t)(uintptr_t)d->dst) & 15)) {
+            atomicExch(&gbx_bulk_status, 2);
+            dst_of[q] = nullptr;
+            len_of[q] = 0;
+            pend[q] = false;
+            return;
+        }
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(b), "r"(len) : "memory");
+        asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                     ::"r"(sbuf + q * GBX_BULK_BYTES), "l"(d->src + k.src), "r"(len), "r"(b)
+                     : "memory");
+        dst_of[q] = d->dst + k.dst;
+        len_of[q] = len;
+        pend[q] = true;
+    };
+#pragma unroll
+    for (int q = 0; q < S; q++) {
+        const int64_t t = blockIdx.x + (int64_t)q * gridDim.x;
+        if (t < ntasks) load(q, t);
+    }
+    bool failed = false;
+    for (int64_t k = 0;; k++) {
+        const int64_t t = blockIdx.x + k * gridDim.x;
+        if (t >= ntasks) break;
+        const int q = (int)(k % S);
+        if (pend[q]) {
+            if (!bulk_wait(sbar + 8 * q, parity[q])) {
+                failed = true;
+                break;
+            }
+            parity[q] ^= 1u;
+            pend[q] = false;
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;"
+                         ::"l"(dst_of[q]), "r"(sbuf + q * GBX_BULK_BYTES), "r"(len_of[q])
+                         : "memory");
+        }
+        asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+        // refill the previous piece's stage once its store has read it
+        if (k >= 1) {
+            const int64_t tn = blockIdx.x + (k - 1 + S) * gridDim.x;
+            if (tn < ntasks) {
+                asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
+                load((int)((k - 1) % S), tn);
+            }
+        }
+    }
+    if (failed) {
+        atomicExch(&gbx_bulk_status, 1);
+        for (int q = 0; q < S; q++)
+            if (pend[q]) bulk_wait(sbar + 8 * q, parity[q]);
+    }
+    asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+}
+
+int gbx_bulk_prepare(void) {
+    cudaError_t e = cudaFuncSetAttribute(gbx_bulk_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         GBX_BULK_STAGES * GBX_BULK_BYTES);
+    return e == cudaSuccess ? GBX_SUCCESS : GBX_ERR_CUDA;
+}
+
+int gbx_bulk_status_take(int *status) {
+    int zero = 0;
+    GBX_CUDA_TRY(cudaMemcpyFromSymbol(status, gbx_bulk_status, sizeof(int)));
+    GBX_CUDA_TRY(cudaMemcpyToSymbol(gbx_bulk_status, &zero, sizeof(int)));
+    return GBX_SUCCESS;
+}
+
 // ------------------------------------------------------------------------ fold
 // Payload vectors: the CUDA vector type of `VEC` bytes of T, added component-wise with
 // IEEE round-to-nearest adds (never contracted, never reassociated).
@@ -543,6 +663,7 @@ int gbx_effective_block(int vec_class, int block) { return (vec_class == 0 && bl
 static int pipe_block(int flat, int block) { return (flat == 5 || flat == 7) && block < 512 ? 512 : block; }
 
 int gbx_occupancy(int kind, int dtype, int vec, int block, int flat) {
+    if (kind == 0 && flat == 8) return 1;   // the bulk kernel: one CTA per SM (its shared ring)
     if (kind == 0) block = pipe_block(flat, block);
     const void *f = kind == 0 ? (const void *)copy_fn(vec, block, flat) : (const void *)fold_fn(dtype, vec, block);
     int n = 0;
@@ -558,6 +679,11 @@ static int clamp_grid(int grid, int64_t total_tiles) {
 cudaError_t gbx_launch_copy(const CopyDesc *const *ops, const int64_t *tile_prefix, int nops, int64_t total_tiles,
                             int vec, int flat, int block, int grid, cudaStream_t st) {
     if (total_tiles <= 0) return cudaSuccess;
+    if (flat == 8) {   // bulk form: a "tile" is one piece
+        gbx_bulk_kernel<<<clamp_grid(grid, total_tiles), 32, GBX_BULK_STAGES * GBX_BULK_BYTES, st>>>(
+            ops, tile_prefix, nops, total_tiles);
+        return cudaGetLastError();
+    }
     if ((flat == 5 || flat == 7) && (nops > 1 || vec == 0)) flat -= 4;   // the pipelined kernels take one op
     block = pipe_block(flat, block);
     CopyFn f = copy_fn(vec, block, flat);

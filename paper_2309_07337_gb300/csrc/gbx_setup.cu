@@ -1158,6 +1158,15 @@ __global__ void check_flat_kernel(const int32_t *g, int64_t nelem, int64_t s, in
 __global__ void check_flat2_kernel(const int32_t *gs, const int32_t *gd, int64_t n, int64_t s, int64_t src_bytes,
                                    int64_t src2_bytes, int64_t dst_bytes, int *err);
 
+__global__ void check_bulk_kernel(const BulkTask *tasks, int64_t n, int64_t src_bytes, int64_t dst_bytes, int *err) {
+    FOR_EACH(m, n) {
+        const BulkTask k = tasks[m];
+        if (k.len <= 0 || k.len > GBX_BULK_BYTES || (k.len & 15) || (k.src & 15) || (k.dst & 15) || k.src < 0 ||
+            k.dst < 0 || k.src + k.len > src_bytes || k.dst + k.len > dst_bytes)
+            set_err(err, GBX_ERR_INTERNAL);
+    }
+}
+
 int gbx_validate_program(gbx_request_s *req, int64_t agg_bytes) {
     cudaStream_t st = req->stream;
     DevPool ws;
@@ -1177,6 +1186,9 @@ int gbx_validate_program(gbx_request_s *req, int64_t agg_bytes) {
             if (d.idx)
                 check_copy_idx_kernel<<<grid_of(d.nelem), SETUP_T, 0, st>>>(d.segs, d.nseg, d.nelem, d.idx,
                                                                             d.elem_size, bytes_of(d.src_role), err);
+            if (op.bulk_ok)
+                check_bulk_kernel<<<grid_of(op.nbulk), SETUP_T, 0, st>>>(op.d_bulk, op.nbulk, bytes_of(d.src_role),
+                                                                         bytes_of(d.dst_role), err);
             if (op.flat_ok && (d.flat & 3) == 3)
                 check_flat2_kernel<<<grid_of(d.nelem), SETUP_T, 0, st>>>(d.flat_idx, d.flat_didx, d.nelem, d.elem_size,
                                                                          bytes_of(d.src_role),
@@ -1425,6 +1437,63 @@ __global__ void flat_build_kernel(const Seg *segs, int64_t nseg, const int32_t *
         if (so % s != 0 || so / s > 0x7fffffffll) { atomicOr(bad, 1); continue; }
         g[v] = (int32_t)(so / s);
     }
+}
+
+// ------------------------------------------------------------------ bulk form
+// An op can move as bulk pieces when every segment is contiguous on both sides and its
+// offsets and byte length are multiples of 16; each segment is cut into pieces of at most
+// GBX_BULK_BYTES.
+__global__ void bulk_count_kernel(const Seg *segs, int64_t nseg, int64_t nelem, int64_t s, int64_t *npieces,
+                                  int *bad) {
+    FOR_EACH(q, nseg) {
+        const int64_t n = (q + 1 < nseg ? segs[q + 1].v0 : nelem) - segs[q].v0;
+        const int64_t bytes = n * s;
+        if (segs[q].idx_off >= 0 || (segs[q].src_off & 15) || (segs[q].dst_off & 15) || (bytes & 15)) *bad = 1;
+        npieces[q] = (bytes + GBX_BULK_BYTES - 1) / GBX_BULK_BYTES;
+    }
+}
+
+__global__ void bulk_fill_kernel(const Seg *segs, int64_t nseg, int64_t nelem, int64_t s, const int64_t *first,
+                                 BulkTask *tasks) {
+    FOR_EACH(q, nseg) {
+        const int64_t bytes = ((q + 1 < nseg ? segs[q + 1].v0 : nelem) - segs[q].v0) * s;
+        for (int64_t m = 0, off = 0; off < bytes; m++, off += GBX_BULK_BYTES) {
+            BulkTask k;
+            k.src = segs[q].src_off + off;
+            k.dst = segs[q].dst_off + off;
+            k.len = bytes - off < GBX_BULK_BYTES ? bytes - off : GBX_BULK_BYTES;
+            tasks[first[q] + m] = k;
+        }
+    }
+}
+
+int gbx_make_bulk(gbx_request_s *req, const Seg *segs, int64_t nseg, int64_t nelem, BulkTask **out, int64_t *n,
+                  int *ok) {
+    cudaStream_t st = req->stream;
+    *ok = 0;
+    *n = 0;
+    if (nseg <= 0 || nelem <= 0 || (req->align & 15)) return GBX_SUCCESS;
+    DevPool ws;
+    int *bad;
+    int64_t *np, *first;
+    GBX_TRY(ws.get(&bad, 1));
+    GBX_TRY(ws.get(&np, nseg));
+    GBX_TRY(ws.get(&first, nseg + 1));
+    GBX_CUDA_TRY(cudaMemsetAsync(bad, 0, sizeof(int), st));
+    bulk_count_kernel<<<grid_of(nseg), SETUP_T, 0, st>>>(segs, nseg, nelem, req->elem_size, np, bad);
+    GBX_CUDA_TRY(cudaGetLastError());
+    int hb = 0;
+    GBX_CUDA_TRY(cudaMemcpyAsync(&hb, bad, sizeof(int), cudaMemcpyDeviceToHost, st));
+    GBX_CUDA_TRY(cudaStreamSynchronize(st));
+    if (hb) return GBX_SUCCESS;
+    GBX_TRY(gbx_scan_i64(np, first, nseg, st, ws));
+    GBX_TRY(gbx_read_i64(first + nseg, n, st));
+    GBX_TRY(req->mem.get(out, *n));
+    bulk_fill_kernel<<<grid_of(nseg), SETUP_T, 0, st>>>(segs, nseg, nelem, req->elem_size, first, *out);
+    GBX_CUDA_TRY(cudaGetLastError());
+    GBX_TRY(gbx_bulk_prepare());
+    *ok = 1;
+    return GBX_SUCCESS;
 }
 
 int gbx_make_flat(gbx_request_s *req, const Seg *segs, int64_t nseg, const int32_t *idx, int64_t nelem,
