@@ -414,6 +414,7 @@ def run_ours(args):
     # --------------------------------------------------------------- extras
     if not args.no_extras and rank == 0:
         line["extras"] = extras(gbx, torch, p, field, halo_std, grad_halo, grad_field, dp, ex_std, bwd)
+    line["device_status"] = gbx.device_status()   # 0: no bounded wait of a move kernel gave up
     if rank == 0:
         print(json.dumps(line))
     if dist is not None:
