@@ -58,7 +58,7 @@ def parse_args():
     a.add_argument("--steps", type=int, default=100)
     a.add_argument("--warmup", type=int, default=5)
     a.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    a.add_argument("--e2e-steps", type=int, default=3)
+    a.add_argument("--e2e-steps", type=int, default=8)
     a.add_argument("--cpu-sample-ranks", type=int, default=4096,
                    help="receivers in the CPU-oracle baseline sample (4096 = the whole exchange)")
     a.add_argument("--no-extras", action="store_true")
@@ -404,55 +404,78 @@ def run_ours(args):
             "init_s": t_init}
 
     # ---------------------------------------------------------------- e2e
-    # One step end to end: the field and the incoming gradient come from pinned host memory,
-    # the two halos and the field's gradient go back to it.  The field is uploaded once for
-    # both forward forms; the halos' download overlaps the gradient's upload (separate copy
-    # engines); the exchanges run through the library's start / wait.
+    # Steps end to end: each step copies its inputs (the field, and the incoming gradient of the
+    # halo) in from pinned host memory and its results (both halos, the field's gradient) back.
+    # The field goes up once for both forward forms; the halos' download overlaps the gradient's
+    # upload; and with two device buffer sets, step k+1's uploads run while step k's downloads
+    # do (the two directions use separate copy engines).  The exchanges run through the
+    # persistent requests' start.
     if not args.no_e2e:
         hx = torch.empty(p.sendbuf_bytes, dtype=torch.uint8).pin_memory()
         hx.copy_(torch.from_numpy(x.view(np.uint8)))
-        hh1 = torch.empty(p.recvbuf_bytes, dtype=torch.uint8).pin_memory()
-        hh2 = torch.empty(p.recvbuf_bytes, dtype=torch.uint8).pin_memory()
         hg = torch.empty(p.recvbuf_bytes, dtype=torch.uint8).pin_memory()
         hg.copy_(grad_halo.view(torch.uint8).cpu())
-        hgf = torch.empty(p.sendbuf_bytes, dtype=torch.uint8).pin_memory()
         up, down = torch.cuda.Stream(), torch.cuda.Stream()
         comp = torch.cuda.current_stream()   # the requests' stream
-        fb, gb = field.view(torch.uint8), grad_halo.view(torch.uint8)
+        sets = []
+        for k in range(2):
+            S = {"field": field if k == 0 else torch.empty_like(field),
+                 "hs": halo_std if k == 0 else torch.empty_like(halo_std),
+                 "hl": halo_loc if k == 0 else torch.empty_like(halo_loc),
+                 "g": grad_halo if k == 0 else torch.empty_like(grad_halo),
+                 "gf": grad_field if k == 0 else torch.empty_like(grad_field)}
+            if k == 0:
+                S["reqs"] = reqs
+            else:
+                a = gbx.Exchange(p, S["field"], S["hs"], "standard", dp=dp, graph=ex_std.graph)
+                b = gbx.Exchange(p, S["field"], S["hl"], "locality", dp=dp, graph=ex_std.graph)
+                S["keep"] = (a, b)
+                S["reqs"] = [a.request, b.request, gbx.backward_init(a.request, S["g"], S["gf"])]
+            S["out"] = [torch.empty(p.recvbuf_bytes, dtype=torch.uint8).pin_memory(),
+                        torch.empty(p.recvbuf_bytes, dtype=torch.uint8).pin_memory(),
+                        torch.empty(p.sendbuf_bytes, dtype=torch.uint8).pin_memory()]
+            S["free"] = torch.cuda.Event()
+            S["free"].record(down)
+            sets.append(S)
 
-        def e2e_step():
+        def e2e_step(k):
+            S = sets[k % 2]
+            r_std, r_loc, r_bwd = S["reqs"]
+            up.wait_event(S["free"])          # this set's previous results have been read back
             with torch.cuda.stream(up):
-                fb.copy_(hx, non_blocking=True)
+                S["field"].view(torch.uint8).copy_(hx, non_blocking=True)
                 e_field = torch.cuda.Event()
                 e_field.record(up)
-                gb.copy_(hg, non_blocking=True)
+                S["g"].view(torch.uint8).copy_(hg, non_blocking=True)
                 e_grad = torch.cuda.Event()
                 e_grad.record(up)
             comp.wait_event(e_field)
-            ex_std.request.start()
-            ex_loc.request.start()
+            r_std.start()
+            r_loc.start()
             e_fwd = torch.cuda.Event()
             e_fwd.record(comp)
-            with torch.cuda.stream(down):
-                down.wait_event(e_fwd)
-                hh1.copy_(halo_std.view(torch.uint8), non_blocking=True)
-                hh2.copy_(halo_loc.view(torch.uint8), non_blocking=True)
             comp.wait_event(e_grad)
-            bwd.start()
+            r_bwd.start()
             e_bwd = torch.cuda.Event()
             e_bwd.record(comp)
+            for r in (r_std, r_loc, r_bwd):
+                r.wait_stream(comp)           # completes in stream order; the host does not block
             with torch.cuda.stream(down):
+                down.wait_event(e_fwd)
+                S["out"][0].copy_(S["hs"].view(torch.uint8), non_blocking=True)
+                S["out"][1].copy_(S["hl"].view(torch.uint8), non_blocking=True)
                 down.wait_event(e_bwd)
-                hgf.copy_(grad_field.view(torch.uint8), non_blocking=True)
-            for r in reqs:
-                r.wait()
-            down.synchronize()
-            up.synchronize()
-        e2e_step()
+                S["out"][2].copy_(S["gf"].view(torch.uint8), non_blocking=True)
+                S["free"].record(down)
+
+        for k in range(2):
+            e2e_step(k)
+        torch.cuda.synchronize()
         barrier()
         e0 = time.perf_counter()
-        for _ in range(args.e2e_steps):
-            e2e_step()
+        for k in range(args.e2e_steps):
+            e2e_step(k)
+        torch.cuda.synchronize()
         barrier()
         e_ms = (time.perf_counter() - e0) / args.e2e_steps * 1e3
         e_ms = max_over_ranks(e_ms, dist, device="cuda")
@@ -460,11 +483,13 @@ def run_ours(args):
                        "h2d_bytes_per_step": p.sendbuf_bytes + p.recvbuf_bytes,
                        "d2h_bytes_per_step": 2 * p.recvbuf_bytes + p.sendbuf_bytes,
                        "ms_per_step": e_ms, "steps": args.e2e_steps,
-                       "api": "pinned host field + gradient copied in, start/wait of the three requests, "
-                              "both halos + field gradient copied out; halo download overlaps gradient upload"}
-        assert torch.equal(hh1, hh2)
-        assert torch.equal(hgf.cuda(), grad_field.view(torch.uint8))
-        del hx, hh1, hh2, hg, hgf
+                       "api": "per step: pinned host field + gradient copied in, start of the three persistent "
+                              "requests, both halos + field gradient copied out; two device buffer sets, so a "
+                              "step's uploads overlap the previous step's downloads"}
+        for S in sets:
+            assert torch.equal(S["out"][0], S["out"][1])
+            assert torch.equal(S["out"][2].cuda(), sets[0]["gf"].view(torch.uint8))
+        del hx, hg, sets
 
     # ---------------------------------------------------------- cpu baseline
     if rank == 0 and not args.no_cpu:
