@@ -27,7 +27,11 @@ Two other modes print their own JSON line instead of the step's:
   --sweep  message-size sweep of the stencil at P = 4096: block edge 8/16/32 points x 1..16
            fp64 per point, standard and locality forms, cold L2;
   --faces  the standard exchange per direction class (x, y, z faces; edges and corners) of
-           the 512^3 stencil, with each class's 128-byte-line DRAM floor.
+           the 512^3 stencil, with each class's 128-byte-line DRAM floor;
+  --bwd-forms  the 512^3 backward (standard and locality order) in every program shape the
+           library offers (tuned default, bulk forms off, scatter form forced, single-term
+           rows folded, destination-ordered pairs), each checked bit for bit against the
+           default.
 """
 from __future__ import annotations
 
@@ -67,6 +71,8 @@ def parse_args():
     a.add_argument("--edge", type=int, default=32, help="block edge (32 = the 512^3 workload)")
     a.add_argument("--sweep", action="store_true",
                    help="instead of the step: message-size sweep, comps 1..16 x block edge 8..32 at P=4096")
+    a.add_argument("--bwd-forms", action="store_true",
+                   help="time the backward in each program shape (own JSON line)")
     a.add_argument("--faces", action="store_true",
                    help="instead of the step: standard exchange per face / edge+corner subset of the 512^3 "
                         "stencil, with the 128-byte-line DRAM floor of each")
@@ -960,6 +966,66 @@ def run_faces(args):
                       "rows": rows}))
 
 
+COPY_FORM_NAMES = {0: "segments", 1: "gather", 3: "two-index", 5: "gather pipelined", 7: "two-index pipelined",
+                   8: "bulk pieces", 9: "scatter windows"}
+
+
+def run_bwd_forms(args):
+    """The backward of the 512^3 exchange in each program shape, CUDA-event timed (median of
+    20 starts; the gradient buffers, 1.6 GB and 8.6 GB, exceed L2)."""
+    import torch
+    import paper_2309_07337_gb300 as gbx
+    peak, peak_kind = measured_peaks()
+    p = pt.config5(edge=args.edge)
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(pt.SEED + 5)
+    x = torch.rand(p.sendbuf_bytes // 8, dtype=torch.float64, device="cuda", generator=gen)
+    h = torch.zeros(p.recvbuf_bytes // 8, dtype=torch.float64, device="cuda")
+    g = torch.randn(p.recvbuf_bytes // 8, dtype=torch.float64, device="cuda", generator=gen)
+    shapes = ["", "bulk=0", "bulk=2", "single_split=0", "split_order=dest"]
+    rows = []
+    for alg in ("standard", "locality"):
+        ex = gbx.Exchange(p, x, h, alg)
+        ref = None
+        for info in shapes:
+            gs = torch.zeros_like(x)
+            b = gbx.backward_init(ex.request, g, gs, info=info)
+            for _ in range(3):
+                b.start()
+                b.wait()
+            ts = []
+            for _ in range(20):
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record()
+                b.start()
+                e1.record()
+                b.wait()
+                e1.synchronize()
+                ts.append(e0.elapsed_time(e1))
+            ms = statistics.median(ts)
+            i = b.info()
+            if ref is None:
+                ref = gs
+            forms = [COPY_FORM_NAMES.get(f, str(f)) for f in range(16) if i["copy_forms"] >> f & 1]
+            row = {"order": alg, "info": info or "(default)", "ms": ms, "launches": i["launches"],
+                   "copy_forms": forms, "block": i["block"], "algo_bytes": i["algo_bytes"],
+                   "algo_GBps": i["algo_bytes"] / (ms * 1e-3) / 1e9,
+                   "frac_of_measured_hbm": i["algo_bytes"] / (ms * 1e-3) / 1e9 / peak,
+                   "device_bytes": i["device_bytes"],
+                   "identical_to_default": bool(torch.equal(gs.view(torch.uint8), ref.view(torch.uint8)))}
+            rows.append(row)
+            print(json.dumps(row), file=sys.stderr)
+            del b
+            if gs is not ref:
+                del gs
+            torch.cuda.empty_cache()
+        del ex, ref
+        torch.cuda.empty_cache()
+    print(json.dumps({"bwd_forms": f"stencil27_{16 * args.edge}cube_P4096_c8", "peak_GBps": peak,
+                      "peak_kind": peak_kind, "rows": rows}))
+
+
 def main():
     args = parse_args()
     if args.impl == "reference":
@@ -968,6 +1034,8 @@ def main():
         run_sweep(args)
     elif args.faces:
         run_faces(args)
+    elif args.bwd_forms:
+        run_bwd_forms(args)
     else:
         run_ours(args)
 

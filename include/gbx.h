@@ -107,6 +107,9 @@ typedef struct {
     int64_t algo_bytes;     /* bytes the method must read and write per start,
                                index and descriptor reads included                    */
     int64_t device_bytes;   /* device memory the request owns                         */
+    int64_t copy_forms;     /* bit f set when some copy runs in form f: 0 segments,
+                               1 gather, 3 two-index, 5/7 pipelined 1/3, 8 bulk pieces,
+                               9 source windows scattered (fixed at init by the tuner) */
 } gbx_request_info_t;
 
 const char *gbx_error_string(int code);
@@ -189,7 +192,10 @@ int gbx_graph_free(gbx_graph_t *graph);
  *       timeout_ms=T       limit of gbx_wait (default 60000)
  *       bulk=0|1|2         offer the bulk form (contiguous pieces moved through shared memory
  *                          by the bulk-copy engine) to the autotuner where every block is
- *                          contiguous and 16-byte aligned (default 1; 2 forces it there)
+ *                          contiguous and 16-byte aligned (default 1; 2 forces it there).
+ *                          In a backward the same key offers (1) or forces (2) the scatter
+ *                          form of the single-term rows: source windows read by the
+ *                          bulk-copy engine, scattered to their destinations by the threads
  *       check_dup=0|1      locality form: at init, compare the bytes of every element that
  *                          shares a (node pair, global index) value with the value's
  *                          representative in the send buffer as bound then (default 0)
@@ -363,9 +369,13 @@ int gbx_alltoallv_init(gbx_comm_t comm, const void *sendbuf, int64_t sendbuf_byt
  * (dtype of the forward must be GBX_F32 or GBX_F64, elem_size a multiple of it); the
  * order is fixed, so results are bitwise reproducible.  Buffers and base offsets must be
  * aligned to the payload type (GBX_ERR_UNSUPPORTED otherwise).  The forward request must
- * outlive the backward one.  info: graph=, autotune=, timeout_ms=, vec=, block= as above;
- * single_split=0 keeps rows with a single term in the summing kernel (by default, without
- * accumulate, such rows are plain copies and run as one two-index gather-scatter). */
+ * outlive the backward one.  info: graph=, autotune=, timeout_ms=, vec=, block=, bulk= as
+ * above; single_split=0 keeps rows with a single term in the summing kernel (by default,
+ * without accumulate, such rows are plain copies and run as one two-index gather-scatter);
+ * split_order=auto|source|dest orders that copy's pairs by source or by destination (auto,
+ * the default: by source where the scatter form can run, that is 16-byte elements and
+ * alignment with bulk forms allowed, so the autotuner may pick it; else by destination);
+ * bulk=2 forces the scatter form where it applies. */
 int gbx_backward_init(gbx_request_t forward, const void *grad_recv, void *grad_send,
                       int accumulate, const char *info, void *stream,
                       gbx_request_t *request);

@@ -35,7 +35,7 @@ class RequestInfo(ctypes.Structure):
                [(n, ctypes.c_int64) for n in
                 ("elem_size", "V", "E", "E_nonzero", "V_direct", "V_inter", "U", "node_pairs",
                  "msgs_inter", "msgs_intra", "msgs_step1", "msgs_step3", "rows", "terms",
-                 "user_bytes", "algo_bytes", "device_bytes")]
+                 "user_bytes", "algo_bytes", "device_bytes", "copy_forms")]
 
     def as_dict(self):
         return {n: getattr(self, n) for n, _ in self._fields_}

@@ -55,7 +55,7 @@ struct Opts {
     int algorithm = GBX_ALG_STANDARD;
     int algorithm_auto = 0;
     int graph = 1, autotune = 1, vec = 0, block = 0, timeout_ms = 60000, min_run = 4, piece = 0, flat = -1;
-    int split = 1, split_order = 0;
+    int split = 1, split_order = 2;   // 2: source order where the scatter form can run, else dest
     int check_dup = 0, bulk = 1;
     bool ok = true;
 };
@@ -88,7 +88,7 @@ static Opts parse_info(const char *info) {
         else if (k == "piece") o.piece = atoi(v.c_str());
         else if (k == "flat") o.flat = atoi(v.c_str()) != 0;
         else if (k == "single_split") o.split = atoi(v.c_str()) != 0;
-        else if (k == "split_order") o.split_order = v == "source" ? 1 : v == "dest" ? 0 : -1;
+        else if (k == "split_order") o.split_order = v == "source" ? 1 : v == "dest" ? 0 : v == "auto" ? 2 : -1;
         else if (k == "check_dup") o.check_dup = atoi(v.c_str()) != 0;
         else if (k == "bulk") o.bulk = atoi(v.c_str());
         else o.ok = false;
@@ -255,6 +255,13 @@ int gbx_make_flat_op(gbx_request_s *req, int level, const char *src, int src_rol
     return GBX_SUCCESS;
 }
 
+// Single-term pairs run in source order when asked for, or by default where the scatter form
+// (16-byte elements and alignment, bulk forms allowed) can use them.
+static bool pairs_in_source_order(const gbx_request_s *req) {
+    return req->split_order == 1 ||
+           (req->split_order == 2 && req->allow_bulk && (req->elem_size & 15) == 0 && (req->align & 15) == 0);
+}
+
 int gbx_make_flat2_op(gbx_request_s *req, int level, const char *src, int src_role, const char *src2, int src2_role,
                       char *dst, int dst_role, const int32_t *gs, const int32_t *gd, int64_t nelem) {
     GBX_TRY(gbx_make_flat_op(req, level, src, src_role, src2, src2_role, dst, dst_role, gs, nelem, 0));
@@ -262,6 +269,12 @@ int gbx_make_flat2_op(gbx_request_s *req, int level, const char *src, int src_ro
     op.cd.flat = 3;
     op.cd.flat_didx = gd;
     op.algo_bytes = op.algo_bytes_flat = 2 * nelem * req->elem_size + 8 * nelem;
+    if (req->allow_bulk && pairs_in_source_order(req) && nelem > 0) {
+        GBX_TRY(gbx_make_scatter(req, gs, gd, nelem, &op.d_scat, &op.nscat, &op.scat_ok));
+        op.cd.scat = op.d_scat;
+        op.cd.nscat = op.nscat;
+        op.algo_bytes_scat = 2 * nelem * req->elem_size + 8 * nelem + op.nscat * (int64_t)sizeof(ScatterPiece);
+    }
     return GBX_SUCCESS;
 }
 
@@ -277,7 +290,9 @@ int gbx_make_fold_op(gbx_request_s *req, int level, char *out, int out_role, con
         GBX_TRY(gbx_split_single_rows(req, row_ptr, row_out, terms, nrows, &gs, &gd, &ns, &rp2, &ro2, &t2, &nm, &nt,
                                       &ok));
         if (ok) {
-            if (req->split_order == 1) GBX_TRY(gbx_sort_pairs_by_source(req, gs, gd, ns));
+            // source order (also what the scatter form needs); the two-index kernels run
+            // equally fast in either order
+            if (pairs_in_source_order(req)) GBX_TRY(gbx_sort_pairs_by_source(req, gs, gd, ns));
             GBX_TRY(gbx_make_flat2_op(req, level, bufA, a_role, bufB, b_role, out, out_role, gs, gd, ns));
             if (nm == 0) return GBX_SUCCESS;
             row_ptr = rp2;
@@ -345,6 +360,8 @@ static int set_vec(gbx_request_s *req, HostOp &op, int vec) {
         d.ntiles = ceil_div(d.nchunks, GBX_TILE);
         if (d.flat == 8)   // bulk form: one "tile" per piece, no tile table
             d.ntiles = d.nbulk;
+        else if (d.flat == 9)   // scatter form: one "tile" per source window
+            d.ntiles = d.nscat;
         else if (op.flat_only)
             GBX_TRY(gbx_build_tile_meta(nullptr, 0, cpe, d.ntiles, nullptr, op.d_tile_e0, req->stream));
         else
@@ -433,7 +450,9 @@ static int time_op(gbx_request_s *req, HostOp &op, int block, int persistent, in
 // algorithmic bytes of a copy in the form it runs in
 static void set_form_bytes(HostOp &op) {
     if (op.kind != 0) return;
-    op.algo_bytes = op.cd.flat == 8 ? op.algo_bytes_bulk : op.cd.flat ? op.algo_bytes_flat : op.algo_bytes_seg;
+    op.algo_bytes = op.cd.flat == 8 ? op.algo_bytes_bulk
+                  : op.cd.flat == 9 ? op.algo_bytes_scat
+                  : op.cd.flat ? op.algo_bytes_flat : op.algo_bytes_seg;
 }
 
 static int tune_op(gbx_request_s *req, HostOp &op) {
@@ -443,13 +462,16 @@ static int tune_op(gbx_request_s *req, HostOp &op) {
     key.units = op.units; key.elem_size = req->elem_size;
     key.nseg = op.kind == 0 ? op.cd.nseg : 0;
     key.nterms = op.kind == 1 ? op.fd.nchunks : 0;
-    key.flat_ok = op.kind == 0 ? op.flat_ok + 2 * op.flat_only + 4 * ((op.cd.flat & 3) == 3) + 8 * op.bulk_ok : 0;
+    key.flat_ok = op.kind == 0 ? op.flat_ok + 2 * op.flat_only + 4 * ((op.cd.flat & 3) == 3) + 8 * op.bulk_ok +
+                                     16 * op.scat_ok + 32 * (req->allow_bulk == 2)   // forced forms tune apart
+                               : 0;
     int blocks[4] = {128, 256, 512, 1024};
     if (!req->autotune || req->forced_block) {
         op.block = req->forced_block ? req->forced_block : 256;
         op.persistent = 1;
         if (op.kind == 0 && !op.flat_only) op.cd.flat = op.flat_ok && req->forced_flat != 0;
         if (op.kind == 0 && op.bulk_ok && req->allow_bulk == 2) op.cd.flat = 8;
+        if (op.kind == 0 && op.scat_ok && req->allow_bulk == 2) op.cd.flat = 9;
         set_form_bytes(op);
         return set_vec(req, op, op.max_vec);
     }
@@ -483,13 +505,15 @@ static int tune_op(gbx_request_s *req, HostOp &op) {
     else if (op.flat_ok && req->forced_flat > 0) { forms.push_back(1); forms.push_back(5); }
     else forms.push_back(0);
     if (op.kind == 0 && op.bulk_ok && req->forced_flat != 1 && op.max_vec == 16) forms.push_back(8);
+    if (op.kind == 0 && op.scat_ok && op.max_vec == 16) forms.push_back(9);
     if (op.kind == 0 && op.bulk_ok && req->allow_bulk == 2) forms.assign(1, 8);   // forced where it applies
+    if (op.kind == 0 && op.scat_ok && req->allow_bulk == 2) forms.assign(1, 9);
     for (int form : forms) {
         if (op.kind == 0) op.cd.flat = form;
-        const bool pipe = form >= 4 && form < 8, bulk = form == 8;
+        const bool pipe = form >= 4 && form < 8, bulk = form >= 8;
         for (int vec = op.max_vec; vec >= (bulk ? 16 : op.min_vec); vec >>= 1) {
             GBX_TRY(set_vec(req, op, vec));
-            for (int bi = pipe ? 2 : bulk ? 3 : 0; bi < 4; bi++)
+            for (int bi = pipe ? 2 : form == 8 ? 3 : 0; bi < 4; bi++)
                 for (int pers = 1; pers >= (pipe ? 1 : 0); pers--) {
                     float ms = 0;
                     GBX_TRY(time_op(req, op, blocks[bi], pers, 3, &ms));
@@ -568,7 +592,7 @@ static int build_levels(DevPool &mem, const std::vector<HostOp *> &ops, const st
                 // and (payload type, vector width) for folds; a batch fuses all patterns of a
                 // class, with every copy that has the flat form in one flat launch whatever form
                 // it was tuned to alone (fewer, larger launches)
-                const int form = !batch || op_flat(*op) == 8 ? op_flat(*op)   // bulk ops pool only with bulk ops
+                const int form = !batch || op_flat(*op) >= 8 ? op_flat(*op)   // bulk / scatter ops pool only with their own kind
                                         : (op->flat_ok ? ((op_flat(*op) & 3) == 3 ? 3 : 1) : 0);
                 std::pair<int, int> k = kind ? std::make_pair(dtypes[i], op_vec(*op))
                                              : std::make_pair(form, op_vec(*op));
@@ -658,9 +682,11 @@ static void fill_info(gbx_request_s *req) {
     int nlev = 0;
     int64_t algo = 0;
     const HostOp *big = nullptr;
+    I.copy_forms = 0;
     for (const HostOp &op : req->ops) {
         nlev = std::max(nlev, op.level + 1);
         algo += op.algo_bytes;
+        if (op.kind == 0) I.copy_forms |= (int64_t)1 << op.cd.flat;
         if (!big || op.algo_bytes > big->algo_bytes) big = &op;
     }
     I.levels = nlev;

@@ -53,6 +53,23 @@ struct CopyDesc {
     // bulk form (flat == 8): contiguous pieces moved by the bulk-copy engine
     const struct BulkTask *bulk;
     int64_t nbulk;
+    // scatter form (flat == 9) of a two-index copy whose pairs (flat_idx, flat_didx) are sorted
+    // by source: the sources are read a window at a time by the bulk-copy engine and
+    // scattered from shared memory by the threads
+    const struct ScatterPiece *scat;
+    int64_t nscat;
+};
+
+// One window of a scatter-form copy: the source elements of sorted pairs m0 .. m0+n-1 lie in
+// nrun runs of contiguous source bytes, run r at [src + run_off[r], src + run_off[r] +
+// run_len[r]) (16-byte multiples, ascending, disjoint, inside [src, src + len), len at most
+// GBX_SCAT_WIN); the gaps between runs hold no pair's source and are not read.
+#define GBX_SCAT_RUNS 24
+#define GBX_SCAT_GAP 1024   // gaps up to this many bytes are read with their run
+struct ScatterPiece {
+    int64_t src, m0;
+    int32_t len, n, nrun, pad;
+    uint16_t run_off[GBX_SCAT_RUNS], run_len[GBX_SCAT_RUNS];
 };
 
 // One piece of a bulk-form copy: len bytes (a multiple of 16, at most GBX_BULK_BYTES) from
@@ -62,6 +79,13 @@ struct BulkTask {
 };
 #define GBX_BULK_BYTES 32768             // bytes per bulk piece (one shared-memory stage)
 #define GBX_BULK_STAGES 4                // stages per CTA of the bulk kernel
+// scatter form: a stage holds one source window of GBX_SCAT_WIN bytes, then the window's
+// source indices and its destination indices (at most GBX_SCAT_MAXN pairs, each index copy
+// rounded out to 16-byte boundaries, so the index arrays carry 4 elements of padding)
+#define GBX_SCAT_WIN 16384
+#define GBX_SCAT_MAXN (GBX_SCAT_WIN / 16)
+#define GBX_SCAT_IDX (GBX_SCAT_MAXN * 4 + 16)
+#define GBX_SCAT_STAGE (GBX_SCAT_WIN + 2 * GBX_SCAT_IDX)
 #define GBX_FLAT_SRC2 0x80000000u
 
 struct FoldDesc {

@@ -132,6 +132,10 @@ struct HostOp {
     int bulk_ok;            // every segment is contiguous on both sides and 16-byte aligned
     BulkTask *d_bulk;       // its pieces for the bulk form
     int64_t nbulk;
+    int scat_ok;            // two-index copy with the scatter form available
+    ScatterPiece *d_scat;
+    int64_t nscat;
+    int64_t algo_bytes_scat;
     void **d_self;          // one-entry descriptor list for launching the op alone
     int64_t *d_self_prefix; // {0, ntiles}
 };
@@ -251,6 +255,11 @@ int gbx_make_flat2_op(gbx_request_s *req, int level, const char *src, int src_ro
 int gbx_make_bulk(gbx_request_s *req, const Seg *segs, int64_t nseg, int64_t nelem, BulkTask **out, int64_t *n,
                   int *ok);
 int gbx_bulk_prepare(void);
+int gbx_scatter_prepare(void);
+// Scatter-form windows of a two-index copy whose pairs (gs, gd) are sorted by source and
+// whose arrays carry 4 elements of padding; *ok = 0 where the form does not apply.
+int gbx_make_scatter(gbx_request_s *req, const int32_t *gs, const int32_t *gd, int64_t n, ScatterPiece **pieces,
+                     int64_t *npieces, int *ok);
 int gbx_bulk_status_take(int *status);
 int gbx_make_flat(gbx_request_s *req, const Seg *segs, int64_t nseg, const int32_t *idx, int64_t nelem,
                   int32_t **flat_idx, int64_t *dst0, int *ok);

@@ -445,6 +445,192 @@ int gbx_bulk_prepare(void) {
     return e == cudaSuccess ? GBX_SUCCESS : GBX_ERR_CUDA;
 }
 
+// ----------------------------------------------------------------- scatter
+// Scatter form of a two-index copy whose pairs are sorted by source: each piece is a window of
+// the source.  Thread 0 has the bulk-copy engine read the window's runs of source elements
+// (the gaps between them are not read) and the window's source and destination indices into
+// one of S shared-memory stages (one mbarrier counts every copy), and the threads then
+// scatter the window's elements from shared memory to their destinations with 16-byte stores,
+// so the only global accesses left in the threads are the stores.  Piece descriptors are
+// staged in shared memory; thread 0 fetches the next one while the current window is
+// scattered.  Every thread waits on the stage's mbarrier itself (bounded); a block-wide vote
+// makes the decision to give up uniform, so no barrier is ever left waiting.
+template <int NT, int S>
+__global__ void __launch_bounds__(NT) gbx_scatter_kernel(const CopyDesc *const *__restrict__ ops,
+                                                         const int64_t *__restrict__ prefix, int nops,
+                                                         int64_t npieces) {
+    extern __shared__ __align__(128) unsigned char gbx_scatter_smem[];
+    __shared__ __align__(8) uint64_t bar[S];
+    __shared__ int loaded[S];
+    __shared__ ScatterPiece piece_s[S];
+    __shared__ __align__(16) ScatterPiece next_s;   // the next refill's piece, fetched ahead
+    __shared__ const CopyDesc *desc_s[S];
+    const uint32_t sbuf = (uint32_t)__cvta_generic_to_shared(gbx_scatter_smem);
+    const uint32_t sbar = (uint32_t)__cvta_generic_to_shared(bar);
+    auto piece_ptr = [&](int64_t t, const CopyDesc *&d) {
+        const int op = nops > 1 ? find_op(prefix, nops, t) : 0;
+        d = ops[op];
+        return d->scat + (t - (nops > 1 ? __ldg(prefix + op) : 0));
+    };
+    // thread 0: starts an asynchronous copy of piece t into next_s (8 x 16 bytes)
+    auto fetch = [&](int64_t t, const CopyDesc *&d) {
+        const char *g = reinterpret_cast<const char *>(piece_ptr(t, d));
+        const uint32_t sl = (uint32_t)__cvta_generic_to_shared(&next_s);
+#pragma unroll
+        for (int i = 0; i < (int)sizeof(ScatterPiece) / 16; i++)
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sl + 16 * i), "l"(g + 16 * i) : "memory");
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    };
+    auto fetched = [&]() { asm volatile("cp.async.wait_all;" ::: "memory"); };
+    auto issue = [&](int q, const ScatterPiece &P, const CopyDesc *d) {   // thread 0 only
+        // index copies rounded out to 16-byte boundaries (the index arrays carry padding)
+        const int64_t i0 = (P.m0 * 4) & ~(int64_t)15, i1 = ((P.m0 + P.n) * 4 + 15) & ~(int64_t)15;
+        bool good = P.len > 0 && P.len <= GBX_SCAT_WIN && P.n > 0 && P.n <= GBX_SCAT_MAXN && P.m0 >= 0 &&
+                    P.nrun > 0 && P.nrun <= GBX_SCAT_RUNS &&
+                    ((P.src | (int64_t)(uintptr_t)d->src | (int64_t)(uintptr_t)d->flat_idx |
+                      (int64_t)(uintptr_t)d->flat_didx) & 15) == 0;
+        uint32_t bytes = 0;
+        for (int r = 0; good && r < P.nrun; r++) {
+            const uint32_t o = P.run_off[r], l = P.run_len[r];
+            good = ((o | l) & 15) == 0 && l > 0 && o + l <= (uint32_t)P.len;
+            bytes += l;
+        }
+        if (!good) {   // validated at init; recorded and skipped
+            atomicExch(&gbx_bulk_status, 2);
+            loaded[q] = 0;
+            return;
+        }
+        const uint32_t b = sbar + 8 * q, ilen = (uint32_t)(i1 - i0);
+        const uint32_t stage = sbuf + q * GBX_SCAT_STAGE;
+        piece_s[q] = P;
+        desc_s[q] = d;
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(b), "r"(bytes + 2 * ilen)
+                     : "memory");
+        for (int r = 0; r < P.nrun; r++)
+            asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                         ::"r"(stage + P.run_off[r]), "l"(d->src + P.src + P.run_off[r]), "r"((uint32_t)P.run_len[r]),
+                         "r"(b)
+                         : "memory");
+        asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                     ::"r"(stage + GBX_SCAT_WIN), "l"(reinterpret_cast<const char *>(d->flat_idx) + i0), "r"(ilen),
+                     "r"(b)
+                     : "memory");
+        asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                     ::"r"(stage + GBX_SCAT_WIN + GBX_SCAT_IDX),
+                     "l"(reinterpret_cast<const char *>(d->flat_didx) + i0), "r"(ilen), "r"(b)
+                     : "memory");
+        loaded[q] = 1;
+    };
+    if (threadIdx.x == 0) {
+        for (int q = 0; q < S; q++) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(sbar + 8 * q) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        for (int q = 0; q < S; q++) {
+            const int64_t t = blockIdx.x + (int64_t)q * gridDim.x;
+            loaded[q] = 0;
+            if (t < npieces) {
+                const CopyDesc *d;
+                fetch(t, d);
+                fetched();
+                issue(q, next_s, d);
+            }
+        }
+    }
+    __syncthreads();
+    uint32_t parity[S];
+#pragma unroll
+    for (int q = 0; q < S; q++) parity[q] = 0;
+    bool failed = false;
+    for (int64_t k = 0;; k++) {
+        const int64_t t = blockIdx.x + k * gridDim.x;
+        if (t >= npieces) break;
+        const int q = (int)(k % S);
+        const int64_t tn = t + (int64_t)S * gridDim.x;
+        const CopyDesc *nd = nullptr;
+        if (threadIdx.x == 0 && tn < npieces) fetch(tn, nd);
+        const bool have = loaded[q] != 0;
+        bool ok = true;
+        if (have) {
+            ok = bulk_wait(sbar + 8 * q, parity[q]);
+            if (ok) parity[q] ^= 1u;
+        }
+        if (!__syncthreads_and(ok)) {
+            failed = true;
+            break;
+        }
+        if (have) {
+            const CopyDesc *d = desc_s[q];
+            const int64_t src0 = piece_s[q].src, m0 = piece_s[q].m0;
+            const int s = (int)d->elem_size, cpe = s >> 4, len = piece_s[q].len, n = piece_s[q].n;
+            const unsigned char *win = gbx_scatter_smem + q * GBX_SCAT_STAGE;
+            const int32_t *ps = reinterpret_cast<const int32_t *>(win + GBX_SCAT_WIN) + (m0 & 3);
+            const int32_t *pd = reinterpret_cast<const int32_t *>(win + GBX_SCAT_WIN + GBX_SCAT_IDX) + (m0 & 3);
+            char *dst = d->dst;
+            for (int i = threadIdx.x; i < n * cpe; i += NT) {
+                const int j = i / cpe, c = i - j * cpe;
+                const int64_t w = (int64_t)ps[j] * s - src0 + c * 16;
+                if (w < 0 || w + 16 > len) {   // validated at init; recorded and skipped
+                    atomicExch(&gbx_bulk_status, 2);
+                    continue;
+                }
+                const uint4 v = *reinterpret_cast<const uint4 *>(win + w);
+                stv<16>(dst + (int64_t)pd[j] * s + c * 16, v);
+            }
+        }
+        __syncthreads();   // every thread is done with stage q
+        if (threadIdx.x == 0) {
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // reads before the refill
+            loaded[q] = 0;
+            if (tn < npieces) {
+                fetched();
+                issue(q, next_s, nd);
+            }
+        }
+        __syncthreads();
+    }
+    if (failed && threadIdx.x == 0) {
+        atomicExch(&gbx_bulk_status, 1);
+        fetched();
+        for (int q = 0; q < S; q++)
+            if (loaded[q]) bulk_wait(sbar + 8 * q, parity[q]);
+    }
+}
+
+// Shapes of the scatter kernel, chosen by the launch's block value: threads per CTA, stages
+// per CTA and CTAs per SM (each shape fills about 192 KB of shared memory per SM).
+struct ScatShape { int nt, stages, per_sm; };
+static ScatShape scatter_shape(int block) {
+    if (block <= 128) return {256, 2, 4};
+    if (block <= 256) return {256, 4, 2};
+    if (block <= 512) return {512, 4, 2};
+    return {1024, 8, 1};
+}
+
+static cudaError_t scatter_launch(int block, int grid, cudaStream_t st, const CopyDesc *const *ops,
+                                  const int64_t *prefix, int nops, int64_t n) {
+    const ScatShape h = scatter_shape(block);
+    const size_t smem = (size_t)h.stages * GBX_SCAT_STAGE;
+    if (h.stages == 2) gbx_scatter_kernel<256, 2><<<grid, 256, smem, st>>>(ops, prefix, nops, n);
+    else if (h.nt == 256) gbx_scatter_kernel<256, 4><<<grid, 256, smem, st>>>(ops, prefix, nops, n);
+    else if (h.nt == 512) gbx_scatter_kernel<512, 4><<<grid, 512, smem, st>>>(ops, prefix, nops, n);
+    else gbx_scatter_kernel<1024, 8><<<grid, 1024, smem, st>>>(ops, prefix, nops, n);
+    return cudaGetLastError();
+}
+
+int gbx_scatter_prepare(void) {
+    cudaError_t e = cudaFuncSetAttribute(gbx_scatter_kernel<256, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         2 * GBX_SCAT_STAGE);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(gbx_scatter_kernel<256, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 4 * GBX_SCAT_STAGE);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(gbx_scatter_kernel<512, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 4 * GBX_SCAT_STAGE);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(gbx_scatter_kernel<1024, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 8 * GBX_SCAT_STAGE);
+    return e == cudaSuccess ? GBX_SUCCESS : GBX_ERR_CUDA;
+}
+
 int gbx_bulk_status_take(int *status) {
     int zero = 0;
     GBX_CUDA_TRY(cudaMemcpyFromSymbol(status, gbx_bulk_status, sizeof(int)));
@@ -663,7 +849,8 @@ int gbx_effective_block(int vec_class, int block) { return (vec_class == 0 && bl
 static int pipe_block(int flat, int block) { return (flat == 5 || flat == 7) && block < 512 ? 512 : block; }
 
 int gbx_occupancy(int kind, int dtype, int vec, int block, int flat) {
-    if (kind == 0 && flat == 8) return 1;   // the bulk kernel: one CTA per SM (its shared ring)
+    if (kind == 0 && flat == 8) return 1;   // bulk kernel: one CTA per SM (its ring)
+    if (kind == 0 && flat == 9) return scatter_shape(block).per_sm;
     if (kind == 0) block = pipe_block(flat, block);
     const void *f = kind == 0 ? (const void *)copy_fn(vec, block, flat) : (const void *)fold_fn(dtype, vec, block);
     int n = 0;
@@ -683,6 +870,9 @@ cudaError_t gbx_launch_copy(const CopyDesc *const *ops, const int64_t *tile_pref
         gbx_bulk_kernel<<<clamp_grid(grid, total_tiles), 32, GBX_BULK_STAGES * GBX_BULK_BYTES, st>>>(
             ops, tile_prefix, nops, total_tiles);
         return cudaGetLastError();
+    }
+    if (flat == 9) {   // scatter form: a "tile" is one source window
+        return scatter_launch(block, clamp_grid(grid, total_tiles), st, ops, tile_prefix, nops, total_tiles);
     }
     if ((flat == 5 || flat == 7) && (nops > 1 || vec == 0)) flat -= 4;   // the pipelined kernels take one op
     block = pipe_block(flat, block);

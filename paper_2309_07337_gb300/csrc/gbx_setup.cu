@@ -1158,6 +1158,152 @@ __global__ void check_flat_kernel(const int32_t *g, int64_t nelem, int64_t s, in
 __global__ void check_flat2_kernel(const int32_t *gs, const int32_t *gd, int64_t n, int64_t s, int64_t src_bytes,
                                    int64_t src2_bytes, int64_t dst_bytes, int *err);
 
+// ---------------------------------------------------------------- scatter form
+// A two-index copy can be read a source window at a time when its element size is a multiple
+// of 16 bytes and at most one window, its buffers are 16-byte aligned, and no pair reads the
+// second buffer.  The pairs, sorted by source, are grouped by aligned GBX_SCAT_WIN-byte
+// window of the source; one thread per window walks its pairs and cuts them into pieces of
+// at most GBX_SCAT_RUNS runs and GBX_SCAT_MAXN pairs.  A run is a stretch of source elements
+// with no gap longer than GBX_SCAT_GAP bytes: a short gap is cheaper to read than to skip
+// with another bulk copy.
+__global__ void scatter_flag_kernel(const int32_t *gs, int64_t n, int64_t w, int64_t *flag, int *bad) {
+    FOR_EACH(m, n) {
+        const uint32_t x = (uint32_t)gs[m];
+        if (x & GBX_FLAT_SRC2) *bad = 1;
+        if (m > 0 && (uint32_t)gs[m - 1] > x) *bad = 1;   // not in source order
+        flag[m] = m == 0 || (int64_t)x / w != (int64_t)(uint32_t)gs[m - 1] / w;
+    }
+}
+
+__global__ void scatter_start_kernel(const int64_t *flag, const int64_t *pid, int64_t n, int64_t *start) {
+    FOR_EACH(m, n) if (flag[m]) start[pid[m]] = m;
+}
+
+// Walks window w's pairs; counts its pieces (out == nullptr) or writes them from out[0].
+__device__ int64_t scatter_walk(const int32_t *gs, int64_t m0, int64_t m1, int64_t s, ScatterPiece *out) {
+    int64_t np = 0;
+    ScatterPiece k;
+    int64_t run_lo = 0, run_hi = 0;   // current run, in source elements [lo, hi]
+    auto close_run = [&]() {
+        k.run_off[k.nrun] = (uint16_t)((run_lo * s) - k.src);
+        k.run_len[k.nrun] = (uint16_t)((run_hi + 1 - run_lo) * s);
+        k.nrun++;
+        k.len = (int32_t)((run_hi + 1) * s - k.src);
+    };
+    for (int64_t m = m0; m < m1; m++) {
+        const int64_t x = gs[m];
+        const bool open = m > m0 && k.n < GBX_SCAT_MAXN;
+        if (open && (x - run_hi - 1) * s <= GBX_SCAT_GAP) {   // extends the current run (reading a short gap)
+            run_hi = x > run_hi ? x : run_hi;
+            k.n++;
+            continue;
+        }
+        if (open && k.nrun + 1 < GBX_SCAT_RUNS) {   // a new run in the same piece
+            close_run();
+            run_lo = run_hi = x;
+            k.n++;
+            continue;
+        }
+        if (m > m0) {   // close the piece
+            close_run();
+            if (out) out[np] = k;
+            np++;
+        }
+        k.src = x * s;
+        k.m0 = m;
+        k.n = 1;
+        k.nrun = 0;
+        k.pad = 0;
+        run_lo = run_hi = x;
+    }
+    if (m1 > m0) {
+        close_run();
+        if (out) out[np] = k;
+        np++;
+    }
+    return np;
+}
+
+__global__ void scatter_count_kernel(const int32_t *gs, const int64_t *start, int64_t nw, int64_t n, int64_t s,
+                                     int64_t *cnt) {
+    FOR_EACH(w, nw) cnt[w] = scatter_walk(gs, start[w], w + 1 < nw ? start[w + 1] : n, s, nullptr);
+}
+
+__global__ void scatter_fill_kernel(const int32_t *gs, const int64_t *start, const int64_t *off, int64_t nw,
+                                    int64_t n, int64_t s, ScatterPiece *pieces) {
+    FOR_EACH(w, nw) scatter_walk(gs, start[w], w + 1 < nw ? start[w + 1] : n, s, pieces + off[w]);
+}
+
+int gbx_make_scatter(gbx_request_s *req, const int32_t *gs, const int32_t *gd, int64_t n, ScatterPiece **pieces,
+                     int64_t *npieces, int *ok) {
+    cudaStream_t st = req->stream;
+    const int64_t s = req->elem_size;
+    (void)gd;
+    *ok = 0;
+    *npieces = 0;
+    if (n <= 0 || (s & 15) || s > GBX_SCAT_WIN || (req->align & 15)) return GBX_SUCCESS;
+    DevPool ws;
+    int *bad;
+    int64_t *flag, *wid, *start, *cnt, *off;
+    GBX_TRY(ws.get(&bad, 1));
+    GBX_TRY(ws.get(&flag, n));
+    GBX_TRY(ws.get(&wid, n + 1));
+    GBX_CUDA_TRY(cudaMemsetAsync(bad, 0, sizeof(int), st));
+    scatter_flag_kernel<<<grid_of(n), SETUP_T, 0, st>>>(gs, n, GBX_SCAT_WIN / s, flag, bad);
+    GBX_CUDA_TRY(cudaGetLastError());
+    int hb = 0;
+    GBX_CUDA_TRY(cudaMemcpyAsync(&hb, bad, sizeof(int), cudaMemcpyDeviceToHost, st));
+    GBX_CUDA_TRY(cudaStreamSynchronize(st));
+    if (hb) return GBX_SUCCESS;
+    GBX_TRY(gbx_scan_i64(flag, wid, n, st, ws));
+    int64_t nw = 0, np = 0;
+    GBX_TRY(gbx_read_i64(wid + n, &nw, st));
+    GBX_TRY(ws.get(&start, nw));
+    GBX_TRY(ws.get(&cnt, nw));
+    GBX_TRY(ws.get(&off, nw + 1));
+    scatter_start_kernel<<<grid_of(n), SETUP_T, 0, st>>>(flag, wid, n, start);
+    GBX_CUDA_TRY(cudaGetLastError());
+    scatter_count_kernel<<<grid_of(nw), SETUP_T, 0, st>>>(gs, start, nw, n, s, cnt);
+    GBX_CUDA_TRY(cudaGetLastError());
+    GBX_TRY(gbx_scan_i64(cnt, off, nw, st, ws));
+    GBX_TRY(gbx_read_i64(off + nw, &np, st));
+    GBX_TRY(req->mem.get(pieces, np));
+    scatter_fill_kernel<<<grid_of(nw), SETUP_T, 0, st>>>(gs, start, off, nw, n, s, *pieces);
+    GBX_CUDA_TRY(cudaGetLastError());
+    GBX_CUDA_TRY(cudaStreamSynchronize(st));
+    GBX_TRY(gbx_scatter_prepare());
+    *npieces = np;
+    *ok = 1;
+    return GBX_SUCCESS;
+}
+
+// every piece inside the source and at most one window, its runs aligned, ascending and
+// disjoint inside it, its pairs inside the index arrays; every pair's source inside one of
+// its piece's runs and its destination inside the destination
+__global__ void check_scatter_kernel(const ScatterPiece *pieces, int64_t np, const int32_t *gs, const int32_t *gd,
+                                     int64_t n, int64_t s, int64_t src_bytes, int64_t dst_bytes, int *err) {
+    FOR_EACH(p, np) {
+        const ScatterPiece k = pieces[p];
+        bool good = k.len > 0 && k.len <= GBX_SCAT_WIN && (k.src & 15) == 0 && k.src >= 0 &&
+                    k.src + k.len <= src_bytes && k.m0 >= 0 && k.n > 0 && k.n <= GBX_SCAT_MAXN && k.m0 + k.n <= n &&
+                    k.nrun > 0 && k.nrun <= GBX_SCAT_RUNS && ((uintptr_t)gs & 15) == 0 && ((uintptr_t)gd & 15) == 0;
+        int64_t end = 0;
+        for (int r = 0; good && r < k.nrun; r++) {
+            const int64_t o = k.run_off[r], l = k.run_len[r];
+            good = (o & 15) == 0 && (l & 15) == 0 && l > 0 && o >= end && o + l <= k.len;
+            end = o + l;
+        }
+        int r = 0;
+        for (int64_t m = k.m0; good && m < k.m0 + k.n; m++) {
+            const int64_t a = (int64_t)(uint32_t)gs[m] * s - k.src;
+            while (r < k.nrun && a >= k.run_off[r] + k.run_len[r]) r++;
+            good = r < k.nrun && a >= k.run_off[r] && a + s <= k.run_off[r] + k.run_len[r] && gd[m] >= 0 &&
+                   ((int64_t)gd[m] + 1) * s <= dst_bytes;
+        }
+        if (!good) set_err(err, GBX_ERR_INTERNAL);
+    }
+}
+
 __global__ void check_bulk_kernel(const BulkTask *tasks, int64_t n, int64_t src_bytes, int64_t dst_bytes, int *err) {
     FOR_EACH(m, n) {
         const BulkTask k = tasks[m];
@@ -1189,6 +1335,10 @@ int gbx_validate_program(gbx_request_s *req, int64_t agg_bytes) {
             if (op.bulk_ok)
                 check_bulk_kernel<<<grid_of(op.nbulk), SETUP_T, 0, st>>>(op.d_bulk, op.nbulk, bytes_of(d.src_role),
                                                                          bytes_of(d.dst_role), err);
+            if (op.scat_ok)
+                check_scatter_kernel<<<grid_of(op.nscat), SETUP_T, 0, st>>>(
+                    op.d_scat, op.nscat, d.flat_idx, d.flat_didx, d.nelem, d.elem_size, bytes_of(d.src_role),
+                    bytes_of(d.dst_role), err);
             if (op.flat_ok && (d.flat & 3) == 3)
                 check_flat2_kernel<<<grid_of(d.nelem), SETUP_T, 0, st>>>(d.flat_idx, d.flat_didx, d.nelem, d.elem_size,
                                                                          bytes_of(d.src_role),
@@ -1595,7 +1745,7 @@ int gbx_split_single_rows(gbx_request_s *req, const int64_t *row_ptr, const int6
     GBX_TRY(gbx_read_i64(mrow + nrows, &nm, st));
     GBX_TRY(gbx_read_i64(mterm + nrows, &nt, st));
     if (ns == 0) return GBX_SUCCESS;
-    GBX_TRY(req->mem.get(gs, ns)); GBX_TRY(req->mem.get(gd, ns));
+    GBX_TRY(req->mem.get(gs, ns + 4)); GBX_TRY(req->mem.get(gd, ns + 4));   // padding for the scatter form
     GBX_TRY(req->mem.get(row_ptr2, nm + 1)); GBX_TRY(req->mem.get(row_out2, nm)); GBX_TRY(req->mem.get(terms2, nt));
     row_split_kernel<<<grid_of(nrows), SETUP_T, 0, st>>>(row_ptr, row_out, terms, nrows, req->elem_size, sidx, mrow,
                                                          mterm, *gs, *gd, *row_ptr2, *row_out2, *terms2, bad);

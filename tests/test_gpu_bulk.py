@@ -15,7 +15,7 @@ if not torch.cuda.is_available():
 import oracle  # noqa: E402
 import paper_2309_07337_gb300 as gbx  # noqa: E402
 from paper_2309_07337_gb300 import patterns as pt  # noqa: E402
-from gpu_util import assert_bytes_equal, dev_bytes, forward, payload  # noqa: E402
+from gpu_util import assert_bytes_equal, backward, dev_bytes, forward, grad_payload, payload  # noqa: E402
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -110,3 +110,86 @@ def test_full_size_locality_bulk():
     a.start(); a.wait()
     b.start(); b.wait()
     assert torch.equal(h1.view(torch.uint8), h2.view(torch.uint8))
+
+
+SCATTER = 1 << 9
+
+
+@pytest.mark.parametrize("seed,s", [(11, 16), (12, 32), (13, 64), (14, 128), (15, 4096)])
+def test_backward_scatter_form(seed, s):
+    """The reverse exchange's one-term rows in the scatter form (source windows read by the
+    bulk-copy engine, scattered to their destinations by threads) give the oracle's bytes,
+    alone and beside the folded rows, with and without accumulation (an accumulating
+    backward folds every row, so it must equal the oracle too)."""
+    for p in (pt.random_pattern(seed, P=24, elem_size=s, dtype="f64", gaps=False, max_count=12, max_deg=8),
+              pt.config5(edge=4, comps=s // 8) if s <= 128 else None):
+        if p is None:
+            continue
+        x = payload(p, 1)
+        g = grad_payload(p, 2)
+        old = payload(p, 3)
+        for alg, form in (("standard", 0), ("locality", 1)):
+            _, ex = forward(p, x, alg)
+            got, b = backward(ex, g, info="bulk=2")
+            assert_bytes_equal(got, oracle.backward(p, g, form=form), f"{p.name} {alg} s={s}")
+            if alg == "standard" and p.volume > 0:   # one-term rows all read the one gradient buffer
+                assert b.info()["copy_forms"] & SCATTER, (p.name, b.info()["copy_forms"])
+            got, _ = backward(ex, g, old, accumulate=True, info="bulk=2")
+            assert_bytes_equal(got, oracle.backward(p, g, old, form=form, accumulate=True),
+                               f"{p.name} {alg} s={s} acc")
+
+
+@pytest.mark.parametrize("info", ["bulk=2;graph=0", "bulk=2;autotune=0", "bulk=2;split_order=source", "bulk=1",
+                                  "bulk=2;split_order=dest", "bulk=2;block=128", "bulk=2;block=256",
+                                  "bulk=2;block=512", "bulk=2;block=1024"])
+def test_backward_scatter_info_variants(info):
+    """Every scatter-kernel shape (block=128/256/512/1024 select threads x stages x CTAs per
+    SM), eager and graph launches, and the orders that leave the form out."""
+    p = pt.config5(edge=8, comps=4)
+    x = payload(p, 5)
+    g = grad_payload(p, 6)
+    for alg, form in (("standard", 0), ("locality", 1)):
+        _, ex = forward(p, x, alg)
+        gs = torch.zeros(p.sendbuf_bytes, dtype=torch.uint8, device="cuda")
+        b = gbx.backward_init(ex.request, dev_bytes(g), gs, info=info)
+        want = oracle.backward(p, g, form=form)
+        for rep in range(2):
+            b.start()
+            b.wait()
+            assert_bytes_equal(gs.cpu().numpy(), want, f"{alg} {info} start {rep}")
+        if info.startswith("bulk=2") and alg == "standard":   # destination order has no scatter form
+            assert bool(b.info()["copy_forms"] & SCATTER) == ("dest" not in info)
+
+
+def test_backward_scatter_batch_and_full_size():
+    """Two scatter-form backwards in one batch; then the 512^3 backward in the scatter form
+    equals the default backward (which the exchange tests pin to the oracle) bit for bit."""
+    pats = [pt.config5(edge=4, comps=2), pt.config5(edge=8, comps=4)]
+    reqs, outs = [], []
+    for k, p in enumerate(pats):
+        _, ex = forward(p, payload(p, k), "standard")
+        g = grad_payload(p, 10 + k)
+        gs = torch.zeros(p.sendbuf_bytes, dtype=torch.uint8, device="cuda")
+        b = gbx.backward_init(ex.request, dev_bytes(g), gs, info="bulk=2")
+        reqs.append(b)
+        outs.append((gs, oracle.backward(p, g, form=0), ex))
+    gbx.startall(reqs)
+    gbx.waitall(reqs)
+    for gs, want, _ in outs:
+        assert_bytes_equal(gs.cpu().numpy(), want, "batched scatter backward")
+    del reqs, outs
+    p = pt.config5()
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(8)
+    x = torch.rand(p.sendbuf_bytes // 8, dtype=torch.float64, device="cuda", generator=gen)
+    h = torch.zeros(p.recvbuf_bytes // 8, dtype=torch.float64, device="cuda")
+    ex = gbx.Exchange(p, x, h, "standard")
+    g = torch.randn(p.recvbuf_bytes // 8, dtype=torch.float64, device="cuda", generator=gen)
+    g1 = torch.zeros_like(x)
+    g2 = torch.zeros_like(x)
+    b1 = gbx.backward_init(ex.request, g, g1)
+    b2 = gbx.backward_init(ex.request, g, g2, info="bulk=2")
+    assert b2.info()["copy_forms"] & SCATTER
+    b1.start(); b1.wait()
+    b2.start(); b2.wait()
+    assert torch.equal(g1.view(torch.uint8), g2.view(torch.uint8))

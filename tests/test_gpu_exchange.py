@@ -277,7 +277,8 @@ def test_error_codes_match_oracle(case):
 
 
 @pytest.mark.parametrize("info", ["", "single_split=0", "flat=0", "vec=8;block=128", "single_split=0;block=1024",
-                                  "split_order=source", "split_order=source;vec=8"])
+                                  "split_order=source", "split_order=source;vec=8", "split_order=dest",
+                                  "bulk=2"])
 def test_backward_modes_identical(info):
     """Every backward program shape (single-term rows split out or folded, flat or segment
     copies, any launch shape) gives the oracle's bytes."""
