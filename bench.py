@@ -410,19 +410,18 @@ def run_ours(args):
             "init_s": t_init}
 
     # ---------------------------------------------------------------- e2e
-    # Steps end to end: each step copies its inputs (the field, and the incoming gradient of the
-    # halo) in from pinned host memory and its results (both halos, the field's gradient) back.
-    # The field goes up once for both forward forms; the halos' download overlaps the gradient's
-    # upload; and with two device buffer sets, step k+1's uploads run while step k's downloads
-    # do (the two directions use separate copy engines).  The exchanges run through the
-    # persistent requests' start.
+    # Steps end to end through the library's host-buffer call (gbx_start_host_async): each
+    # step uploads its inputs (the field, and the incoming gradient of the halo) from pinned
+    # host memory and reads its results (both halos, the field's gradient) back.  The field
+    # goes up once for both forward forms (the locality request reuses the device copy the
+    # standard request's upload wrote).  Two device buffer sets, so step k+1's uploads run
+    # while step k's downloads do (the two directions use separate copy engines).
     if not args.no_e2e:
         hx = torch.empty(p.sendbuf_bytes, dtype=torch.uint8).pin_memory()
         hx.copy_(torch.from_numpy(x.view(np.uint8)))
         hg = torch.empty(p.recvbuf_bytes, dtype=torch.uint8).pin_memory()
         hg.copy_(grad_halo.view(torch.uint8).cpu())
-        up, down = torch.cuda.Stream(), torch.cuda.Stream()
-        comp = torch.cuda.current_stream()   # the requests' stream
+        side = torch.cuda.Stream()           # completes the requests without ordering their stream
         sets = []
         for k in range(2):
             S = {"field": field if k == 0 else torch.empty_like(field),
@@ -440,39 +439,16 @@ def run_ours(args):
             S["out"] = [torch.empty(p.recvbuf_bytes, dtype=torch.uint8).pin_memory(),
                         torch.empty(p.recvbuf_bytes, dtype=torch.uint8).pin_memory(),
                         torch.empty(p.sendbuf_bytes, dtype=torch.uint8).pin_memory()]
-            S["free"] = torch.cuda.Event()
-            S["free"].record(down)
             sets.append(S)
 
         def e2e_step(k):
             S = sets[k % 2]
             r_std, r_loc, r_bwd = S["reqs"]
-            up.wait_event(S["free"])          # this set's previous results have been read back
-            with torch.cuda.stream(up):
-                S["field"].view(torch.uint8).copy_(hx, non_blocking=True)
-                e_field = torch.cuda.Event()
-                e_field.record(up)
-                S["g"].view(torch.uint8).copy_(hg, non_blocking=True)
-                e_grad = torch.cuda.Event()
-                e_grad.record(up)
-            comp.wait_event(e_field)
-            r_std.start()
-            r_loc.start()
-            e_fwd = torch.cuda.Event()
-            e_fwd.record(comp)
-            comp.wait_event(e_grad)
-            r_bwd.start()
-            e_bwd = torch.cuda.Event()
-            e_bwd.record(comp)
+            r_std.start_host_async(hx, S["out"][0])
+            r_loc.start_host_async(None, S["out"][1])
+            r_bwd.start_host_async(hg, S["out"][2])
             for r in (r_std, r_loc, r_bwd):
-                r.wait_stream(comp)           # completes in stream order; the host does not block
-            with torch.cuda.stream(down):
-                down.wait_event(e_fwd)
-                S["out"][0].copy_(S["hs"].view(torch.uint8), non_blocking=True)
-                S["out"][1].copy_(S["hl"].view(torch.uint8), non_blocking=True)
-                down.wait_event(e_bwd)
-                S["out"][2].copy_(S["gf"].view(torch.uint8), non_blocking=True)
-                S["free"].record(down)
+                r.wait_stream(side)
 
         for k in range(2):
             e2e_step(k)
@@ -489,9 +465,9 @@ def run_ours(args):
                        "h2d_bytes_per_step": p.sendbuf_bytes + p.recvbuf_bytes,
                        "d2h_bytes_per_step": 2 * p.recvbuf_bytes + p.sendbuf_bytes,
                        "ms_per_step": e_ms, "steps": args.e2e_steps,
-                       "api": "per step: pinned host field + gradient copied in, start of the three persistent "
-                              "requests, both halos + field gradient copied out; two device buffer sets, so a "
-                              "step's uploads overlap the previous step's downloads"}
+                       "api": "gbx_start_host_async on the three persistent requests per step: pinned host "
+                              "field + gradient copied in, both halos + field gradient copied out; two device "
+                              "buffer sets, so a step's uploads overlap the previous step's downloads"}
         for S in sets:
             assert torch.equal(S["out"][0], S["out"][1])
             assert torch.equal(S["out"][2].cuda(), sets[0]["gf"].view(torch.uint8))

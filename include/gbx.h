@@ -418,6 +418,21 @@ int gbx_request_bind(gbx_request_t request, const void *src, void *dst);
  * then waits as gbx_wait does. */
 int gbx_start_host(gbx_request_t request, const void *host_src, void *host_dst);
 
+/* The same on HOST buffers without blocking: enqueues (1) the copy of host_src to the
+ * bound device source buffer on the request's own upload stream, after the work already
+ * queued on the request's stream (the earlier exchanges that read that buffer); (2) the
+ * exchange on the request's stream, after that copy; (3) the copy of the bound destination
+ * buffer to host_dst on the request's own download stream, after the exchange.  host_src =
+ * NULL skips (1) (the device source is used as it is: e.g. a second request over the same
+ * source, started after the first on the same stream); host_dst = NULL skips (3).  The
+ * request completes (gbx_wait, gbx_test, gbx_wait_stream) once (3), else (2), is done;
+ * its next exchange, from any start call, is ordered after (3).  Successive calls on two
+ * requests whose buffers differ overlap one's upload with the other's download: the two
+ * copy directions use separate copy engines.  host_src and host_dst must stay valid and
+ * unchanged until completion; pinned memory makes the copies asynchronous.  Errors:
+ * GBX_ERR_ARG, _ACTIVE, _UNSUPPORTED (partitioned requests), _CUDA. */
+int gbx_start_host_async(gbx_request_t request, const void *host_src, void *host_dst);
+
 int gbx_request_get_info(gbx_request_t request, gbx_request_info_t *info);
 
 /* Largest edge count gbx_neighbor_alltoallv_noalloc accepts (in-edges and out-edges). */

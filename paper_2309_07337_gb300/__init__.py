@@ -86,6 +86,7 @@ def lib():
         "gbx_waitall": [ctypes.c_int, _pvp],
         "gbx_request_bind": [_vp, _vp, _vp],
         "gbx_start_host": [_vp, _vp, _vp],
+        "gbx_start_host_async": [_vp, _vp, _vp],
         "gbx_request_get_info": [_vp, ctypes.POINTER(RequestInfo)],
         "gbx_request_free": [_pvp],
     }
@@ -214,6 +215,15 @@ class Request:
     def start_host(self, host_src, host_dst):
         """One exchange on host tensors (copied in, exchanged, copied out)."""
         _check(lib().gbx_start_host(self.handle, host_src.data_ptr(), host_dst.data_ptr()), "start_host")
+
+    def start_host_async(self, host_src=None, host_dst=None):
+        """Stream-ordered exchange on host tensors (see gbx_start_host_async in include/gbx.h):
+        None skips that copy.  The host tensors must stay alive until the request completes."""
+        for t in (host_src, host_dst):
+            assert t is None or (not t.is_cuda and t.is_contiguous()), "host buffers must be contiguous CPU tensors"
+        _check(lib().gbx_start_host_async(self.handle, None if host_src is None else host_src.data_ptr(),
+                                          None if host_dst is None else host_dst.data_ptr()), "start_host_async")
+        self._host_keep = (host_src, host_dst)
 
     def info(self) -> dict:
         i = RequestInfo()

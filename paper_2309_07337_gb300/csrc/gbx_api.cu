@@ -744,6 +744,12 @@ static void destroy_request(gbx_request_s *req) {
         cudaEventSynchronize(ev);
     }
     while (!req->batches.empty()) destroy_batch(req->batches.back());
+    if (req->host_down_pending) cudaEventSynchronize(req->host_down_ev);
+    if (req->host_up) cudaStreamSynchronize(req->host_up);
+    for (cudaEvent_t e : {req->host_up_ev, req->host_down_ev, req->host_mark})
+        if (e) cudaEventDestroy(e);
+    for (cudaStream_t s : {req->host_up, req->host_down})
+        if (s) cudaStreamDestroy(s);
     if (req->exec) cudaGraphExecDestroy(req->exec);
     if (req->done) cudaEventDestroy(req->done);
     gbx_graph_s *g = req->owned_graph;
@@ -1053,6 +1059,8 @@ extern "C" int gbx_backward_init(gbx_request_t forward, const void *grad_recv, v
 
 // ------------------------------------------------------------- start / wait
 static int enqueue_start(gbx_request_s *req) {
+    // the exchange overwrites the bound destination: it follows the last host read-back of it
+    if (req->host_down_pending) GBX_CUDA_TRY(cudaStreamWaitEvent(req->stream, req->host_down_ev, 0));
     if (req->use_graph && req->exec) {
         GBX_CUDA_TRY(cudaGraphLaunch(req->exec, req->stream));
     } else {
@@ -1160,6 +1168,8 @@ extern "C" int gbx_startall(int count, gbx_request_t *reqs) {
         if (reqs[i]->active) return GBX_ERR_ACTIVE;
         for (int j = 0; j < i; j++) if (reqs[j] == reqs[i]) return GBX_ERR_ARG;
     }
+    for (int i = 0; i < count; i++)   // destinations still being read back to the host
+        if (reqs[i]->host_down_pending) GBX_CUDA_TRY(cudaStreamWaitEvent(reqs[0]->stream, reqs[i]->host_down_ev, 0));
     std::vector<gbx_request_s *> key(reqs, reqs + count);
     Batch *b = nullptr;
     for (Batch *c : reqs[0]->batches)
@@ -1228,16 +1238,45 @@ extern "C" int gbx_request_bind(gbx_request_t req, const void *src, void *dst) {
     return GBX_SUCCESS;
 }
 
-extern "C" int gbx_start_host(gbx_request_t req, const void *host_src, void *host_dst) {
-    if (!req || (req->src_bytes > 0 && !host_src) || (req->dst_bytes > 0 && !host_dst)) return GBX_ERR_ARG;
+static int host_streams(gbx_request_s *req) {
+    if (req->host_up) return GBX_SUCCESS;
+    GBX_CUDA_TRY(cudaStreamCreateWithFlags(&req->host_up, cudaStreamNonBlocking));
+    GBX_CUDA_TRY(cudaStreamCreateWithFlags(&req->host_down, cudaStreamNonBlocking));
+    GBX_CUDA_TRY(cudaEventCreateWithFlags(&req->host_up_ev, cudaEventDisableTiming));
+    GBX_CUDA_TRY(cudaEventCreateWithFlags(&req->host_down_ev, cudaEventDisableTiming));
+    GBX_CUDA_TRY(cudaEventCreateWithFlags(&req->host_mark, cudaEventDisableTiming));
+    return GBX_SUCCESS;
+}
+
+extern "C" int gbx_start_host_async(gbx_request_t req, const void *host_src, void *host_dst) {
+    if (!req) return GBX_ERR_ARG;
     if (req->kind == 2) return GBX_ERR_UNSUPPORTED;
     if (req->active) return GBX_ERR_ACTIVE;
-    if (req->src_bytes > 0)
-        GBX_CUDA_TRY(cudaMemcpyAsync((void *)req->src, host_src, req->src_bytes, cudaMemcpyHostToDevice, req->stream));
+    GBX_TRY(host_streams(req));
+    if (host_src && req->src_bytes > 0) {
+        // the upload overwrites the bound source: it follows everything already queued on the
+        // request's stream (earlier exchanges that read the source)
+        GBX_CUDA_TRY(cudaEventRecord(req->host_mark, req->stream));
+        GBX_CUDA_TRY(cudaStreamWaitEvent(req->host_up, req->host_mark, 0));
+        GBX_CUDA_TRY(cudaMemcpyAsync((void *)req->src, host_src, req->src_bytes, cudaMemcpyHostToDevice,
+                                     req->host_up));
+        GBX_CUDA_TRY(cudaEventRecord(req->host_up_ev, req->host_up));
+        GBX_CUDA_TRY(cudaStreamWaitEvent(req->stream, req->host_up_ev, 0));
+    }
     GBX_TRY(enqueue_start(req));
-    if (req->dst_bytes > 0)
-        GBX_CUDA_TRY(cudaMemcpyAsync(host_dst, req->dst, req->dst_bytes, cudaMemcpyDeviceToHost, req->stream));
-    GBX_CUDA_TRY(cudaEventRecord(req->done, req->stream));
+    if (host_dst && req->dst_bytes > 0) {
+        GBX_CUDA_TRY(cudaStreamWaitEvent(req->host_down, req->done, 0));
+        GBX_CUDA_TRY(cudaMemcpyAsync(host_dst, req->dst, req->dst_bytes, cudaMemcpyDeviceToHost, req->host_down));
+        GBX_CUDA_TRY(cudaEventRecord(req->host_down_ev, req->host_down));
+        GBX_CUDA_TRY(cudaEventRecord(req->done, req->host_down));   // complete once read back
+        req->host_down_pending = 1;
+    }
+    return GBX_SUCCESS;
+}
+
+extern "C" int gbx_start_host(gbx_request_t req, const void *host_src, void *host_dst) {
+    if (!req || (req->src_bytes > 0 && !host_src) || (req->dst_bytes > 0 && !host_dst)) return GBX_ERR_ARG;
+    GBX_TRY(gbx_start_host_async(req, host_src, host_dst));
     return gbx_wait(req);
 }
 

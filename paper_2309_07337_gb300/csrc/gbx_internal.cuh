@@ -178,6 +178,11 @@ struct gbx_request_s {
     cudaEvent_t done;
     cudaEvent_t *pending;    // event to wait on while active (own or a batch's)
     int active;
+    // host-buffer starts: the request's own copy streams (upload, download), the event the
+    // upload records, and the event of the last download (the next exchange waits for it)
+    cudaStream_t host_up = nullptr, host_down = nullptr;
+    cudaEvent_t host_up_ev = nullptr, host_down_ev = nullptr, host_mark = nullptr;
+    int host_down_pending = 0;
     const char *src;         // bound buffers
     char *dst;
     int64_t src_bytes, dst_bytes;

@@ -235,6 +235,49 @@ def test_host_buffers_end_to_end():
     assert_bytes_equal(hr.numpy(), oracle.standard(p, x), "host buffers")
 
 
+def test_host_buffers_pipelined_steps():
+    """Stream-ordered host-buffer starts over two request sets (standard and locality forward
+    over one uploaded field, backward with an uploaded gradient), four steps with different
+    inputs in flight together: every step's read-back equals the oracle's."""
+    p = pt.config5(edge=4, comps=2)
+    steps = 4
+    xs = [payload(p, 20 + k) for k in range(steps)]
+    gs = [grad_payload(p, 40 + k) for k in range(steps)]
+    hx = [torch.from_numpy(x.view(np.uint8).copy()).pin_memory() for x in xs]
+    hg = [torch.from_numpy(g.view(np.uint8).copy()).pin_memory() for g in gs]
+    out = [[torch.zeros(n, dtype=torch.uint8).pin_memory() for n in (p.recvbuf_bytes, p.recvbuf_bytes,
+                                                                       p.sendbuf_bytes)] for _ in range(steps)]
+    sets = []
+    for k in range(2):
+        field = torch.zeros(p.sendbuf_bytes, dtype=torch.uint8, device="cuda")
+        h1 = torch.zeros(p.recvbuf_bytes, dtype=torch.uint8, device="cuda")
+        h2 = torch.zeros_like(h1)
+        g = torch.zeros(p.recvbuf_bytes, dtype=torch.uint8, device="cuda")
+        gf = torch.zeros_like(field)
+        a = gbx.Exchange(p, field, h1, "standard")
+        b = gbx.Exchange(p, field, h2, "locality")
+        sets.append((a, b, gbx.backward_init(a.request, g, gf), (field, h1, h2, g, gf)))
+    side = torch.cuda.Stream()
+    for k in range(steps):
+        a, b, bw, _ = sets[k % 2]
+        a.request.start_host_async(hx[k], out[k][0])
+        b.request.start_host_async(None, out[k][1])
+        bw.start_host_async(hg[k], out[k][2])
+        for r in (a.request, b.request, bw):
+            r.wait_stream(side)          # completes without ordering the requests' stream
+    torch.cuda.synchronize()
+    for k in range(steps):
+        want = oracle.standard(p, xs[k])
+        assert_bytes_equal(out[k][0].numpy(), want, f"step {k} standard")
+        assert_bytes_equal(out[k][1].numpy(), want, f"step {k} locality")
+        assert_bytes_equal(out[k][2].numpy(), oracle.backward(p, gs[k], form=0), f"step {k} backward")
+    # a plain start after host starts is ordered after their read-back
+    a, _, _, bufs = sets[0]
+    a.start()
+    a.wait()
+    assert_bytes_equal(bufs[1].cpu().numpy(), oracle.standard(p, xs[2]), "plain start after host starts")
+
+
 # ------------------------------------------------------------------- errors
 def _error_cases():
     base = pins.load_golden("ring3.json")
