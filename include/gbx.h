@@ -249,8 +249,9 @@ int gbx_neighbor_allgatherv_init(const void *sendbuf, int64_t sendbuf_bytes, con
                                  const char *info, void *stream, gbx_request_t *request);
 
 /* Reads and clears the device status word of the move kernels: 1 when a bounded wait of
- * the bulk-copy kernel gave up since the last call (the launch then left its pieces
- * unfinished), else 0.  No counterpart in the paper. */
+ * the bulk or scatter kernel gave up since the last call (the launch then left its pieces
+ * unfinished), 2 when one of their pieces failed its in-kernel check and was skipped, else
+ * 0.  No counterpart in the paper. */
 int gbx_device_status(int *status);
 
 /* Persistent partitioned exchange (section 2.3: partitioned communication lets marked
