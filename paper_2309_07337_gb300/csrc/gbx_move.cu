@@ -447,161 +447,167 @@ int gbx_bulk_prepare(void) {
 
 // ----------------------------------------------------------------- scatter
 // Scatter form of a two-index copy whose pairs are sorted by source: each piece is a window of
-// the source.  Thread 0 has the bulk-copy engine read the window's runs of source elements
-// (the gaps between them are not read) and the window's source and destination indices into
-// one of S shared-memory stages (one mbarrier counts every copy), and the threads then
-// scatter the window's elements from shared memory to their destinations with 16-byte stores,
-// so the only global accesses left in the threads are the stores.  Piece descriptors are
-// staged in shared memory; thread 0 fetches the next one while the current window is
-// scattered.  Every thread waits on the stage's mbarrier itself (bounded); a block-wide vote
-// makes the decision to give up uniform, so no barrier is ever left waiting.
+// the source.  Warp 0 is the producer: its lane 0 has the bulk-copy engine read a window's
+// runs of source elements (the gaps between them are not read) and the window's source and
+// destination indices into one of S shared-memory stages, completing on the stage's "full"
+// mbarrier.  The other warps are consumers: they wait on "full", scatter the window's elements
+// from shared memory to their destinations with 16-byte stores, and release the stage on its
+// "empty" mbarrier (one arrival per consumer warp), which the producer waits on before
+// refilling it.  No CTA-wide barrier is crossed after setup, so a slow warp holds back only
+// its own stage.  Every wait is bounded: a consumer that gives up raises `abort`, the producer
+// then stops issuing, waits (bounded) for the copies it has in flight, and every warp leaves.
 template <int NT, int S>
 __global__ void __launch_bounds__(NT) gbx_scatter_kernel(const CopyDesc *const *__restrict__ ops,
                                                          const int64_t *__restrict__ prefix, int nops,
                                                          int64_t npieces) {
+    constexpr int NC = NT - 32;          // consumer threads
+    constexpr int NCW = NC / 32;         // consumer warps: arrivals that release a stage
     extern __shared__ __align__(128) unsigned char gbx_scatter_smem[];
-    __shared__ __align__(8) uint64_t bar[S];
-    __shared__ int loaded[S];
+    __shared__ __align__(8) uint64_t full[S], empty[S];
     __shared__ ScatterPiece piece_s[S];
-    __shared__ __align__(16) ScatterPiece next_s;   // the next refill's piece, fetched ahead
+    __shared__ __align__(16) ScatterPiece next_s;   // the producer's next piece, fetched ahead
     __shared__ const CopyDesc *desc_s[S];
+    __shared__ volatile int abort_flag;
     const uint32_t sbuf = (uint32_t)__cvta_generic_to_shared(gbx_scatter_smem);
-    const uint32_t sbar = (uint32_t)__cvta_generic_to_shared(bar);
-    auto piece_ptr = [&](int64_t t, const CopyDesc *&d) {
-        const int op = nops > 1 ? find_op(prefix, nops, t) : 0;
-        d = ops[op];
-        return d->scat + (t - (nops > 1 ? __ldg(prefix + op) : 0));
-    };
-    // thread 0: starts an asynchronous copy of piece t into next_s (8 x 16 bytes)
-    auto fetch = [&](int64_t t, const CopyDesc *&d) {
-        const char *g = reinterpret_cast<const char *>(piece_ptr(t, d));
-        const uint32_t sl = (uint32_t)__cvta_generic_to_shared(&next_s);
-#pragma unroll
-        for (int i = 0; i < (int)sizeof(ScatterPiece) / 16; i++)
-            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sl + 16 * i), "l"(g + 16 * i) : "memory");
-        asm volatile("cp.async.commit_group;" ::: "memory");
-    };
-    auto fetched = [&]() { asm volatile("cp.async.wait_all;" ::: "memory"); };
-    auto issue = [&](int q, const ScatterPiece &P, const CopyDesc *d) {   // thread 0 only
-        // index copies rounded out to 16-byte boundaries (the index arrays carry padding)
-        const int64_t i0 = (P.m0 * 4) & ~(int64_t)15, i1 = ((P.m0 + P.n) * 4 + 15) & ~(int64_t)15;
-        bool good = P.len > 0 && P.len <= GBX_SCAT_WIN && P.n > 0 && P.n <= GBX_SCAT_MAXN && P.m0 >= 0 &&
-                    P.nrun > 0 && P.nrun <= GBX_SCAT_RUNS &&
-                    ((P.src | (int64_t)(uintptr_t)d->src | (int64_t)(uintptr_t)d->flat_idx |
-                      (int64_t)(uintptr_t)d->flat_didx) & 15) == 0;
-        uint32_t bytes = 0;
-        for (int r = 0; good && r < P.nrun; r++) {
-            const uint32_t o = P.run_off[r], l = P.run_len[r];
-            good = ((o | l) & 15) == 0 && l > 0 && o + l <= (uint32_t)P.len;
-            bytes += l;
-        }
-        if (!good) {   // validated at init; recorded and skipped
-            atomicExch(&gbx_bulk_status, 2);
-            loaded[q] = 0;
-            return;
-        }
-        const uint32_t b = sbar + 8 * q, ilen = (uint32_t)(i1 - i0);
-        const uint32_t stage = sbuf + q * GBX_SCAT_STAGE;
-        piece_s[q] = P;
-        desc_s[q] = d;
-        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(b), "r"(bytes + 2 * ilen)
-                     : "memory");
-        for (int r = 0; r < P.nrun; r++)
-            asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-                         ::"r"(stage + P.run_off[r]), "l"(d->src + P.src + P.run_off[r]), "r"((uint32_t)P.run_len[r]),
-                         "r"(b)
-                         : "memory");
-        asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-                     ::"r"(stage + GBX_SCAT_WIN), "l"(reinterpret_cast<const char *>(d->flat_idx) + i0), "r"(ilen),
-                     "r"(b)
-                     : "memory");
-        asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-                     ::"r"(stage + GBX_SCAT_WIN + GBX_SCAT_IDX),
-                     "l"(reinterpret_cast<const char *>(d->flat_didx) + i0), "r"(ilen), "r"(b)
-                     : "memory");
-        loaded[q] = 1;
-    };
+    const uint32_t sfull = (uint32_t)__cvta_generic_to_shared(full);
+    const uint32_t sempty = (uint32_t)__cvta_generic_to_shared(empty);
     if (threadIdx.x == 0) {
-        for (int q = 0; q < S; q++) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(sbar + 8 * q) : "memory");
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         for (int q = 0; q < S; q++) {
-            const int64_t t = blockIdx.x + (int64_t)q * gridDim.x;
-            loaded[q] = 0;
-            if (t < npieces) {
-                const CopyDesc *d;
-                fetch(t, d);
-                fetched();
-                issue(q, next_s, d);
-            }
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(sfull + 8 * q) : "memory");
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(sempty + 8 * q), "r"(NCW) : "memory");
         }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        abort_flag = 0;
     }
-    __syncthreads();
-    uint32_t parity[S];
+    __syncthreads();   // the only CTA-wide barrier
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (warp == 0) {
+        if (lane != 0) return;
+        // ---------------------------------------------------------------- producer
+        auto fetch = [&](int64_t t, const CopyDesc *&d) {   // piece t into next_s, asynchronously
+            const int op = nops > 1 ? find_op(prefix, nops, t) : 0;
+            d = ops[op];
+            const char *g = reinterpret_cast<const char *>(d->scat + (t - (nops > 1 ? __ldg(prefix + op) : 0)));
+            const uint32_t sl = (uint32_t)__cvta_generic_to_shared(&next_s);
 #pragma unroll
-    for (int q = 0; q < S; q++) parity[q] = 0;
-    bool failed = false;
+            for (int i = 0; i < (int)sizeof(ScatterPiece) / 16; i++)
+                asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sl + 16 * i), "l"(g + 16 * i) : "memory");
+            asm volatile("cp.async.commit_group;" ::: "memory");
+        };
+        int64_t last[S];   // last piece issued on each stage (-1: none)
+#pragma unroll
+        for (int q = 0; q < S; q++) last[q] = -1;
+        bool stop = false;
+        const CopyDesc *d = nullptr;
+        if (blockIdx.x < npieces) fetch(blockIdx.x, d);
+        for (int64_t k = 0;; k++) {
+            const int64_t t = blockIdx.x + k * gridDim.x;
+            if (t >= npieces) break;
+            const int q = (int)(k % S);
+            if (k >= S && !bulk_wait(sempty + 8 * q, (uint32_t)((k / S - 1) & 1))) {
+                abort_flag = 1;
+                stop = true;
+                break;
+            }
+            if (abort_flag) {
+                stop = true;
+                break;
+            }
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // consumers' reads before the refill
+            asm volatile("cp.async.wait_all;" ::: "memory");
+            ScatterPiece P = next_s;
+            const CopyDesc *pd = d;
+            const int64_t tn = t + gridDim.x;
+            if (tn < npieces) fetch(tn, d);   // the next piece's descriptor, while this one loads
+            const int64_t i0 = (P.m0 * 4) & ~(int64_t)15, i1 = ((P.m0 + P.n) * 4 + 15) & ~(int64_t)15;
+            bool good = P.len > 0 && P.len <= GBX_SCAT_WIN && P.n > 0 && P.n <= GBX_SCAT_MAXN && P.m0 >= 0 &&
+                        P.nrun > 0 && P.nrun <= GBX_SCAT_RUNS &&
+                        ((P.src | (int64_t)(uintptr_t)pd->src | (int64_t)(uintptr_t)pd->flat_idx |
+                          (int64_t)(uintptr_t)pd->flat_didx) & 15) == 0;
+            uint32_t bytes = 0;
+            for (int r = 0; good && r < P.nrun; r++) {
+                const uint32_t o = P.run_off[r], l = P.run_len[r];
+                good = ((o | l) & 15) == 0 && l > 0 && o + l <= (uint32_t)P.len;
+                bytes += l;
+            }
+            const uint32_t fb = sfull + 8 * q;
+            if (!good) {   // validated at init; recorded, and the consumers skip it
+                atomicExch(&gbx_bulk_status, 2);
+                P.n = 0;
+                piece_s[q] = P;
+                desc_s[q] = pd;
+                asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(fb) : "memory");
+                continue;
+            }
+            piece_s[q] = P;
+            desc_s[q] = pd;
+            const uint32_t ilen = (uint32_t)(i1 - i0), stage = sbuf + q * GBX_SCAT_STAGE;
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(fb), "r"(bytes + 2 * ilen)
+                         : "memory");
+            for (int r = 0; r < P.nrun; r++)
+                asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                             ::"r"(stage + P.run_off[r]), "l"(pd->src + P.src + P.run_off[r]),
+                             "r"((uint32_t)P.run_len[r]), "r"(fb)
+                             : "memory");
+            asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                         ::"r"(stage + GBX_SCAT_WIN), "l"(reinterpret_cast<const char *>(pd->flat_idx) + i0),
+                         "r"(ilen), "r"(fb)
+                         : "memory");
+            asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                         ::"r"(stage + GBX_SCAT_WIN + GBX_SCAT_IDX),
+                         "l"(reinterpret_cast<const char *>(pd->flat_didx) + i0), "r"(ilen), "r"(fb)
+                         : "memory");
+            last[q] = k;
+        }
+        asm volatile("cp.async.wait_all;" ::: "memory");
+        if (stop) {   // leave no copy in flight: wait (bounded) for the last one issued on each stage
+            atomicExch(&gbx_bulk_status, 1);
+            for (int q = 0; q < S; q++)
+                if (last[q] >= 0) bulk_wait(sfull + 8 * q, (uint32_t)((last[q] / S) & 1));
+        }
+        return;
+    }
+    // -------------------------------------------------------------------- consumers
+    const int ct = threadIdx.x - 32;
     for (int64_t k = 0;; k++) {
         const int64_t t = blockIdx.x + k * gridDim.x;
         if (t >= npieces) break;
         const int q = (int)(k % S);
-        const int64_t tn = t + (int64_t)S * gridDim.x;
-        const CopyDesc *nd = nullptr;
-        if (threadIdx.x == 0 && tn < npieces) fetch(tn, nd);
-        const bool have = loaded[q] != 0;
-        bool ok = true;
-        if (have) {
-            ok = bulk_wait(sbar + 8 * q, parity[q]);
-            if (ok) parity[q] ^= 1u;
-        }
-        if (!__syncthreads_and(ok)) {
-            failed = true;
+        if (!bulk_wait(sfull + 8 * q, (uint32_t)((k / S) & 1))) {
+            abort_flag = 1;
             break;
         }
-        if (have) {
-            const CopyDesc *d = desc_s[q];
-            const int64_t src0 = piece_s[q].src, m0 = piece_s[q].m0;
-            const int s = (int)d->elem_size, cpe = s >> 4, len = piece_s[q].len, n = piece_s[q].n;
-            const unsigned char *win = gbx_scatter_smem + q * GBX_SCAT_STAGE;
-            const int32_t *ps = reinterpret_cast<const int32_t *>(win + GBX_SCAT_WIN) + (m0 & 3);
-            const int32_t *pd = reinterpret_cast<const int32_t *>(win + GBX_SCAT_WIN + GBX_SCAT_IDX) + (m0 & 3);
-            char *dst = d->dst;
-            for (int i = threadIdx.x; i < n * cpe; i += NT) {
-                const int j = i / cpe, c = i - j * cpe;
-                const int64_t w = (int64_t)ps[j] * s - src0 + c * 16;
-                if (w < 0 || w + 16 > len) {   // validated at init; recorded and skipped
-                    atomicExch(&gbx_bulk_status, 2);
-                    continue;
-                }
-                const uint4 v = *reinterpret_cast<const uint4 *>(win + w);
-                stv<16>(dst + (int64_t)pd[j] * s + c * 16, v);
+        const CopyDesc *d = desc_s[q];
+        const int64_t src0 = piece_s[q].src, m0 = piece_s[q].m0;
+        const int s = (int)d->elem_size, cpe = s >> 4, len = piece_s[q].len, n = piece_s[q].n;
+        const unsigned char *win = gbx_scatter_smem + q * GBX_SCAT_STAGE;
+        const int32_t *ps = reinterpret_cast<const int32_t *>(win + GBX_SCAT_WIN) + (m0 & 3);
+        const int32_t *pdst = reinterpret_cast<const int32_t *>(win + GBX_SCAT_WIN + GBX_SCAT_IDX) + (m0 & 3);
+        char *dst = d->dst;
+        for (int i = ct; i < n * cpe; i += NC) {
+            const int j = i / cpe, c = i - j * cpe;
+            const int64_t w = (int64_t)ps[j] * s - src0 + c * 16;
+            if (w < 0 || w + 16 > len) {   // validated at init; recorded and skipped
+                atomicExch(&gbx_bulk_status, 2);
+                continue;
             }
+            const uint4 v = *reinterpret_cast<const uint4 *>(win + w);
+            stv<16>(dst + (int64_t)pdst[j] * s + c * 16, v);
         }
-        __syncthreads();   // every thread is done with stage q
-        if (threadIdx.x == 0) {
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // reads before the refill
-            loaded[q] = 0;
-            if (tn < npieces) {
-                fetched();
-                issue(q, next_s, nd);
-            }
-        }
-        __syncthreads();
-    }
-    if (failed && threadIdx.x == 0) {
-        atomicExch(&gbx_bulk_status, 1);
-        fetched();
-        for (int q = 0; q < S; q++)
-            if (loaded[q]) bulk_wait(sbar + 8 * q, parity[q]);
+        __syncwarp();
+        if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(sempty + 8 * q) : "memory");
+        if (abort_flag) break;
     }
 }
 
-// Shapes of the scatter kernel, chosen by the launch's block value: threads per CTA, stages
-// per CTA and CTAs per SM (each shape fills about 192 KB of shared memory per SM).
+// Shapes of the scatter kernel, chosen by the launch's block value: threads per CTA (one
+// producer warp plus consumers), stages per CTA and CTAs per SM (each shape fills about
+// 192 KB of shared memory per SM).
 struct ScatShape { int nt, stages, per_sm; };
 static ScatShape scatter_shape(int block) {
-    if (block <= 128) return {256, 2, 4};
-    if (block <= 256) return {256, 4, 2};
-    if (block <= 512) return {512, 4, 2};
+    if (block <= 128) return {288, 2, 4};
+    if (block <= 256) return {288, 4, 2};
+    if (block <= 512) return {544, 4, 2};
     return {1024, 8, 1};
 }
 
@@ -609,21 +615,21 @@ static cudaError_t scatter_launch(int block, int grid, cudaStream_t st, const Co
                                   const int64_t *prefix, int nops, int64_t n) {
     const ScatShape h = scatter_shape(block);
     const size_t smem = (size_t)h.stages * GBX_SCAT_STAGE;
-    if (h.stages == 2) gbx_scatter_kernel<256, 2><<<grid, 256, smem, st>>>(ops, prefix, nops, n);
-    else if (h.nt == 256) gbx_scatter_kernel<256, 4><<<grid, 256, smem, st>>>(ops, prefix, nops, n);
-    else if (h.nt == 512) gbx_scatter_kernel<512, 4><<<grid, 512, smem, st>>>(ops, prefix, nops, n);
+    if (h.stages == 2) gbx_scatter_kernel<288, 2><<<grid, 288, smem, st>>>(ops, prefix, nops, n);
+    else if (h.nt == 288) gbx_scatter_kernel<288, 4><<<grid, 288, smem, st>>>(ops, prefix, nops, n);
+    else if (h.nt == 544) gbx_scatter_kernel<544, 4><<<grid, 544, smem, st>>>(ops, prefix, nops, n);
     else gbx_scatter_kernel<1024, 8><<<grid, 1024, smem, st>>>(ops, prefix, nops, n);
     return cudaGetLastError();
 }
 
 int gbx_scatter_prepare(void) {
-    cudaError_t e = cudaFuncSetAttribute(gbx_scatter_kernel<256, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(gbx_scatter_kernel<288, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          2 * GBX_SCAT_STAGE);
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(gbx_scatter_kernel<256, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        e = cudaFuncSetAttribute(gbx_scatter_kernel<288, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  4 * GBX_SCAT_STAGE);
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(gbx_scatter_kernel<512, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        e = cudaFuncSetAttribute(gbx_scatter_kernel<544, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  4 * GBX_SCAT_STAGE);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(gbx_scatter_kernel<1024, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
