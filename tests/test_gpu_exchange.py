@@ -466,3 +466,29 @@ def test_degenerate_patterns(case):
             g = grad_payload(p, 3)
             got, _ = backward(ex, g)
             assert_bytes_equal(got, oracle.backward(p, g, form=0 if alg == "standard" else 1), f"{case[0]} bwd")
+
+
+def test_element_offsets_beyond_int32():
+    """One-byte elements in a 2.15 GB send buffer: rank 1's elements lie past 2^31 elements,
+    which the flat form's 31-bit element indices cannot name, so those copies take the
+    segment form (64-bit offsets).  Both forms give the oracle's bytes, twice."""
+    base1 = (1 << 31) + 4096
+    sendbuf = base1 + 65536
+    p = _explicit(2, 1, [[(1, 1000, 0)], [(0, 3000, 100), (1, 500, 20000)]],
+                  [[(1, 3000, 0)], [(0, 1000, 0), (1, 500, 1000)]], 1, [0, base1], [0, 4096], sendbuf, 8192)
+    assert oracle.validate(p) == 0
+    x = np.zeros(sendbuf, np.uint8)
+    x[:4096] = pt.random_bytes(4096, 7)
+    x[base1:] = pt.random_bytes(65536, 8)
+    init = pt.random_bytes(p.recvbuf_bytes, 9)
+    want = oracle.standard(p, x, init)
+    send = dev_bytes(x)
+    for alg in ("standard", "locality"):
+        recv = dev_bytes(init)
+        ex = gbx.Exchange(p, send, recv, alg)
+        for rep in range(2):
+            ex.start()
+            ex.wait()
+            assert_bytes_equal(recv.cpu().numpy(), want, f"{alg} start {rep}")
+    del send
+    torch.cuda.empty_cache()
