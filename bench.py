@@ -13,6 +13,11 @@ One step = one start + wait of each of the three persistent requests of that pat
 value = (user-visible bytes of the three exchanges) / step time, where a forward moves
 2*V*s user bytes and the backward reads V*s and writes rows*s.
 
+End to end (`e2e`): the same step with every buffer in pinned host memory, bound to the
+three requests, so the kernels read and write it in place over the host link; `e2e_staged`:
+the step through gbx_start_host_async on device-bound requests (whole buffers copied up and
+back, two buffer sets overlapping one step's uploads with the previous step's downloads).
+
 Also reported (extras, on by default): per-form GB/s and roofline fractions, the fused
 forward+backward vs plain (one launch and one host wait per exchange) factor, the
 batched uneven-patterns (config 3: 64 SpMV halos, mixed fp32/fp64) vs plain factor, and
@@ -410,17 +415,55 @@ def run_ours(args):
             "init_s": t_init}
 
     # ---------------------------------------------------------------- e2e
-    # Steps end to end through the library's host-buffer call (gbx_start_host_async): each
-    # step uploads its inputs (the field, and the incoming gradient of the halo) from pinned
-    # host memory and reads its results (both halos, the field's gradient) back.  The field
-    # goes up once for both forward forms (the locality request reuses the device copy the
-    # standard request's upload wrote).  Two device buffer sets, so step k+1's uploads run
-    # while step k's downloads do (the two directions use separate copy engines).
+    # Steps end to end with the data on the host, through the library's C ABI, two ways.
+    # (1) `e2e`: the three persistent requests are bound to pinned host buffers (the field,
+    # both halos, the incoming halo gradient and the field gradient); the kernels read and
+    # write them in place over the host link, so only the bytes the exchange touches cross
+    # it.  (2) `e2e_staged`: requests bound to device buffers, driven by
+    # gbx_start_host_async, which uploads the whole field and gradient and reads whole halos
+    # and field gradient back (two device buffer sets, so a step's uploads overlap the
+    # previous step's downloads).
     if not args.no_e2e:
         hx = torch.empty(p.sendbuf_bytes, dtype=torch.uint8).pin_memory()
         hx.copy_(torch.from_numpy(x.view(np.uint8)))
         hg = torch.empty(p.recvbuf_bytes, dtype=torch.uint8).pin_memory()
         hg.copy_(grad_halo.view(torch.uint8).cpu())
+        hres = [torch.zeros(p.recvbuf_bytes, dtype=torch.uint8).pin_memory(),
+                torch.zeros(p.recvbuf_bytes, dtype=torch.uint8).pin_memory(),
+                torch.zeros(p.sendbuf_bytes, dtype=torch.uint8).pin_memory()]
+        eh_std = gbx.Exchange(p, hx, hres[0], "standard", dp=dp, graph=ex_std.graph)
+        eh_loc = gbx.Exchange(p, hx, hres[1], "locality", dp=dp, graph=ex_std.graph)
+        hreqs = [eh_std.request, eh_loc.request, gbx.backward_init(eh_std.request, hg, hres[2])]
+
+        def host_step():
+            for r in hreqs:
+                r.start()
+            for r in hreqs:
+                r.wait()
+
+        for _ in range(2):
+            host_step()
+        torch.cuda.synchronize()
+        barrier()
+        e0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            host_step()
+        torch.cuda.synchronize()
+        barrier()
+        e_ms = max_over_ranks((time.perf_counter() - e0) / args.e2e_steps * 1e3, dist, device="cuda")
+        hi = [r.info() for r in hreqs]
+        line["e2e"] = {"value": whole_job_rate(step_user, world, e_ms), "unit": UNIT,
+                       "h2d_bytes_per_step": s * (hi[0]["V"] + hi[1]["V_direct"] + hi[1]["U"] + hi[2]["terms"]),
+                       "d2h_bytes_per_step": s * (hi[0]["V"] + hi[1]["V"] + hi[2]["rows"]),
+                       "ms_per_step": e_ms, "steps": args.e2e_steps,
+                       "api": "the three persistent requests bound to pinned host buffers (field, halos, "
+                              "gradients); per step gbx_start + gbx_wait on each; the kernels read the field and "
+                              "gradient and write the halos and field gradient in place over the host link"}
+        assert torch.equal(hres[0], halo_std.view(torch.uint8).cpu()), "host-resident standard halo differs"
+        assert torch.equal(hres[1], hres[0]), "host-resident locality halo differs"
+        assert torch.equal(hres[2], grad_field.view(torch.uint8).cpu()), "host-resident field gradient differs"
+        del eh_std, eh_loc, hreqs, hres
+
         side = torch.cuda.Stream()           # completes the requests without ordering their stream
         sets = []
         for k in range(2):
@@ -441,7 +484,7 @@ def run_ours(args):
                         torch.empty(p.sendbuf_bytes, dtype=torch.uint8).pin_memory()]
             sets.append(S)
 
-        def e2e_step(k):
+        def staged_step(k):
             S = sets[k % 2]
             r_std, r_loc, r_bwd = S["reqs"]
             r_std.start_host_async(hx, S["out"][0])
@@ -451,23 +494,22 @@ def run_ours(args):
                 r.wait_stream(side)
 
         for k in range(2):
-            e2e_step(k)
+            staged_step(k)
         torch.cuda.synchronize()
         barrier()
         e0 = time.perf_counter()
         for k in range(args.e2e_steps):
-            e2e_step(k)
+            staged_step(k)
         torch.cuda.synchronize()
         barrier()
-        e_ms = (time.perf_counter() - e0) / args.e2e_steps * 1e3
-        e_ms = max_over_ranks(e_ms, dist, device="cuda")
-        line["e2e"] = {"value": whole_job_rate(step_user, world, e_ms), "unit": UNIT,
-                       "h2d_bytes_per_step": p.sendbuf_bytes + p.recvbuf_bytes,
-                       "d2h_bytes_per_step": 2 * p.recvbuf_bytes + p.sendbuf_bytes,
-                       "ms_per_step": e_ms, "steps": args.e2e_steps,
-                       "api": "gbx_start_host_async on the three persistent requests per step: pinned host "
-                              "field + gradient copied in, both halos + field gradient copied out; two device "
-                              "buffer sets, so a step's uploads overlap the previous step's downloads"}
+        e_ms = max_over_ranks((time.perf_counter() - e0) / args.e2e_steps * 1e3, dist, device="cuda")
+        line["e2e_staged"] = {"value": whole_job_rate(step_user, world, e_ms), "unit": UNIT,
+                              "h2d_bytes_per_step": p.sendbuf_bytes + p.recvbuf_bytes,
+                              "d2h_bytes_per_step": 2 * p.recvbuf_bytes + p.sendbuf_bytes,
+                              "ms_per_step": e_ms, "steps": args.e2e_steps,
+                              "api": "gbx_start_host_async on device-bound requests: whole field + gradient "
+                                     "uploaded, both halos + whole field gradient read back; two device buffer "
+                                     "sets, so a step's uploads overlap the previous step's downloads"}
         for S in sets:
             assert torch.equal(S["out"][0], S["out"][1])
             assert torch.equal(S["out"][2].cuda(), sets[0]["gf"].view(torch.uint8))

@@ -24,9 +24,14 @@
  *   - Unless stated otherwise, array arguments are DEVICE pointers (setup runs on the
  *     GPU) and are only read during the call; the library keeps its own copies of
  *     whatever it needs, so the caller may free them when the call returns.
- *   - Data buffers (send, receive, gradients) are device memory owned by the caller,
- *     bound to the request at init and used by every start; they must stay valid
- *     until the request is freed (MPI persistent semantics) or re-bound.
+ *   - Data buffers (send, receive, gradients) are owned by the caller, bound to the
+ *     request at init and used by every start; they must stay valid until the request
+ *     is freed (MPI persistent semantics) or re-bound.  They are device memory, or
+ *     pinned host memory the GPU can address (cudaHostAlloc / cudaHostRegister): the
+ *     kernels then read and write those buffers in place over the host link, so only
+ *     the bytes the exchange touches cross it.  The bulk-copy forms (info bulk=) are
+ *     not used on host buffers; re-binding an op tuned to one of them to host memory
+ *     returns GBX_ERR_UNSUPPORTED.
  *   - Handles are opaque and owned by the library; *_free releases them and sets the
  *     handle to NULL.
  *   - `stream` is a cudaStream_t passed as void* (NULL = the legacy default stream).

@@ -121,6 +121,16 @@ def _ptr(t) -> Optional[int]:
     return t.data_ptr()
 
 
+def _buf(t) -> Optional[int]:
+    """A data buffer: a contiguous CUDA tensor, or a contiguous pinned CPU tensor, which the
+    kernels then read or write in place over the host link."""
+    if t is None:
+        return None
+    assert t.is_contiguous() and (t.is_cuda or t.is_pinned()), \
+        "data buffers must be contiguous CUDA tensors or pinned CPU tensors"
+    return t.data_ptr()
+
+
 def _nbytes(t) -> int:
     return 0 if t is None else t.numel() * t.element_size()
 
@@ -209,7 +219,7 @@ class Request:
         _check(lib().gbx_parrived_stream(self.handle, int(rpartition), _stream_handle(stream)), "parrived_stream")
 
     def bind(self, src=None, dst=None):
-        _check(lib().gbx_request_bind(self.handle, _ptr(src), _ptr(dst)), "bind")
+        _check(lib().gbx_request_bind(self.handle, _buf(src), _buf(dst)), "bind")
         self._keep += [t for t in (src, dst) if t is not None]
 
     def start_host(self, host_src, host_dst):
@@ -250,8 +260,8 @@ def neighbor_alltoallv_init(sendbuf, send_base, sendcounts, sdispls, recvbuf, re
     """MPIX_Neighbor_alltoallv_init over the emulated communicator (see include/gbx.h)."""
     h = ctypes.c_void_p()
     _check(lib().gbx_neighbor_alltoallv_init(
-        _ptr(sendbuf), _nbytes(sendbuf), _ptr(send_base), _ptr(sendcounts), _ptr(sdispls),
-        _ptr(send_slot_ptr), _ptr(send_idx), _ptr(recvbuf), _nbytes(recvbuf), _ptr(recv_base),
+        _buf(sendbuf), _nbytes(sendbuf), _ptr(send_base), _ptr(sendcounts), _ptr(sdispls),
+        _ptr(send_slot_ptr), _ptr(send_idx), _buf(recvbuf), _nbytes(recvbuf), _ptr(recv_base),
         _ptr(recvcounts), _ptr(rdispls), _ptr(recv_slot_ptr), int(elem_size), int(dtype),
         _ptr(global_sidx), _ptr(global_ridx), graph.handle, info.encode() if info else None,
         _stream_handle(stream), ctypes.byref(h)), "neighbor_alltoallv_init")
@@ -262,7 +272,7 @@ def backward_init(forward: Request, grad_recv, grad_send, accumulate: bool = Fal
                   info: str = "", stream=None) -> Request:
     """Reverse exchange of a forward request (see include/gbx.h)."""
     h = ctypes.c_void_p()
-    _check(lib().gbx_backward_init(forward.handle, _ptr(grad_recv), _ptr(grad_send),
+    _check(lib().gbx_backward_init(forward.handle, _buf(grad_recv), _buf(grad_send),
                                    int(bool(accumulate)), info.encode() if info else None,
                                    _stream_handle(stream), ctypes.byref(h)), "backward_init")
     return Request(h, keep=(grad_recv, grad_send, forward))
@@ -273,7 +283,7 @@ def neighbor_alltoall_init(sendbuf, send_base, recvbuf, recv_base, count: int, g
     """MPI_Neighbor_alltoall, persistent (see include/gbx.h)."""
     h = ctypes.c_void_p()
     _check(lib().gbx_neighbor_alltoall_init(
-        _ptr(sendbuf), _nbytes(sendbuf), _ptr(send_base), _ptr(recvbuf), _nbytes(recvbuf), _ptr(recv_base),
+        _buf(sendbuf), _nbytes(sendbuf), _ptr(send_base), _buf(recvbuf), _nbytes(recvbuf), _ptr(recv_base),
         int(count), int(elem_size), int(dtype), graph.handle, info.encode() if info else None,
         _stream_handle(stream), ctypes.byref(h)), "neighbor_alltoall_init")
     return Request(h, keep=(sendbuf, recvbuf, graph))
@@ -284,7 +294,7 @@ def neighbor_allgather_init(sendbuf, send_base, recvbuf, recv_base, count: int, 
     """MPI_Neighbor_allgather, persistent (see include/gbx.h)."""
     h = ctypes.c_void_p()
     _check(lib().gbx_neighbor_allgather_init(
-        _ptr(sendbuf), _nbytes(sendbuf), _ptr(send_base), _ptr(recvbuf), _nbytes(recvbuf), _ptr(recv_base),
+        _buf(sendbuf), _nbytes(sendbuf), _ptr(send_base), _buf(recvbuf), _nbytes(recvbuf), _ptr(recv_base),
         int(count), int(elem_size), int(dtype), graph.handle, info.encode() if info else None,
         _stream_handle(stream), ctypes.byref(h)), "neighbor_allgather_init")
     return Request(h, keep=(sendbuf, recvbuf, graph))
@@ -296,7 +306,7 @@ def neighbor_allgatherv_init(sendbuf, send_base, sendcount, recvbuf, recv_base, 
     """MPI_Neighbor_allgatherv, persistent (see include/gbx.h)."""
     h = ctypes.c_void_p()
     _check(lib().gbx_neighbor_allgatherv_init(
-        _ptr(sendbuf), _nbytes(sendbuf), _ptr(send_base), _ptr(sendcount), _ptr(recvbuf), _nbytes(recvbuf),
+        _buf(sendbuf), _nbytes(sendbuf), _ptr(send_base), _ptr(sendcount), _buf(recvbuf), _nbytes(recvbuf),
         _ptr(recv_base), _ptr(recvcounts), _ptr(rdispls), int(elem_size), int(dtype), graph.handle,
         info.encode() if info else None, _stream_handle(stream), ctypes.byref(h)), "neighbor_allgatherv_init")
     return Request(h, keep=(sendbuf, recvbuf, graph))
@@ -307,8 +317,8 @@ def alltoallv_init(comm: Comm, sendbuf, send_base, sendcounts, sdispls, recvbuf,
     """MPIX_Alltoallv over the emulated communicator, persistent (P x P arrays, see include/gbx.h)."""
     h = ctypes.c_void_p()
     _check(lib().gbx_alltoallv_init(
-        comm.handle, _ptr(sendbuf), _nbytes(sendbuf), _ptr(send_base), _ptr(sendcounts), _ptr(sdispls),
-        _ptr(recvbuf), _nbytes(recvbuf), _ptr(recv_base), _ptr(recvcounts), _ptr(rdispls), int(elem_size),
+        comm.handle, _buf(sendbuf), _nbytes(sendbuf), _ptr(send_base), _ptr(sendcounts), _ptr(sdispls),
+        _buf(recvbuf), _nbytes(recvbuf), _ptr(recv_base), _ptr(recvcounts), _ptr(rdispls), int(elem_size),
         int(dtype), info.encode() if info else None, _stream_handle(stream), ctypes.byref(h)), "alltoallv_init")
     return Request(h, keep=(sendbuf, recvbuf, comm))
 
@@ -342,8 +352,8 @@ def neighbor_alltoallw_init(sendbuf, send_base, sendcounts, sdispls, sendtypes, 
     arr, n = datatype_table(types)
     h = ctypes.c_void_p()
     _check(lib().gbx_neighbor_alltoallw_init(
-        _ptr(sendbuf), _nbytes(sendbuf), _ptr(send_base), _ptr(sendcounts), _ptr(sdispls), _ptr(sendtypes),
-        _ptr(recvbuf), _nbytes(recvbuf), _ptr(recv_base), _ptr(recvcounts), _ptr(rdispls), _ptr(recvtypes),
+        _buf(sendbuf), _nbytes(sendbuf), _ptr(send_base), _ptr(sendcounts), _ptr(sdispls), _ptr(sendtypes),
+        _buf(recvbuf), _nbytes(recvbuf), _ptr(recv_base), _ptr(recvcounts), _ptr(rdispls), _ptr(recvtypes),
         ctypes.cast(arr, ctypes.c_void_p), int(n), int(dtype), graph.handle, info.encode() if info else None,
         _stream_handle(stream), ctypes.byref(h)), "neighbor_alltoallw_init")
     return Request(h, keep=(sendbuf, recvbuf, graph))

@@ -153,6 +153,19 @@ extern "C" int gbx_graph_free(gbx_graph_t *graph) {
 }
 
 // ------------------------------------------------------------------------- ops
+// Host memory the kernels can address (pinned, mapped): buffers there are read and written in
+// place over the host link.  The bulk-copy forms are not used on them; the index-driven
+// kernels are.
+static bool host_mem(const void *p) {
+    if (!p) return false;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeHost;
+}
+
 static int vec_of_align(uint64_t align) {
     int v = 16;
     while (v > 1 && (align & (uint64_t)(v - 1))) v >>= 1;
@@ -211,7 +224,7 @@ int gbx_make_copy_op(gbx_request_s *req, int level, const char *src, int src_rol
         d.dst_flat0 = op.flat_dst0;
         op.algo_bytes_flat = 2 * nelem * req->elem_size + 4 * nelem;
     }
-    if (req->allow_bulk) {
+    if (req->allow_bulk && !host_mem(src) && !host_mem(dst)) {
         GBX_TRY(gbx_make_bulk(req, segs, nseg, nelem, &op.d_bulk, &op.nbulk, &op.bulk_ok));
         d.bulk = op.d_bulk;
         d.nbulk = op.nbulk;
@@ -269,7 +282,7 @@ int gbx_make_flat2_op(gbx_request_s *req, int level, const char *src, int src_ro
     op.cd.flat = 3;
     op.cd.flat_didx = gd;
     op.algo_bytes = op.algo_bytes_flat = 2 * nelem * req->elem_size + 8 * nelem;
-    if (req->allow_bulk && pairs_in_source_order(req) && nelem > 0) {
+    if (req->allow_bulk && pairs_in_source_order(req) && nelem > 0 && !host_mem(src) && !host_mem(dst)) {
         GBX_TRY(gbx_make_scatter(req, gs, gd, nelem, &op.d_scat, &op.nscat, &op.scat_ok));
         op.cd.scat = op.d_scat;
         op.cd.nscat = op.nscat;
@@ -1219,9 +1232,14 @@ extern "C" int gbx_request_bind(gbx_request_t req, const void *src, void *dst) {
     }
     const char *ns = src ? (const char *)src : req->src;
     char *nd = dst ? (char *)dst : req->dst;
+    const bool ns_host = src && host_mem(src), nd_host = dst && host_mem(dst);
     for (HostOp &op : req->ops) {
         const int vec = op.kind == 0 ? op.cd.vec : op.fd.vec;
         if (((uintptr_t)ns & (uintptr_t)(vec - 1)) || ((uintptr_t)nd & (uintptr_t)(vec - 1))) return GBX_ERR_ARG;
+        // an op tuned to a bulk-copy form cannot move to host memory
+        if (op.kind == 0 && op.cd.flat >= 8 &&
+            ((ns_host && op.cd.src_role == ROLE_SRC) || (nd_host && op.cd.dst_role == ROLE_DST)))
+            return GBX_ERR_UNSUPPORTED;
     }
     for (HostOp &op : req->ops) {
         if (op.kind == 0) {

@@ -492,3 +492,50 @@ def test_element_offsets_beyond_int32():
             assert_bytes_equal(recv.cpu().numpy(), want, f"{alg} start {rep}")
     del send
     torch.cuda.empty_cache()
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_host_resident_buffers(seed):
+    """Send and receive buffers, and the backward's gradients, in pinned host memory: the
+    kernels read and write them in place over the host link.  Both forms and the backward
+    give the oracle's bytes, also with bulk=2, whose bulk-copy forms then stay on the
+    device-resident aggregates (no scatter form on host gradients)."""
+    p = pt.config5(edge=4, comps=2) if seed == 0 else pt.random_pattern(77, P=24, dtype="f64")
+    x = payload(p, 3)
+    init = pt.random_bytes(p.recvbuf_bytes, 4)
+    want = oracle.standard(p, x, init)
+    send = torch.from_numpy(x.view(np.uint8).copy()).pin_memory()
+    for alg, form in (("standard", 0), ("locality", 1)):
+        for info in ("", "bulk=2"):
+            recv = torch.from_numpy(init.copy()).pin_memory()
+            ex = gbx.Exchange(p, send, recv, alg, info=info)
+            for rep in range(2):
+                ex.start()
+                ex.wait()
+                assert_bytes_equal(recv.numpy(), want, f"{alg} {info} start {rep}")
+            g = grad_payload(p, 5)
+            old = payload(p, 6)
+            gr = torch.from_numpy(g.view(np.uint8).copy()).pin_memory()
+            for acc in (False, True):
+                gs = torch.from_numpy(old.view(np.uint8).copy()).pin_memory()
+                b = gbx.backward_init(ex.request, gr, gs, accumulate=acc, info=info)
+                b.start()
+                b.wait()
+                assert not b.info()["copy_forms"] & (1 << 9), "scatter form on host gradients"
+                assert_bytes_equal(gs.numpy(), oracle.backward(p, g, old, form=form, accumulate=acc),
+                                   f"{alg} {info} backward acc={acc}")
+
+
+def test_rebind_bulk_form_to_host_is_refused():
+    p = pt.random_pattern(3, P=24, elem_size=32, indexed=False, gaps=False, max_count=40)
+    x = pt.random_bytes(p.sendbuf_bytes, 3)
+    got, ex = forward(p, x, "standard", info="bulk=2")
+    assert_bytes_equal(got, oracle.standard(p, x), "device buffers")
+    assert ex.info()["copy_forms"] & (1 << 8)
+    host = torch.from_numpy(x.copy()).pin_memory()
+    with pytest.raises(gbx.GbxError) as e:
+        ex.request.bind(host, None)
+    assert e.value.code == gbx.ERR_UNSUPPORTED
+    ex.start()                      # still bound to its device buffers
+    ex.wait()
+    assert_bytes_equal(ex.recv.cpu().numpy(), oracle.standard(p, x), "after the refused bind")
