@@ -166,6 +166,18 @@ static bool host_mem(const void *p) {
     return a.type == cudaMemoryTypeHost;
 }
 
+// A data buffer must be memory the GPU can address: device, managed, or pinned / registered
+// host memory.  Pageable host memory is refused (GBX_ERR_ARG) rather than faulted on.
+int gbx_check_data_buf(const void *p, int64_t bytes) {
+    if (!p || bytes <= 0) return GBX_SUCCESS;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return GBX_ERR_ARG;
+    }
+    return a.type == cudaMemoryTypeUnregistered ? GBX_ERR_ARG : GBX_SUCCESS;
+}
+
 static int vec_of_align(uint64_t align) {
     int v = 16;
     while (v > 1 && (align & (uint64_t)(v - 1))) v >>= 1;
@@ -829,6 +841,8 @@ extern "C" int gbx_neighbor_alltoallv_init(const void *sendbuf, int64_t sendbuf_
     if ((sendbuf_bytes > 0 && !sendbuf) || (recvbuf_bytes > 0 && !recvbuf)) return GBX_ERR_ARG;
     if (!send_base || !recv_base) return GBX_ERR_ARG;
     if (graph->E > 0 && (!sendcounts || !sdispls || !recvcounts || !rdispls)) return GBX_ERR_ARG;
+    GBX_TRY(gbx_check_data_buf(sendbuf, sendbuf_bytes));
+    GBX_TRY(gbx_check_data_buf(recvbuf, recvbuf_bytes));
     if ((send_idx || global_sidx) && !send_slot_ptr) return GBX_ERR_ARG;
     if (global_ridx && (!recv_slot_ptr || !global_sidx)) return GBX_ERR_ARG;
     Opts o = parse_info(info);
@@ -883,6 +897,8 @@ extern "C" int gbx_neighbor_alltoallw_init(const void *sendbuf, int64_t sendbuf_
     if (!send_base || !recv_base) return GBX_ERR_ARG;
     if (graph->E > 0 && (!sendcounts || !sdispls || !sendtypes || !recvcounts || !rdispls || !recvtypes))
         return GBX_ERR_ARG;
+    GBX_TRY(gbx_check_data_buf(sendbuf, sendbuf_bytes));
+    GBX_TRY(gbx_check_data_buf(recvbuf, recvbuf_bytes));
     Opts o = parse_info(info);
     if (!o.ok) return GBX_ERR_ARG;
     if (o.algorithm != GBX_ALG_STANDARD || o.algorithm_auto) return GBX_ERR_UNSUPPORTED;
@@ -1048,6 +1064,8 @@ extern "C" int gbx_backward_init(gbx_request_t forward, const void *grad_recv, v
     const int dsz = forward->dtype == GBX_F64 ? 8 : 4;
     if (forward->elem_size % dsz) return GBX_ERR_ARG;
     if ((forward->dst_bytes > 0 && !grad_recv) || (forward->src_bytes > 0 && !grad_send)) return GBX_ERR_ARG;
+    GBX_TRY(gbx_check_data_buf(grad_recv, forward->dst_bytes));
+    GBX_TRY(gbx_check_data_buf(grad_send, forward->src_bytes));
     Opts o = parse_info(info);
     if (!o.ok) return GBX_ERR_ARG;
     gbx_request_s *req = new_request(o, stream);
@@ -1230,6 +1248,8 @@ extern "C" int gbx_request_bind(gbx_request_t req, const void *src, void *dst) {
         if (dst) req->dst = (char *)dst;
         return GBX_SUCCESS;
     }
+    GBX_TRY(gbx_check_data_buf(src, req->src_bytes));
+    GBX_TRY(gbx_check_data_buf(dst, req->dst_bytes));
     const char *ns = src ? (const char *)src : req->src;
     char *nd = dst ? (char *)dst : req->dst;
     const bool ns_host = src && host_mem(src), nd_host = dst && host_mem(dst);

@@ -263,6 +263,7 @@ int gbx_bulk_prepare(void);
 int gbx_scatter_prepare(void);
 // Scatter-form windows of a two-index copy whose pairs (gs, gd) are sorted by source and
 // whose arrays carry 4 elements of padding; *ok = 0 where the form does not apply.
+int gbx_check_data_buf(const void *p, int64_t bytes);   // GBX_ERR_ARG unless the GPU can address p
 int gbx_make_scatter(gbx_request_s *req, const int32_t *gs, const int32_t *gd, int64_t n, ScatterPiece **pieces,
                      int64_t *npieces, int *ok);
 int gbx_bulk_status_take(int *status);

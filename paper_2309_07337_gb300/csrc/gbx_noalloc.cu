@@ -206,6 +206,8 @@ extern "C" int gbx_neighbor_alltoallv_noalloc(int P, int64_t n_in_edges, const i
     if (n_in_edges > 0 && (!sources || !recvcounts || !rdispls)) return GBX_ERR_ARG;
     if (n_out_edges > 0 && (!destinations || !sendcounts || !sdispls)) return GBX_ERR_ARG;
     if (n_in_edges > GBX_NOALLOC_MAX_EDGES || n_out_edges > GBX_NOALLOC_MAX_EDGES) return GBX_ERR_LIMIT;
+    GBX_TRY(gbx_check_data_buf(sendbuf, sendbuf_bytes));
+    GBX_TRY(gbx_check_data_buf(recvbuf, recvbuf_bytes));
     unsigned char *scratch = nullptr;
     GBX_TRY(na_scratch(&scratch));
     cudaStream_t st = (cudaStream_t)stream;

@@ -539,3 +539,26 @@ def test_rebind_bulk_form_to_host_is_refused():
     ex.start()                      # still bound to its device buffers
     ex.wait()
     assert_bytes_equal(ex.recv.cpu().numpy(), oracle.standard(p, x), "after the refused bind")
+
+
+def test_pageable_host_buffers_are_refused():
+    """Pageable host memory is not addressable by the kernels: init and bind refuse it with
+    ERR_ARG before anything runs."""
+    import ctypes
+    p = pt.config1()
+    x = payload(p, 1)
+    got, ex = forward(p, x)
+    pageable = np.zeros(p.sendbuf_bytes, np.uint8)
+    rc = gbx.lib().gbx_request_bind(ex.request.handle, ctypes.c_void_p(pageable.ctypes.data), None)
+    assert rc == gbx.ERR_ARG
+    ex.start()
+    ex.wait()
+    assert_bytes_equal(ex.recv.cpu().numpy(), oracle.standard(p, x), "still bound to its device buffers")
+    dp = ex.dp
+    h = ctypes.c_void_p()
+    rc = gbx.lib().gbx_neighbor_alltoallv_init(
+        ctypes.c_void_p(pageable.ctypes.data), p.sendbuf_bytes, dp.send_base.data_ptr(), dp.sendcounts.data_ptr(),
+        dp.sdispls.data_ptr(), None, None, ex.recv.data_ptr(), p.recvbuf_bytes, dp.recv_base.data_ptr(),
+        dp.recvcounts.data_ptr(), dp.rdispls.data_ptr(), None, p.elem_size, gbx.DTYPE_CODES[p.dtype], None, None,
+        ex.graph.handle, None, None, ctypes.byref(h))
+    assert rc == gbx.ERR_ARG and not h.value
