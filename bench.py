@@ -185,6 +185,28 @@ def max_over_ranks(ms_local, dist=None, device="cpu"):
     return float(t.item())
 
 
+def all_ranks_agree(flag, dist=None, device="cpu"):
+    """True only if `flag` holds on every rank (so all ranks take the same branch)."""
+    if dist is None:
+        return bool(flag)
+    import torch
+    t = torch.tensor([1.0 if flag else 0.0], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MIN)
+    return t.item() > 0.5
+
+
+def host_mem_available():
+    """MemAvailable of this host in bytes (0 when unknown)."""
+    try:
+        with open("/proc/meminfo") as f:
+            for line in f:
+                if line.startswith("MemAvailable:"):
+                    return int(line.split()[1]) * 1024
+    except OSError:
+        pass
+    return 0
+
+
 def whole_job_rate(bytes_per_rank_step, world, ms):
     """Aggregate GB/s of `world` replicas that each move bytes_per_rank_step per step."""
     return bytes_per_rank_step * world / (ms * 1e-3) / 1e9
@@ -423,7 +445,19 @@ def run_ours(args):
     # gbx_start_host_async, which uploads the whole field and gradient and reads whole halos
     # and field gradient back (two device buffer sets, so a step's uploads overlap the
     # previous step's downloads).
+    # Every rank on this host pins its own host buffers (22 GB at 512^3): the replicas of a
+    # multi-GPU run measure end to end only where the host has room for all of them.
+    local_world = int(os.environ.get("LOCAL_WORLD_SIZE", world))
+    pinned_need = 2 * (p.sendbuf_bytes + 2 * p.recvbuf_bytes) * local_world
+    e2e_fits = True
     if not args.no_e2e:
+        barrier()
+        e2e_fits = all_ranks_agree(host_mem_available() > 1.15 * pinned_need, dist, device="cuda")
+        if not e2e_fits:
+            line["e2e"] = {"value": None, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0,
+                           "skipped": f"the {local_world} replicas on this host need {pinned_need / 1e9:.0f} GB "
+                                      f"of pinned host memory; {host_mem_available() / 1e9:.0f} GB available"}
+    if not args.no_e2e and e2e_fits:
         hx = torch.empty(p.sendbuf_bytes, dtype=torch.uint8).pin_memory()
         hx.copy_(torch.from_numpy(x.view(np.uint8)))
         hg = torch.empty(p.recvbuf_bytes, dtype=torch.uint8).pin_memory()
@@ -464,56 +498,60 @@ def run_ours(args):
         assert torch.equal(hres[2], grad_field.view(torch.uint8).cpu()), "host-resident field gradient differs"
         del eh_std, eh_loc, hreqs, hres
 
-        side = torch.cuda.Stream()           # completes the requests without ordering their stream
-        sets = []
-        for k in range(2):
-            S = {"field": field if k == 0 else torch.empty_like(field),
-                 "hs": halo_std if k == 0 else torch.empty_like(halo_std),
-                 "hl": halo_loc if k == 0 else torch.empty_like(halo_loc),
-                 "g": grad_halo if k == 0 else torch.empty_like(grad_halo),
-                 "gf": grad_field if k == 0 else torch.empty_like(grad_field)}
-            if k == 0:
-                S["reqs"] = reqs
-            else:
-                a = gbx.Exchange(p, S["field"], S["hs"], "standard", dp=dp, graph=ex_std.graph)
-                b = gbx.Exchange(p, S["field"], S["hl"], "locality", dp=dp, graph=ex_std.graph)
-                S["keep"] = (a, b)
-                S["reqs"] = [a.request, b.request, gbx.backward_init(a.request, S["g"], S["gf"])]
-            S["out"] = [torch.empty(p.recvbuf_bytes, dtype=torch.uint8).pin_memory(),
-                        torch.empty(p.recvbuf_bytes, dtype=torch.uint8).pin_memory(),
-                        torch.empty(p.sendbuf_bytes, dtype=torch.uint8).pin_memory()]
-            sets.append(S)
+        # the staged comparison holds two more device buffer sets and 23.6 GB of pinned host
+        # memory per rank, so replicas (N > 1) leave it out
+        if world == 1:
+            side = torch.cuda.Stream()           # completes the requests without ordering their stream
+            sets = []
+            for k in range(2):
+                S = {"field": field if k == 0 else torch.empty_like(field),
+                     "hs": halo_std if k == 0 else torch.empty_like(halo_std),
+                     "hl": halo_loc if k == 0 else torch.empty_like(halo_loc),
+                     "g": grad_halo if k == 0 else torch.empty_like(grad_halo),
+                     "gf": grad_field if k == 0 else torch.empty_like(grad_field)}
+                if k == 0:
+                    S["reqs"] = reqs
+                else:
+                    a = gbx.Exchange(p, S["field"], S["hs"], "standard", dp=dp, graph=ex_std.graph)
+                    b = gbx.Exchange(p, S["field"], S["hl"], "locality", dp=dp, graph=ex_std.graph)
+                    S["keep"] = (a, b)
+                    S["reqs"] = [a.request, b.request, gbx.backward_init(a.request, S["g"], S["gf"])]
+                S["out"] = [torch.empty(p.recvbuf_bytes, dtype=torch.uint8).pin_memory(),
+                            torch.empty(p.recvbuf_bytes, dtype=torch.uint8).pin_memory(),
+                            torch.empty(p.sendbuf_bytes, dtype=torch.uint8).pin_memory()]
+                sets.append(S)
 
-        def staged_step(k):
-            S = sets[k % 2]
-            r_std, r_loc, r_bwd = S["reqs"]
-            r_std.start_host_async(hx, S["out"][0])
-            r_loc.start_host_async(None, S["out"][1])
-            r_bwd.start_host_async(hg, S["out"][2])
-            for r in (r_std, r_loc, r_bwd):
-                r.wait_stream(side)
+            def staged_step(k):
+                S = sets[k % 2]
+                r_std, r_loc, r_bwd = S["reqs"]
+                r_std.start_host_async(hx, S["out"][0])
+                r_loc.start_host_async(None, S["out"][1])
+                r_bwd.start_host_async(hg, S["out"][2])
+                for r in (r_std, r_loc, r_bwd):
+                    r.wait_stream(side)
 
-        for k in range(2):
-            staged_step(k)
-        torch.cuda.synchronize()
-        barrier()
-        e0 = time.perf_counter()
-        for k in range(args.e2e_steps):
-            staged_step(k)
-        torch.cuda.synchronize()
-        barrier()
-        e_ms = max_over_ranks((time.perf_counter() - e0) / args.e2e_steps * 1e3, dist, device="cuda")
-        line["e2e_staged"] = {"value": whole_job_rate(step_user, world, e_ms), "unit": UNIT,
-                              "h2d_bytes_per_step": p.sendbuf_bytes + p.recvbuf_bytes,
-                              "d2h_bytes_per_step": 2 * p.recvbuf_bytes + p.sendbuf_bytes,
-                              "ms_per_step": e_ms, "steps": args.e2e_steps,
-                              "api": "gbx_start_host_async on device-bound requests: whole field + gradient "
-                                     "uploaded, both halos + whole field gradient read back; two device buffer "
-                                     "sets, so a step's uploads overlap the previous step's downloads"}
-        for S in sets:
-            assert torch.equal(S["out"][0], S["out"][1])
-            assert torch.equal(S["out"][2].cuda(), sets[0]["gf"].view(torch.uint8))
-        del hx, hg, sets
+            for k in range(2):
+                staged_step(k)
+            torch.cuda.synchronize()
+            barrier()
+            e0 = time.perf_counter()
+            for k in range(args.e2e_steps):
+                staged_step(k)
+            torch.cuda.synchronize()
+            barrier()
+            e_ms = max_over_ranks((time.perf_counter() - e0) / args.e2e_steps * 1e3, dist, device="cuda")
+            line["e2e_staged"] = {"value": whole_job_rate(step_user, world, e_ms), "unit": UNIT,
+                                  "h2d_bytes_per_step": p.sendbuf_bytes + p.recvbuf_bytes,
+                                  "d2h_bytes_per_step": 2 * p.recvbuf_bytes + p.sendbuf_bytes,
+                                  "ms_per_step": e_ms, "steps": args.e2e_steps,
+                                  "api": "gbx_start_host_async on device-bound requests: whole field + gradient "
+                                         "uploaded, both halos + whole field gradient read back; two device buffer "
+                                         "sets, so a step's uploads overlap the previous step's downloads"}
+            for S in sets:
+                assert torch.equal(S["out"][0], S["out"][1])
+                assert torch.equal(S["out"][2].cuda(), sets[0]["gf"].view(torch.uint8))
+            del sets
+        del hx, hg
 
     # ---------------------------------------------------------- cpu baseline
     if rank == 0 and not args.no_cpu:
