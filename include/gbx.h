@@ -201,6 +201,9 @@ int gbx_graph_free(gbx_graph_t *graph);
  *                          In a backward the same key offers (1) or forces (2) the scatter
  *                          form of the single-term rows: source windows read by the
  *                          bulk-copy engine, scattered to their destinations by the threads
+ *       max_ctas=N         at most N thread blocks in any launch (default 0: no cap), leaving
+ *                          the rest of the GPU to other requests' kernels on other streams;
+ *                          every move kernel covers its work with any grid
  *       check_dup=0|1      locality form: at init, compare the bytes of every element that
  *                          shares a (node pair, global index) value with the value's
  *                          representative in the send buffer as bound then (default 0)

@@ -56,7 +56,7 @@ struct Opts {
     int algorithm_auto = 0;
     int graph = 1, autotune = 1, vec = 0, block = 0, timeout_ms = 60000, min_run = 4, piece = 0, flat = -1;
     int split = 1, split_order = 2;   // 2: source order where the scatter form can run, else dest
-    int check_dup = 0, bulk = 1;
+    int check_dup = 0, bulk = 1, max_ctas = 0;
     bool ok = true;
 };
 
@@ -91,12 +91,13 @@ static Opts parse_info(const char *info) {
         else if (k == "split_order") o.split_order = v == "source" ? 1 : v == "dest" ? 0 : v == "auto" ? 2 : -1;
         else if (k == "check_dup") o.check_dup = atoi(v.c_str()) != 0;
         else if (k == "bulk") o.bulk = atoi(v.c_str());
+        else if (k == "max_ctas") o.max_ctas = atoi(v.c_str());
         else o.ok = false;
     }
     if (o.vec && !(o.vec == 1 || o.vec == 2 || o.vec == 4 || o.vec == 8 || o.vec == 16)) o.ok = false;
     if (o.block && !(o.block == 128 || o.block == 256 || o.block == 512 || o.block == 1024)) o.ok = false;
     if (o.timeout_ms <= 0 || o.min_run < 0 || o.piece < 0 || o.split_order < 0) o.ok = false;
-    if (o.bulk < 0 || o.bulk > 2) o.ok = false;
+    if (o.bulk < 0 || o.bulk > 2 || o.max_ctas < 0) o.ok = false;
     return o;
 }
 
@@ -409,9 +410,14 @@ static int set_vec(gbx_request_s *req, HostOp &op, int vec) {
 
 static int op_vec(const HostOp &op) { return op.kind == 0 ? op.cd.vec : op.fd.vec; }
 
-static int grid_for(int kind, int dtype, int vec, int flat, int block, int persistent, int64_t tiles) {
-    if (!persistent) return (int)std::min<int64_t>(tiles, 1ll << 30);
-    int64_t g = (int64_t)gbx_num_sms() * gbx_occupancy(kind, dtype, vec, block, flat);
+// Grid of a launch: one block per tile, or persistent (SMs x resident blocks); at most
+// max_ctas blocks when that is set (every move kernel walks its tiles grid-stride, so any
+// grid covers them), which leaves room for other requests' kernels on other streams.
+static int grid_for(int kind, int dtype, int vec, int flat, int block, int persistent, int64_t tiles,
+                    int max_ctas) {
+    int64_t g = persistent ? (int64_t)gbx_num_sms() * gbx_occupancy(kind, dtype, vec, block, flat)
+                           : std::min<int64_t>(tiles, 1ll << 30);
+    if (max_ctas > 0) g = std::min<int64_t>(g, max_ctas);
     return (int)std::max<int64_t>(1, std::min<int64_t>(g, tiles));
 }
 
@@ -428,7 +434,7 @@ static cudaError_t launch_op_alone(gbx_request_s *req, HostOp &op, int block, in
     int64_t tiles = op_tiles(op);
     const int vec = op_vec(op), flat = op_flat(op);
     return launch_list(op.kind, req->dtype, vec, flat, op.d_self, op.d_self_prefix, 1, tiles, block,
-                       grid_for(op.kind, req->dtype, vec, flat, block, persistent, tiles), req->stream);
+                       grid_for(op.kind, req->dtype, vec, flat, block, persistent, tiles, req->max_ctas), req->stream);
 }
 
 // ------------------------------------------------------------------ autotuner
@@ -576,7 +582,7 @@ static int tune_launch(LevelLaunch &L, cudaStream_t st) {
     for (int bi = 0; bi < 4 && e == cudaSuccess; bi++)
         for (int pers = 1; pers >= 0 && e == cudaSuccess; pers--) {
             const int blk = gbx_effective_block(L.vec, blocks[bi]);
-            const int grid = grid_for(L.kind, L.dtype, L.vec, L.flat, blk, pers, L.total_tiles);
+            const int grid = grid_for(L.kind, L.dtype, L.vec, L.flat, blk, pers, L.total_tiles, L.max_ctas);
             e = launch_list(L.kind, L.dtype, L.vec, L.flat, L.d_ops, L.d_prefix, L.nops, L.total_tiles, blk, grid, st);
             float t = 1e30f;
             for (int r = 0; r < 3 && e == cudaSuccess; r++) {
@@ -603,7 +609,7 @@ static int tune_launch(LevelLaunch &L, cudaStream_t st) {
 }
 
 static int build_levels(DevPool &mem, const std::vector<HostOp *> &ops, const std::vector<int> &dtypes,
-                        std::vector<LevelLaunch> &out, int batch, cudaStream_t st, int tune = 0) {
+                        std::vector<LevelLaunch> &out, int batch, cudaStream_t st, int tune = 0, int max_ctas = 0) {
     int nlev = 0;
     for (HostOp *op : ops) nlev = std::max(nlev, op->level + 1);
     for (int lv = 0; lv < nlev; lv++)
@@ -654,7 +660,8 @@ static int build_levels(DevPool &mem, const std::vector<HostOp *> &ops, const st
                 L.total_tiles = pre.back();
                 // the launch takes the tuned shape of its largest op
                 L.block = gbx_effective_block(L.vec, big->block);
-                L.grid = grid_for(kind, L.dtype, L.vec, L.flat, L.block, big->persistent, L.total_tiles);
+                L.max_ctas = max_ctas;
+                L.grid = grid_for(kind, L.dtype, L.vec, L.flat, L.block, big->persistent, L.total_tiles, max_ctas);
                 GBX_TRY(mem.get(&L.d_ops, L.nops));
                 GBX_TRY(mem.get(&L.d_prefix, L.nops + 1));
                 GBX_CUDA_TRY(cudaMemcpyAsync(L.d_ops, ptrs.data(), sizeof(void *) * ptrs.size(),
@@ -732,7 +739,7 @@ static int finalize(gbx_request_s *req) {
     std::vector<HostOp *> ptrs;
     std::vector<int> dts;
     for (HostOp &op : req->ops) { ptrs.push_back(&op); dts.push_back(req->dtype); }
-    GBX_TRY(build_levels(req->mem, ptrs, dts, req->launches, 0, req->stream));
+    GBX_TRY(build_levels(req->mem, ptrs, dts, req->launches, 0, req->stream, 0, req->max_ctas));
     if (req->use_graph && !req->launches.empty()) GBX_TRY(capture(req->launches, &req->exec));
     fill_info(req);
     return GBX_SUCCESS;
@@ -800,6 +807,7 @@ static gbx_request_s *new_request(const Opts &o, void *stream) {
     req->split_order = o.split_order;
     req->check_dup = o.check_dup;
     req->allow_bulk = o.bulk;
+    req->max_ctas = o.max_ctas;
     if (cudaEventCreateWithFlags(&req->done, cudaEventDisableTiming) != cudaSuccess) {
         cudaGetLastError();
         req->done = nullptr;
@@ -1213,9 +1221,12 @@ extern "C" int gbx_startall(int count, gbx_request_t *reqs) {
         std::vector<int> dts;
         for (gbx_request_s *r : key)
             for (HostOp &op : r->ops) { ops.push_back(&op); dts.push_back(r->dtype); }
-        int tune = 1;
-        for (gbx_request_s *r : key) tune &= r->autotune && !r->forced_block;
-        int rc = build_levels(b->mem, ops, dts, b->launches, 1, st, tune);
+        int tune = 1, cap = 0;
+        for (gbx_request_s *r : key) {
+            tune &= r->autotune && !r->forced_block;
+            if (r->max_ctas > 0) cap = cap > 0 ? std::min(cap, r->max_ctas) : r->max_ctas;
+        }
+        int rc = build_levels(b->mem, ops, dts, b->launches, 1, st, tune, cap);
         if (rc == GBX_SUCCESS && cudaEventCreateWithFlags(&b->done, cudaEventDisableTiming) != cudaSuccess)
             rc = GBX_ERR_CUDA;
         if (rc == GBX_SUCCESS && !b->launches.empty()) rc = capture(b->launches, &b->exec);

@@ -150,6 +150,7 @@ struct LevelLaunch {
     int grid;
     int nops;
     int64_t total_tiles;
+    int max_ctas;           // grid cap (0: none)
     void **d_ops;           // device array of descriptor pointers
     int64_t *d_prefix;      // device tile prefix (nops + 1)
 };
@@ -170,6 +171,7 @@ struct gbx_request_s {
     int split_order;         // single-term rows as copies: 0 in row (destination) order, 1 in source order
     int check_dup;           // locality form: compare every deduplicated value's bytes with its representative's at init
     int allow_bulk;          // offer the bulk form to the autotuner where it applies
+    int max_ctas;            // cap on every launch's grid (0: none)
     int timeout_ms;
     gbx_graph_s *graph;
     gbx_request_s *forward;  // backward: its forward request

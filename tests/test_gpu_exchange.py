@@ -320,6 +320,7 @@ def test_error_codes_match_oracle(case):
 
 
 @pytest.mark.parametrize("info", ["", "single_split=0", "flat=0", "vec=8;block=128", "single_split=0;block=1024",
+                                  "max_ctas=7", "max_ctas=1;bulk=2",
                                   "split_order=source", "split_order=source;vec=8", "split_order=dest",
                                   "bulk=2"])
 def test_backward_modes_identical(info):
