@@ -1307,7 +1307,7 @@ extern "C" int gbx_start_host_async(gbx_request_t req, const void *host_src, voi
         // request's stream (earlier exchanges that read the source)
         GBX_CUDA_TRY(cudaEventRecord(req->host_mark, req->stream));
         GBX_CUDA_TRY(cudaStreamWaitEvent(req->host_up, req->host_mark, 0));
-        GBX_CUDA_TRY(cudaMemcpyAsync((void *)req->src, host_src, req->src_bytes, cudaMemcpyHostToDevice,
+        GBX_CUDA_TRY(cudaMemcpyAsync((void *)req->src, host_src, req->src_bytes, cudaMemcpyDefault,
                                      req->host_up));
         GBX_CUDA_TRY(cudaEventRecord(req->host_up_ev, req->host_up));
         GBX_CUDA_TRY(cudaStreamWaitEvent(req->stream, req->host_up_ev, 0));
@@ -1315,7 +1315,7 @@ extern "C" int gbx_start_host_async(gbx_request_t req, const void *host_src, voi
     GBX_TRY(enqueue_start(req));
     if (host_dst && req->dst_bytes > 0) {
         GBX_CUDA_TRY(cudaStreamWaitEvent(req->host_down, req->done, 0));
-        GBX_CUDA_TRY(cudaMemcpyAsync(host_dst, req->dst, req->dst_bytes, cudaMemcpyDeviceToHost, req->host_down));
+        GBX_CUDA_TRY(cudaMemcpyAsync(host_dst, req->dst, req->dst_bytes, cudaMemcpyDefault, req->host_down));
         GBX_CUDA_TRY(cudaEventRecord(req->host_down_ev, req->host_down));
         GBX_CUDA_TRY(cudaEventRecord(req->done, req->host_down));   // complete once read back
         req->host_down_pending = 1;

@@ -499,21 +499,26 @@ def test_element_offsets_beyond_int32():
 def test_host_resident_buffers(seed):
     """Send and receive buffers, and the backward's gradients, in pinned host memory: the
     kernels read and write them in place over the host link.  Both forms and the backward
-    give the oracle's bytes, also with bulk=2, whose bulk-copy forms then stay on the
-    device-resident aggregates (no scatter form on host gradients)."""
+    give the oracle's bytes, graph-captured, eager and batched, also with bulk=2, whose
+    bulk-copy forms then stay on the device-resident aggregates (no scatter form on host
+    gradients)."""
     p = pt.config5(edge=4, comps=2) if seed == 0 else pt.random_pattern(77, P=24, dtype="f64")
     x = payload(p, 3)
     init = pt.random_bytes(p.recvbuf_bytes, 4)
     want = oracle.standard(p, x, init)
     send = torch.from_numpy(x.view(np.uint8).copy()).pin_memory()
     for alg, form in (("standard", 0), ("locality", 1)):
-        for info in ("", "bulk=2"):
+        for info in ("", "bulk=2", "graph=0"):
             recv = torch.from_numpy(init.copy()).pin_memory()
             ex = gbx.Exchange(p, send, recv, alg, info=info)
             for rep in range(2):
                 ex.start()
                 ex.wait()
                 assert_bytes_equal(recv.numpy(), want, f"{alg} {info} start {rep}")
+            recv.copy_(torch.from_numpy(init))
+            gbx.startall([ex.request])
+            gbx.waitall([ex.request])
+            assert_bytes_equal(recv.numpy(), want, f"{alg} {info} batched")
             g = grad_payload(p, 5)
             old = payload(p, 6)
             gr = torch.from_numpy(g.view(np.uint8).copy()).pin_memory()
