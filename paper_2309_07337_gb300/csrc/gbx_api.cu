@@ -296,7 +296,7 @@ int gbx_make_flat2_op(gbx_request_s *req, int level, const char *src, int src_ro
     op.cd.flat_didx = gd;
     op.algo_bytes = op.algo_bytes_flat = 2 * nelem * req->elem_size + 8 * nelem;
     if (req->allow_bulk && pairs_in_source_order(req) && nelem > 0 && !host_mem(src) && !host_mem(dst)) {
-        GBX_TRY(gbx_make_scatter(req, gs, gd, nelem, &op.d_scat, &op.nscat, &op.scat_ok));
+        GBX_TRY(gbx_make_scatter(req, gs, nelem, &op.d_scat, &op.nscat, &op.scat_ok));
         op.cd.scat = op.d_scat;
         op.cd.nscat = op.nscat;
         op.algo_bytes_scat = 2 * nelem * req->elem_size + 8 * nelem + op.nscat * (int64_t)sizeof(ScatterPiece);

@@ -1234,11 +1234,10 @@ __global__ void scatter_fill_kernel(const int32_t *gs, const int64_t *start, con
     FOR_EACH(w, nw) scatter_walk(gs, start[w], w + 1 < nw ? start[w + 1] : n, s, pieces + off[w]);
 }
 
-int gbx_make_scatter(gbx_request_s *req, const int32_t *gs, const int32_t *gd, int64_t n, ScatterPiece **pieces,
+int gbx_make_scatter(gbx_request_s *req, const int32_t *gs, int64_t n, ScatterPiece **pieces,
                      int64_t *npieces, int *ok) {
     cudaStream_t st = req->stream;
     const int64_t s = req->elem_size;
-    (void)gd;
     *ok = 0;
     *npieces = 0;
     if (n <= 0 || (s & 15) || s > GBX_SCAT_WIN || (req->align & 15)) return GBX_SUCCESS;
