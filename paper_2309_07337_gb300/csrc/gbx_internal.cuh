@@ -263,11 +263,12 @@ int gbx_make_bulk(gbx_request_s *req, const Seg *segs, int64_t nseg, int64_t nel
                   int *ok);
 int gbx_bulk_prepare(void);
 int gbx_scatter_prepare(void);
-// Scatter-form windows of a two-index copy whose pairs (gs, gd) are sorted by source and
-// whose arrays carry 4 elements of padding; *ok = 0 where the form does not apply.
 int gbx_check_data_buf(const void *p, int64_t bytes);   // GBX_ERR_ARG unless the GPU can address p
-int gbx_make_scatter(gbx_request_s *req, const int32_t *gs, const int32_t *gd, int64_t n, ScatterPiece **pieces,
-                     int64_t *npieces, int *ok);
+// Scatter-form windows of a two-index copy whose pairs are sorted by source (gs, the source
+// indices, decide the windows) and whose index arrays carry 4 elements of padding; *ok = 0
+// where the form does not apply.
+int gbx_make_scatter(gbx_request_s *req, const int32_t *gs, int64_t n, ScatterPiece **pieces, int64_t *npieces,
+                     int *ok);
 int gbx_bulk_status_take(int *status);
 int gbx_make_flat(gbx_request_s *req, const Seg *segs, int64_t nseg, const int32_t *idx, int64_t nelem,
                   int32_t **flat_idx, int64_t *dst0, int *ok);
