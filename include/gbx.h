@@ -156,13 +156,14 @@ int gbx_graph_free(gbx_graph_t *graph);
  * recvbuf, and elem_r(q) = send_idx[send_slot_ptr[r] + q] when send_idx is given (the
  * pack-by-send-index-list step), else q (a user-packed send buffer).
  *
- *   sendbuf, sendbuf_bytes     device send buffer of all ranks and its size in bytes
+ *   sendbuf, sendbuf_bytes     send buffer of all ranks (device, or pinned host memory; a
+ *                              pageable host pointer gives GBX_ERR_ARG) and its size in bytes
  *   send_base[P]               byte offset of each rank's send region (int64)
  *   sendcounts, sdispls        per out-edge, in elements (int32, >= 0)
  *   send_slot_ptr[P+1]         CSR of send slots; required with send_idx or global_sidx,
  *                              then sdispls[e] + sendcounts[e] <= slots of r; else NULL
  *   send_idx                   per send slot, element index in the rank's region; or NULL
- *   recvbuf, recvbuf_bytes     device receive buffer of all ranks and its size
+ *   recvbuf, recvbuf_bytes     receive buffer of all ranks (same rules) and its size
  *   recv_base[P]               byte offset of each rank's receive region
  *   recvcounts, rdispls        per in-edge, in elements; recvcounts must equal the paired
  *                              sendcounts (else GBX_ERR_TRUNCATE)
