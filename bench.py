@@ -1050,6 +1050,8 @@ def run_bwd_forms(args):
                 b.start()
                 b.wait()
             ts = []
+            tag = "bwdform_" + alg + "_" + ("".join(c if c.isalnum() else "_" for c in info) or "default")
+            torch.cuda.nvtx.range_push(tag)   # for ncu --nvtx-include "<tag>/"
             for _ in range(20):
                 e0 = torch.cuda.Event(enable_timing=True)
                 e1 = torch.cuda.Event(enable_timing=True)
@@ -1059,6 +1061,7 @@ def run_bwd_forms(args):
                 b.wait()
                 e1.synchronize()
                 ts.append(e0.elapsed_time(e1))
+            torch.cuda.nvtx.range_pop()
             ms = statistics.median(ts)
             i = b.info()
             if ref is None:
