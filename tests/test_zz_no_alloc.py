@@ -94,3 +94,23 @@ def test_noalloc_refuses_sizes_beyond_its_scratch(noalloc):
     assert call(noalloc, p, dp, send, out, n_in=MAX_EDGES + 1, n_out=MAX_EDGES + 1) == gbx.ERR_LIMIT
     # still usable afterwards
     assert call(noalloc, p, dp, send, out) == gbx.SUCCESS
+
+
+def test_noalloc_on_host_buffers(noalloc):
+    """Send and receive buffers in pinned host memory, read and written in place; a pageable
+    host buffer is refused with ERR_ARG before any device work."""
+    p = packed(pt.config1())
+    dp = gbx.DevicePattern(p)
+    x = pt.random_bytes(p.sendbuf_bytes, 7)
+    init = pt.random_bytes(p.recvbuf_bytes, 8)
+    ref = torch.from_numpy(init.copy()).cuda()
+    ex = gbx.Exchange(p, torch.from_numpy(x).cuda(), ref, dp=dp)
+    ex.start()
+    ex.wait()
+    send = torch.from_numpy(x.copy()).pin_memory()
+    out = torch.from_numpy(init.copy()).pin_memory()
+    assert call(noalloc, p, dp, send, out) == gbx.SUCCESS
+    torch.cuda.synchronize()
+    assert torch.equal(out, ref.cpu())
+    pageable = torch.from_numpy(x.copy())
+    assert call(noalloc, p, dp, pageable, out) == gbx.ERR_ARG
