@@ -568,3 +568,37 @@ def test_pageable_host_buffers_are_refused():
         dp.recvcounts.data_ptr(), dp.rdispls.data_ptr(), None, p.elem_size, gbx.DTYPE_CODES[p.dtype], None, None,
         ex.graph.handle, None, None, ctypes.byref(h))
     assert rc == gbx.ERR_ARG and not h.value
+
+
+@pytest.mark.parametrize("info", ["", "bulk=2", "flat=0", "graph=0;max_ctas=5"])
+def test_guard_bands_untouched(info):
+    """Every form writes only inside the buffers bound to it: 4 KB bands of random bytes just
+    before and after the receive buffer and the gradient buffer are unchanged after the
+    forward and the backward, and the bytes inside match the oracle (receive slots and
+    gradient elements no block writes keep their old bytes)."""
+    G = 4096
+    for p in (pt.config5(edge=4, comps=2), pt.random_pattern(123, P=24, dtype="f64")):
+        x = payload(p, 1)
+        g = grad_payload(p, 2)
+        send = dev_bytes(x)
+        for alg, form in (("standard", 0), ("locality", 1)):
+            big = torch.from_numpy(pt.random_bytes(p.recvbuf_bytes + 2 * G, 9)).cuda()
+            before = big.clone()
+            recv = big[G:G + p.recvbuf_bytes]
+            ex = gbx.Exchange(p, send, recv, alg, info=info)
+            ex.start()
+            ex.wait()
+            assert torch.equal(big[:G], before[:G]) and torch.equal(big[G + p.recvbuf_bytes:],
+                                                                    before[G + p.recvbuf_bytes:]), f"{alg} recv guard"
+            assert_bytes_equal(recv.cpu().numpy(), oracle.standard(p, x, before[G:G + p.recvbuf_bytes].cpu().numpy()),
+                               f"{alg} {info} forward")
+            gbig = torch.from_numpy(pt.random_bytes(p.sendbuf_bytes + 2 * G, 10)).cuda()
+            gbefore = gbig.clone()
+            gs = gbig[G:G + p.sendbuf_bytes]
+            b = gbx.backward_init(ex.request, dev_bytes(g), gs, info=info)
+            b.start()
+            b.wait()
+            assert torch.equal(gbig[:G], gbefore[:G]) and torch.equal(gbig[G + p.sendbuf_bytes:],
+                                                                      gbefore[G + p.sendbuf_bytes:]), f"{alg} grad guard"
+            old = gbefore[G:G + p.sendbuf_bytes].cpu().numpy()
+            assert_bytes_equal(gs.cpu().numpy(), oracle.backward(p, g, old, form=form), f"{alg} {info} backward")
