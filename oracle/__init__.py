@@ -18,7 +18,11 @@ follows, from "MPI Advance: Open-Source Message Passing Optimizations" (arXiv
     orc_alltoallw_backward);
   * the partitioned (early-bird) exchange of section 2.3: the state after a subset of
     send partitions has moved, and which receive partitions have arrived
-    (orc_standard_partial, orc_arrived).
+    (orc_standard_partial, orc_arrived);
+  * the other neighbourhood collectives (MPI_Neighbor_alltoall, _allgather, _allgatherv:
+    section 2.2's drop-in replacements) and MPIX_Alltoallv over the whole communicator
+    (section 2.1, Listing 2), each as the neighbourhood all-to-all-v whose counts and
+    displacements the MPI standard fixes (orc_derive_neighbor, orc_complete_graph).
 
 Parity is pinned by tests/test_oracle_pins.py against brute-force global indexing,
 hand-worked golden cases, invariants and closed-form counts.  The backward's bit
@@ -31,6 +35,7 @@ from __future__ import annotations
 import ctypes
 import os
 import subprocess
+import types
 
 import numpy as np
 
@@ -39,7 +44,7 @@ _SRC = os.path.join(_HERE, "oracle.c")
 _LIB = os.path.join(_HERE, "liboracle.so")
 
 OK, ERR_ARG, ERR_RANK, ERR_TRUNCATE, ERR_INDEX, ERR_DUP, ERR_GIDX = 0, 1, 2, 3, 4, 5, 6
-ERR_NOMEM, ERR_OVERLAP = 10, 13
+ERR_NOMEM, ERR_UNSUPPORTED, ERR_OVERLAP = 10, 11, 13
 DTYPES = {"bytes": 0, "f32": 1, "f64": 2}
 
 _lib = None
@@ -109,7 +114,9 @@ def load(path: str | None = None):
     lib.orc_alltoallw_backward.argtypes = [W, ctypes.c_int, ctypes.c_int, vp, vp]
     lib.orc_standard_partial.argtypes = [P, ctypes.c_int, vp, vp, vp, vp]
     lib.orc_arrived.argtypes = [P, ctypes.c_int, vp, vp, ctypes.c_int, vp, vp]
-    for f in ("orc_standard_partial", "orc_arrived"):
+    lib.orc_derive_neighbor.argtypes = [P, ctypes.c_int, ctypes.c_int, vp, vp, vp, vp, vp]
+    lib.orc_complete_graph.argtypes = [ctypes.c_int, vp, vp]
+    for f in ("orc_standard_partial", "orc_arrived", "orc_derive_neighbor", "orc_complete_graph"):
         getattr(lib, f).restype = ctypes.c_int
     for f in ("orc_match", "orc_validate", "orc_standard", "orc_locality",
               "orc_locality_stats", "orc_locality_layout", "orc_backward",
@@ -347,3 +354,88 @@ def arrived(p, part_ptr, ready, rpart_ptr, lib=None):
     if rc:
         raise OracleError(rc)
     return out
+
+
+# ------------------------------------------------ derived neighbourhood collectives
+
+_PATTERN_KEYS = ("name", "P", "ppn", "in_ptr", "sources", "out_ptr", "dests", "sendcounts", "sdispls",
+                 "recvcounts", "rdispls", "send_base", "recv_base", "send_slot_ptr", "send_idx",
+                 "recv_slot_ptr", "global_sidx", "global_ridx", "elem_size", "sendbuf_bytes",
+                 "recvbuf_bytes", "dtype")
+
+
+def _explicit(g, sendcounts, sdispls, recvcounts, rdispls):
+    """The neighbourhood all-to-all-v problem of g's graph, bases and buffers with the given
+    per-edge arrays, user-packed (no send lists, no global indices)."""
+    q = types.SimpleNamespace(**{k: getattr(g, k, None) for k in _PATTERN_KEYS})
+    q.sendcounts = np.ascontiguousarray(sendcounts, dtype=np.int32)
+    q.sdispls = np.ascontiguousarray(sdispls, dtype=np.int32)
+    q.recvcounts = np.ascontiguousarray(recvcounts, dtype=np.int32)
+    q.rdispls = np.ascontiguousarray(rdispls, dtype=np.int32)
+    q.send_slot_ptr = q.send_idx = q.recv_slot_ptr = q.global_sidx = q.global_ridx = None
+    q.dtype = q.dtype or "bytes"
+    return q
+
+
+def neighbor_pattern(g, kind, count=0, sendcount=None, recvcounts=None, rdispls=None, lib=None):
+    """The all-to-all-v problem equal to MPI_Neighbor_<kind> on g (its graph, per-rank byte
+    bases, element size and buffer sizes): kind "alltoall" or "allgather" with `count`,
+    or "allgatherv" with the per-rank `sendcount` and the caller's per-in-edge `recvcounts`
+    and `rdispls`.  The counts and displacements come from orc_derive_neighbor."""
+    lib = lib or load()
+    mode = {"alltoall": 0, "allgather": 1, "allgatherv": 2}[kind]
+    E, Ein = int(g.out_ptr[-1]), int(g.in_ptr[-1])
+    sc, sd = np.zeros(max(E, 1), np.int32), np.zeros(max(E, 1), np.int32)
+    rc, rd = np.zeros(max(Ein, 1), np.int32), np.zeros(max(Ein, 1), np.int32)
+    rk = None if sendcount is None else np.ascontiguousarray(sendcount, dtype=np.int32)
+    m = _Marshalled(types.SimpleNamespace(**{k: getattr(g, k, None) for k in _PATTERN_KEYS}))
+    err = lib.orc_derive_neighbor(m.ref(), mode, int(count), None if rk is None else rk.ctypes.data,
+                                  sc.ctypes.data, sd.ctypes.data, rc.ctypes.data, rd.ctypes.data)
+    if err:
+        raise OracleError(err)
+    if mode == 2:
+        rc, rd = recvcounts, rdispls
+    return _explicit(g, sc[:E], sd[:E], np.asarray(rc)[:Ein], np.asarray(rd)[:Ein])
+
+
+def neighbor_alltoall(g, count, sendbuf, recvbuf=None, lib=None):
+    """MPI_Neighbor_alltoall on g; returns the receive bytes (see neighbor_pattern)."""
+    return standard(neighbor_pattern(g, "alltoall", count=count, lib=lib), sendbuf, recvbuf, lib=lib)
+
+
+def neighbor_allgather(g, count, sendbuf, recvbuf=None, lib=None):
+    """MPI_Neighbor_allgather on g; returns the receive bytes."""
+    return standard(neighbor_pattern(g, "allgather", count=count, lib=lib), sendbuf, recvbuf, lib=lib)
+
+
+def neighbor_allgatherv(g, sendcount, recvcounts, rdispls, sendbuf, recvbuf=None, lib=None):
+    """MPI_Neighbor_allgatherv on g; returns the receive bytes."""
+    q = neighbor_pattern(g, "allgatherv", sendcount=sendcount, recvcounts=recvcounts, rdispls=rdispls, lib=lib)
+    return standard(q, sendbuf, recvbuf, lib=lib)
+
+
+def alltoallv_pattern(P, ppn, sendcounts, sdispls, recvcounts, rdispls, send_base, recv_base, elem_size,
+                      sendbuf_bytes, recvbuf_bytes, dtype="bytes", lib=None):
+    """The neighbourhood all-to-all-v problem equal to MPIX_Alltoallv over P ranks: the
+    complete graph of orc_complete_graph with the P x P matrices (row-major by rank:
+    sendcounts[r*P + d] from r to d, recvcounts[d*P + r] at d from r) as per-edge arrays."""
+    lib = lib or load()
+    ptr = np.zeros(P + 1, np.int32)
+    ranks = np.zeros(max(P * P, 1), np.int32)
+    err = lib.orc_complete_graph(int(P), ptr.ctypes.data, ranks.ctypes.data)
+    if err:
+        raise OracleError(err)
+    g = types.SimpleNamespace(name="alltoallv", P=int(P), ppn=int(ppn), in_ptr=ptr, sources=ranks[:P * P],
+                              out_ptr=ptr, dests=ranks[:P * P], send_base=np.asarray(send_base, np.int64),
+                              recv_base=np.asarray(recv_base, np.int64), elem_size=int(elem_size),
+                              sendbuf_bytes=int(sendbuf_bytes), recvbuf_bytes=int(recvbuf_bytes), dtype=dtype)
+    return _explicit(g, np.ravel(sendcounts), np.ravel(sdispls), np.ravel(recvcounts), np.ravel(rdispls))
+
+
+def alltoallv(P, ppn, sendcounts, sdispls, recvcounts, rdispls, send_base, recv_base, elem_size, sendbuf,
+              recvbuf_bytes, recvbuf=None, lib=None):
+    """MPIX_Alltoallv over P ranks; returns the receive bytes."""
+    sb = np.ascontiguousarray(sendbuf).view(np.uint8).reshape(-1)
+    q = alltoallv_pattern(P, ppn, sendcounts, sdispls, recvcounts, rdispls, send_base, recv_base, elem_size,
+                          sb.size, recvbuf_bytes, lib=lib)
+    return standard(q, sb, recvbuf, lib=lib)

@@ -56,6 +56,7 @@ enum {
     ORC_ERR_DUP = 5,       /* one global index carried by different bytes             */
     ORC_ERR_GIDX = 6,      /* receive global index differs from the matched send index */
     ORC_ERR_NOMEM = 10,
+    ORC_ERR_UNSUPPORTED = 11, /* a derived displacement beyond the int32 range           */
     ORC_ERR_OVERLAP = 13   /* two receive blocks write the same bytes                  */
 };
 enum { ORC_BYTES = 0, ORC_F32 = 1, ORC_F64 = 2 };
@@ -982,4 +983,73 @@ int orc_arrived(const orc_pattern *pt, int npart, const int64_t *part_ptr, const
     }
     free(sp); free(rp); free(match);
     return err;
+}
+
+/* -------------------------------------------- derived neighbourhood collectives --- */
+
+/* MPI Advance offers its persistent neighbourhood collectives as drop-in replacements of
+ * the MPI calls (section 2.2) and its all-to-all-v over the whole communicator as
+ * MPIX_Alltoallv (section 2.1, Listing 2).  Their meaning is the MPI standard's, and each
+ * is a neighbourhood all-to-all-v with counts and displacements fixed by the call:
+ *   mode 0, MPI_Neighbor_alltoall(count): rank r sends `count` elements starting at
+ *     element j*count of its send region to its j-th out-neighbour; rank d stores the
+ *     `count` elements coming from its i-th in-neighbour at element i*count of its
+ *     receive region;
+ *   mode 1, MPI_Neighbor_allgather(count): rank r sends the same elements [0, count) of
+ *     its send region to every out-neighbour; rank d stores the block from its i-th
+ *     in-neighbour at element i*count;
+ *   mode 2, MPI_Neighbor_allgatherv(sendcount[r], recvcounts, rdispls): rank r sends its
+ *     elements [0, sendcount[r]) to every out-neighbour; rank d receives recvcounts[i]
+ *     elements from its i-th in-neighbour at element rdispls[i] (given by the caller, so
+ *     only the send side is derived here).
+ * "j-th" and "i-th" are positions in the rank's own out- and in-list.  A repeated
+ * neighbour is paired by the multigraph rule of orc_match, like every other exchange.
+ * This fills the per-out-edge sendcounts / sdispls and, for modes 0 and 1, the per-in-edge
+ * recvcounts / rdispls.  Errors: the graph's own (orc_match), ORC_ERR_ARG for a negative
+ * count or a missing array, ORC_ERR_UNSUPPORTED when a derived displacement exceeds the
+ * int32 range of the all-to-all-v arguments. */
+int orc_derive_neighbor(const orc_pattern *g, int mode, int count, const int *rank_count, int *sendcounts,
+                        int *sdispls, int *recvcounts, int *rdispls) {
+    if (!g || g->P <= 0 || !g->in_ptr || !g->out_ptr || mode < 0 || mode > 2) return ORC_ERR_ARG;
+    int P = g->P;
+    int64_t n = g->out_ptr[P] > 0 ? g->out_ptr[P] : 1;
+    int64_t *match = malloc(sizeof(int64_t) * n);
+    if (!match) return ORC_ERR_NOMEM;
+    int err = orc_match(g, match);
+    free(match);
+    if (err) return err;
+    if ((mode != 2 && count < 0) || (mode == 2 && !rank_count)) return ORC_ERR_ARG;
+    if (!sendcounts || !sdispls || (mode != 2 && (!recvcounts || !rdispls))) return ORC_ERR_ARG;
+    for (int r = 0; r < P; r++)
+        for (int64_t e = g->out_ptr[r]; e < g->out_ptr[r + 1]; e++) {
+            int64_t j = e - g->out_ptr[r];     /* position of this neighbour in r's out-list */
+            int64_t disp = mode == 0 ? j * (int64_t)count : 0;
+            if (disp > INT32_MAX) err = ORC_ERR_UNSUPPORTED;
+            sendcounts[e] = mode == 2 ? rank_count[r] : count;
+            sdispls[e] = disp > INT32_MAX ? 0 : (int)disp;
+        }
+    if (mode != 2)
+        for (int d = 0; d < P; d++)
+            for (int64_t i = g->in_ptr[d]; i < g->in_ptr[d + 1]; i++) {
+                int64_t k = i - g->in_ptr[d];  /* position of this neighbour in d's in-list */
+                int64_t disp = k * (int64_t)count;
+                if (disp > INT32_MAX) err = ORC_ERR_UNSUPPORTED;
+                recvcounts[i] = count;
+                rdispls[i] = disp > INT32_MAX ? 0 : (int)disp;
+            }
+    return err;
+}
+
+/* The communicator of MPIX_Alltoallv as a distributed graph: every rank lists every rank,
+ * itself included, in rank order, in both its in- and out-list.  Rank r's out-edge to d is
+ * then edge r*P + d and d's in-edge from r is edge d*P + r, so the P x P count and
+ * displacement matrices of the call (row-major by rank) are the per-edge arrays as they
+ * are.  ptr has P+1 entries, ranks P*P; ORC_ERR_UNSUPPORTED when P*P exceeds int32. */
+int orc_complete_graph(int P, int *ptr, int *ranks) {
+    if (P <= 0 || !ptr || !ranks) return ORC_ERR_ARG;
+    if ((int64_t)P * P > INT32_MAX) return ORC_ERR_UNSUPPORTED;
+    for (int r = 0; r <= P; r++) ptr[r] = r * P;
+    for (int r = 0; r < P; r++)
+        for (int d = 0; d < P; d++) ranks[(int64_t)r * P + d] = d;
+    return ORC_OK;
 }

@@ -693,7 +693,151 @@ def check_w_adjoint(lib):
         assert np.array_equal(acc[~hit], old[~hit]), w.name
 
 
-ALL_CHECKS = [check_partitioned_bruteforce, check_locality_names_values_by_source_element, check_w_golden, check_w_bruteforce_random, check_w_reduces_to_v,
+# ------------------------------------------------------ derived collectives ----
+
+def _coll_problem(c):
+    """A golden collective case as the oracle's argument (graph, bases, buffers; bytes)."""
+    g = types.SimpleNamespace(name=c["name"], P=c["P"], ppn=c["ppn"], elem_size=c["elem_size"], dtype="bytes")
+    for k in ("in_ptr", "sources", "out_ptr", "dests"):
+        setattr(g, k, np.array(c[k], np.int32) if k in c else None)
+    g.send_base = np.array(c["send_base"], np.int64)
+    g.recv_base = np.array(c["recv_base"], np.int64)
+    g.sendbuf = np.array(c["send_values"], np.uint8)
+    g.recv_init = np.array(c["recv_init"], np.uint8)
+    g.sendbuf_bytes, g.recvbuf_bytes = len(g.sendbuf), len(g.recv_init)
+    return g
+
+
+def _coll_run(c, lib):
+    g = _coll_problem(c)
+    if c["kind"] == "alltoall":
+        return oracle.neighbor_alltoall(g, c["count"], g.sendbuf, g.recv_init, lib=lib)
+    if c["kind"] == "allgather":
+        return oracle.neighbor_allgather(g, c["count"], g.sendbuf, g.recv_init, lib=lib)
+    if c["kind"] == "allgatherv":
+        return oracle.neighbor_allgatherv(g, c["sendcount"], c["recvcounts"], c["rdispls"], g.sendbuf, g.recv_init,
+                                          lib=lib)
+    return oracle.alltoallv(g.P, g.ppn, c["sendcounts"], c["sdispls"], c["recvcounts"], c["rdispls"], g.send_base,
+                            g.recv_base, g.elem_size, g.sendbuf, g.recvbuf_bytes, g.recv_init, lib=lib)
+
+
+def check_collectives_golden(lib):
+    with open(os.path.join(GOLDEN, "collectives.json")) as f:
+        gold = json.load(f)
+    cases = {c["name"]: c for c in gold["cases"]}
+    for c in gold["cases"]:
+        got = _coll_run(c, lib)
+        assert np.array_equal(got, np.array(c["expected_recv"], np.uint8)), c["name"]
+    for e in gold["errors"]:
+        c = dict(cases[e["of"]], **e["change"]) if "of" in e else e
+        try:
+            _coll_run(c, lib)
+            code = 0
+        except oracle.OracleError as x:
+            code = x.code
+        assert code == e["expected_error"], (e["name"], code)
+
+
+def _listing_pairs(p):
+    """(in-edge i, receiver d, position of i in d's in-list, sender r, position in r's
+    out-list of the listing it pairs with): the t-th listing of r by d pairs with the t-th
+    listing of d by r, found by scanning the lists."""
+    out = []
+    for d in range(p.P):
+        seen = {}
+        for i in range(p.in_ptr[d], p.in_ptr[d + 1]):
+            r = int(p.sources[i])
+            t = seen.get(r, 0)
+            seen[r] = t + 1
+            js = [j for j in range(p.out_ptr[r + 1] - p.out_ptr[r]) if p.dests[p.out_ptr[r] + j] == d]
+            out.append((i, d, i - p.in_ptr[d], r, js[t]))
+    return out
+
+
+def _packed_layout(rng, sizes):
+    """Displacements placing blocks of the given sizes one after another in a random order."""
+    order = rng.permutation(len(sizes))
+    disp = np.zeros(len(sizes), np.int64)
+    acc = 0
+    for k in order:
+        disp[k] = acc
+        acc += sizes[k]
+    return disp, acc
+
+
+def check_collectives_bruteforce(lib):
+    """Every derived collective on random multigraphs equals its MPI definition, written out
+    element by element from the listing pairs."""
+    for seed in (3, 11, 19, 26):
+        p = pt.random_pattern(seed)
+        P, s = p.P, [1, 4, 8, 2][seed % 4]
+        rng = np.random.default_rng(seed)
+        deg_out, deg_in = np.diff(p.out_ptr), np.diff(p.in_ptr)
+        pairs = _listing_pairs(p)
+        for kind in ("alltoall", "allgather", "allgatherv"):
+            count = 1 + seed % 3
+            sendcount = rng.integers(0, 4, P)
+            region_send = {"alltoall": deg_out * count, "allgather": np.full(P, count), "allgatherv": sendcount}[kind]
+            rcnt = np.array([sendcount[p.sources[i]] if kind == "allgatherv" else count
+                             for i in range(len(p.sources))], np.int64)
+            rd = np.zeros(len(p.sources), np.int64)
+            region_recv = np.zeros(P, np.int64)
+            for d in range(P):
+                lo, hi = p.in_ptr[d], p.in_ptr[d + 1]
+                if kind == "allgatherv":
+                    rd[lo:hi], region_recv[d] = _packed_layout(rng, rcnt[lo:hi])
+                else:
+                    region_recv[d] = (hi - lo) * count
+            g = types.SimpleNamespace(name=f"{kind}{seed}", P=P, ppn=p.ppn, in_ptr=p.in_ptr, sources=p.sources,
+                                      out_ptr=p.out_ptr, dests=p.dests, elem_size=s, dtype="bytes")
+            g.send_base = np.concatenate([[0], np.cumsum(region_send)[:-1]]).astype(np.int64) * s
+            g.recv_base = np.concatenate([[0], np.cumsum(region_recv + 1)[:-1]]).astype(np.int64) * s
+            g.sendbuf_bytes = int(region_send.sum()) * s
+            g.recvbuf_bytes = int((region_recv + 1).sum()) * s
+            x = rng.integers(0, 256, g.sendbuf_bytes).astype(np.uint8)
+            init = rng.integers(0, 256, g.recvbuf_bytes).astype(np.uint8)
+            want = init.copy()
+            for i, d, k, r, j in pairs:
+                if kind == "alltoall":
+                    src, n, dst = g.send_base[r] + j * count * s, count * s, g.recv_base[d] + k * count * s
+                elif kind == "allgather":
+                    src, n, dst = g.send_base[r], count * s, g.recv_base[d] + k * count * s
+                else:
+                    src, n, dst = g.send_base[r], sendcount[r] * s, g.recv_base[d] + rd[i] * s
+                want[dst:dst + n] = x[src:src + n]
+            if kind == "alltoall":
+                got = oracle.neighbor_alltoall(g, count, x, init, lib=lib)
+            elif kind == "allgather":
+                got = oracle.neighbor_allgather(g, count, x, init, lib=lib)
+            else:
+                got = oracle.neighbor_allgatherv(g, sendcount, rcnt, rd, x, init, lib=lib)
+            assert np.array_equal(got, want), (kind, seed)
+    for P in (1, 3, 6):
+        rng = np.random.default_rng(100 + P)
+        s = 4
+        cnt = rng.integers(0, 4, (P, P))
+        sd = np.zeros((P, P), np.int64)
+        rd = np.zeros((P, P), np.int64)
+        region_send, region_recv = np.zeros(P, np.int64), np.zeros(P, np.int64)
+        for r in range(P):
+            sd[r], region_send[r] = _packed_layout(rng, cnt[r])
+        for d in range(P):
+            rd[d], region_recv[d] = _packed_layout(rng, cnt[:, d])
+        send_base = np.concatenate([[0], np.cumsum(region_send)[:-1]]).astype(np.int64) * s
+        recv_base = np.concatenate([[0], np.cumsum(region_recv)[:-1]]).astype(np.int64) * s
+        x = rng.integers(0, 256, int(region_send.sum()) * s).astype(np.uint8)
+        want = np.zeros(int(region_recv.sum()) * s, np.uint8)
+        for r in range(P):
+            for d in range(P):
+                n = cnt[r, d] * s
+                src, dst = send_base[r] + sd[r, d] * s, recv_base[d] + rd[d, r] * s
+                want[dst:dst + n] = x[src:src + n]
+        got = oracle.alltoallv(P, 2, cnt, sd, cnt.T, rd, send_base, recv_base, s, x, len(want), lib=lib)
+        assert np.array_equal(got, want), ("alltoallv", P)
+
+
+ALL_CHECKS = [check_collectives_golden, check_collectives_bruteforce,
+              check_partitioned_bruteforce, check_locality_names_values_by_source_element, check_w_golden, check_w_bruteforce_random, check_w_reduces_to_v,
               check_w_stencil_bruteforce, check_w_adjoint,
               check_golden_forward, check_golden_multigraph_truncate, check_golden_locality,
               check_golden_backward_order, check_bruteforce_stencil, check_bruteforce_spmv,

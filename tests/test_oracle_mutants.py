@@ -53,6 +53,14 @@ MUTANTS = [
      "sp[n] = part_of(npart, part_ptr, dst < pt->sendbuf_bytes ? dst : 0, s);"),
     ("partition_straddle_accepted", "return off + s <= ptr[p + 1] ? p : -1;", "return p;"),
     ("arrival_ignores_readiness", "if (!ready[sp[n]]) arrived[rp[n]] = 0;", "(void)0;"),
+    ("collective_receives_at_out_position", "int64_t k = i - g->in_ptr[d];  /* position",
+     "int64_t k = i - g->out_ptr[d];  /* position"),
+    ("alltoall_sends_from_zero", "int64_t disp = mode == 0 ? j * (int64_t)count : 0;", "int64_t disp = 0;"),
+    ("allgather_sends_from_position", "mode == 0 ? j * (int64_t)count : 0", "mode <= 1 ? j * (int64_t)count : 0"),
+    ("allgatherv_fixed_count", "sendcounts[e] = mode == 2 ? rank_count[r] : count;", "sendcounts[e] = count;"),
+    ("alltoall_overflow_unchecked", "if (disp > INT32_MAX) err = ORC_ERR_UNSUPPORTED;\n            sendcounts",
+     "if (0) err = ORC_ERR_UNSUPPORTED;\n            sendcounts"),
+    ("dense_graph_reversed", "ranks[(int64_t)r * P + d] = d;", "ranks[(int64_t)r * P + d] = P - 1 - d;"),
     ("dedup_by_gidx_only", "if (p->a != q->a) return p->a < q->a ? -1 : 1;\n    if (p->b != q->b) return p->b < q->b ? -1 : 1;\n    if (p->gidx",
      "if (0) return 0;\n    if (0) return 0;\n    if (p->gidx"),
 ]
