@@ -35,7 +35,9 @@
  *   - Handles are opaque and owned by the library; *_free releases them and sets the
  *     handle to NULL.
  *   - `stream` is a cudaStream_t passed as void* (NULL = the legacy default stream).
- *   - Nothing here allocates host-pinned memory or changes device settings.
+ *   - Nothing here changes device settings.  The only host-pinned memory the library
+ *     allocates is one 64-byte status word per request (mapped, written by its kernels
+ *     only when a bounded device wait gives up).
  */
 #ifndef GBX_H
 #define GBX_H
@@ -70,6 +72,12 @@ extern "C" {
 #define GBX_ERR_STATE       15   /* call not allowed in the request's current state (partitioned:
                                     pready before start or twice in one epoch, a wait or an
                                     arrival wait before the partitions it needs were marked) */
+#define GBX_ERR_DEVICE_WAIT 16   /* the exchange finished on the GPU but incomplete: a bounded
+                                    wait of one of its kernels on its own copies gave up (or a
+                                    move piece failed the kernel's own check); the receive
+                                    buffer is partly written.  Reported once by gbx_wait /
+                                    gbx_test / gbx_waitall; the request is then inactive and
+                                    may be started again */
 
 /* payload types: only the backward (which adds) needs to know them */
 #define GBX_BYTES 0
@@ -114,7 +122,8 @@ typedef struct {
     int64_t device_bytes;   /* device memory the request owns                         */
     int64_t copy_forms;     /* bit f set when some copy runs in form f: 0 segments,
                                1 gather, 3 two-index, 5/7 pipelined 1/3, 8 bulk pieces,
-                               9 source windows scattered (fixed at init by the tuner) */
+                               9 source windows scattered, 10/11 stream forms of 1/3
+                               (fixed at init by the tuner) */
 } gbx_request_info_t;
 
 const char *gbx_error_string(int code);
@@ -202,12 +211,25 @@ int gbx_graph_free(gbx_graph_t *graph);
  *                          In a backward the same key offers (1) or forces (2) the scatter
  *                          form of the single-term rows: source windows read by the
  *                          bulk-copy engine, scattered to their destinations by the threads
+ *       stream=0|1|2       offer the stream form of the flat copies (the per-element index
+ *                          arrays copied into shared memory ahead of the payload loads by the
+ *                          bulk-copy engine) to the autotuner (default 1; 0 leaves it out, 2
+ *                          forces it where it applies: index arrays the library built, vectors
+ *                          of at least 4 bytes)
+ *       form=F             the autotuner times only copy form F (a bit number of copy_forms
+ *                          below) in every copy that offers it, the others as usual (default
+ *                          -1); for reproducing one program shape, e.g. under a profiler
  *       max_ctas=N         at most N thread blocks in any launch (default 0: no cap), leaving
  *                          the rest of the GPU to other requests' kernels on other streams;
  *                          every move kernel covers its work with any grid
  *       check_dup=0|1      locality form: at init, compare the bytes of every element that
  *                          shares a (node pair, global index) value with the value's
  *                          representative in the send buffer as bound then (default 0)
+ *       wait_limit=N       polls (N >= 0, default 4194304) of each main wait of the kernels
+ *                          that wait on their own asynchronous copies (the bulk-copy and
+ *                          scatter forms) before the wait gives up and the start reports
+ *                          GBX_ERR_DEVICE_WAIT; waits that drain copies already in flight
+ *                          keep the default.  In a batch the first request's limit applies
  * Errors: GBX_ERR_ARG, _TRUNCATE, _INDEX, _GIDX, _OVERLAP (receive blocks must not
  * overlap), _DUP (with check_dup=1), _NOMEM, _CUDA.  Validation and map building run as device kernels; the
  * call blocks on `stream` to read their status.  The autotuner's trial launches write
@@ -257,10 +279,11 @@ int gbx_neighbor_allgatherv_init(const void *sendbuf, int64_t sendbuf_bytes, con
                                  int64_t elem_size, int dtype, gbx_graph_t graph,
                                  const char *info, void *stream, gbx_request_t *request);
 
-/* Reads and clears the device status word of the move kernels: 1 when a bounded wait of
- * the bulk or scatter kernel gave up since the last call (the launch then left its pieces
- * unfinished), 2 when one of their pieces failed its in-kernel check and was skipped, else
- * 0.  No counterpart in the paper. */
+/* Reads and clears the process-wide status word of the move kernels, the aggregate of every
+ * request's own word: 1 when a bounded wait of the bulk or scatter kernel gave up since the
+ * last call (the launch then left its pieces unfinished), 2 when one of their pieces failed
+ * its in-kernel check and was skipped, else 0.  Each request also has its own word, which
+ * gbx_wait / gbx_test read (GBX_ERR_DEVICE_WAIT).  No counterpart in the paper. */
 int gbx_device_status(int *status);
 
 /* Persistent partitioned exchange (section 2.3: partitioned communication lets marked
@@ -397,14 +420,22 @@ int gbx_start(gbx_request_t request);
 
 /* MPIX_Wait (section 2.2, Listing 4): blocks the host until the started exchange has
  * finished on the GPU, polling with a limit of timeout_ms; returns GBX_ERR_TIMEOUT
- * (request still active) when the limit passes.  An inactive request returns at once. */
+ * (request still active) when the limit passes.  An inactive request returns at once.
+ * When the exchange finished but one of its kernels gave up a bounded wait (see
+ * GBX_ERR_DEVICE_WAIT and info wait_limit), returns GBX_ERR_DEVICE_WAIT and clears the
+ * request's status word; the request is inactive either way.  On an inactive request it
+ * reports (and clears) a status word left set by an exchange completed with
+ * gbx_wait_stream, once that exchange's kernels have finished. */
 int gbx_wait(gbx_request_t request);
 
-/* Non-blocking completion check: *flag = 1 and the request becomes inactive if done. */
+/* Non-blocking completion check: *flag = 1 and the request becomes inactive if done; the
+ * return code reports a device wait that gave up as gbx_wait does. */
 int gbx_test(gbx_request_t request, int *flag);
 
 /* Completes a started request without blocking the host: `stream` waits for it on the
- * GPU and the request becomes inactive (stream-ordered use, e.g. autograd). */
+ * GPU and the request becomes inactive (stream-ordered use, e.g. autograd).  It cannot
+ * read the request's status word (the kernels have not finished yet): a device wait that
+ * gave up stays recorded and is reported by the request's next gbx_wait or gbx_test. */
 int gbx_wait_stream(gbx_request_t request, void *stream);
 
 /* Starts `count` inactive requests as one batch: all their move phases run as fused
@@ -456,21 +487,27 @@ int gbx_request_get_info(gbx_request_t request, gbx_request_info_t *info);
  * callbacks that are not allowed to touch the allocator.  It does no persistent setup
  * and returns no handle: every call matches, validates and moves in one go.
  *   Meaning: that of gbx_neighbor_alltoallv_init with send_idx, the slot CSRs and the
- *   global indices all NULL (a user-packed send buffer, the plain MPI call of
- *   section 2.2, Listing 3): for every in-edge i of rank d from r, paired under the
- *   multigraph rule with out-edge e of r,
+ *   global indices all NULL (a user-packed send buffer): for every in-edge i of rank d
+ *   from r, paired under the multigraph rule with out-edge e of r,
  *     recv bytes [recv_base[d] + rdispls[i]*s, +recvcounts[i]*s) =
  *     send bytes [send_base[r] + sdispls[e]*s, +sendcounts[e]*s).
- *   Arguments: as gbx_dist_graph_create_adjacent and gbx_neighbor_alltoallv_init; all
- *   arrays and both buffers are device memory owned by the caller.
+ *   Arguments: as gbx_dist_graph_create_adjacent and gbx_neighbor_alltoallv_init.  The
+ *   index and count arrays (in_ptr, sources, out_ptr, destinations, send_base,
+ *   sendcounts, sdispls, recv_base, recvcounts, rdispls) are device memory; sendbuf and
+ *   recvbuf are device memory or pinned host memory the GPU can address (read and written
+ *   in place); a pageable host pointer gives GBX_ERR_ARG before any device work.  All of
+ *   them stay owned by the caller.
  *   Scratch: the per-edge tables live in one file-scope device array sized for
- *   GBX_NOALLOC_MAX_EDGES edges (about 6 MB), which every GPU that loads the library
- *   holds until the process exits.  Edge counts above the limit return GBX_ERR_LIMIT
- *   before any device work.  The first call on a device looks the array's device address
- *   up (cudaGetSymbolAddress) with that device current; make that first call before any
- *   stream capture.  All calls on a device share the array and a call overwrites what the
- *   previous one left there, so calls that may overlap on the GPU (different streams,
- *   other host threads) race and must be serialised by the caller.
+ *   GBX_NOALLOC_MAX_EDGES edges (about 6 MB).  Edge counts above the limit return
+ *   GBX_ERR_LIMIT before any device work.  CUDA loads a library's device code lazily by
+ *   default, so the first call on a device loads the part of the library that holds the
+ *   array, which reserves its 6 MB of device memory, and looks the array's device address
+ *   up (cudaGetSymbolAddress) with that device current; make that first call while the
+ *   device still has that memory free and before any stream capture.  From then on the
+ *   device holds the array until the process exits and no call allocates anything.  All
+ *   calls on a device share the array and a call overwrites what the previous one left
+ *   there, so calls that may overlap on the GPU (different streams, other host threads)
+ *   race and must be serialised by the caller.
  *   Errors: GBX_ERR_ARG, _RANK, _TRUNCATE, _INDEX, _LIMIT, _CUDA as in the persistent
  *   path; overlapping receive blocks are not detected (MPI makes them erroneous).
  *   The call enqueues its kernels on `stream` and blocks until they finish, then returns

@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(_HERE, "libgbx.so")
 
 SUCCESS, ERR_ARG, ERR_RANK, ERR_TRUNCATE, ERR_INDEX, ERR_DUP, ERR_GIDX = 0, 1, 2, 3, 4, 5, 6
 ERR_ACTIVE, ERR_TIMEOUT, ERR_CUDA, ERR_NOMEM, ERR_UNSUPPORTED, ERR_INTERNAL, ERR_OVERLAP = 7, 8, 9, 10, 11, 12, 13
-ERR_LIMIT, ERR_STATE = 14, 15
+ERR_LIMIT, ERR_STATE, ERR_DEVICE_WAIT = 14, 15, 16
 BYTES, F32, F64 = 0, 1, 2
 ALG_STANDARD, ALG_LOCALITY = 0, 1
 DTYPE_CODES = {"bytes": BYTES, "f32": F32, "f64": F64}
@@ -220,7 +220,11 @@ class Request:
 
     def bind(self, src=None, dst=None):
         _check(lib().gbx_request_bind(self.handle, _buf(src), _buf(dst)), "bind")
-        self._keep += [t for t in (src, dst) if t is not None]
+        # the request now uses these buffers: keep them (and only the latest ones) alive
+        if src is not None:
+            self._bound_src = src
+        if dst is not None:
+            self._bound_dst = dst
 
     def start_host(self, host_src, host_dst):
         """One exchange on host tensors (copied in, exchanged, copied out)."""

@@ -39,6 +39,7 @@ extern "C" const char *gbx_error_string(int code) {
         case GBX_ERR_INTERNAL: return "internal error: a generated move program failed validation";
         case GBX_ERR_LIMIT: return "size beyond the fixed scratch of the allocation-free exchange";
         case GBX_ERR_STATE: return "call not allowed in the request's current state";
+        case GBX_ERR_DEVICE_WAIT: return "a bounded device wait gave up: the exchange is incomplete";
         default: return "unknown error";
     }
 }
@@ -56,7 +57,7 @@ struct Opts {
     int algorithm_auto = 0;
     int graph = 1, autotune = 1, vec = 0, block = 0, timeout_ms = 60000, min_run = 4, piece = 0, flat = -1;
     int split = 1, split_order = 2;   // 2: source order where the scatter form can run, else dest
-    int check_dup = 0, bulk = 1, max_ctas = 0;
+    int check_dup = 0, bulk = 1, max_ctas = 0, wait_limit = GBX_WAIT_LIMIT, stream = 1, form = -1;
     bool ok = true;
 };
 
@@ -92,12 +93,16 @@ static Opts parse_info(const char *info) {
         else if (k == "check_dup") o.check_dup = atoi(v.c_str()) != 0;
         else if (k == "bulk") o.bulk = atoi(v.c_str());
         else if (k == "max_ctas") o.max_ctas = atoi(v.c_str());
+        else if (k == "wait_limit") o.wait_limit = atoi(v.c_str());
+        else if (k == "stream") o.stream = atoi(v.c_str());
+        else if (k == "form") o.form = atoi(v.c_str());
         else o.ok = false;
     }
     if (o.vec && !(o.vec == 1 || o.vec == 2 || o.vec == 4 || o.vec == 8 || o.vec == 16)) o.ok = false;
     if (o.block && !(o.block == 128 || o.block == 256 || o.block == 512 || o.block == 1024)) o.ok = false;
     if (o.timeout_ms <= 0 || o.min_run < 0 || o.piece < 0 || o.split_order < 0) o.ok = false;
-    if (o.bulk < 0 || o.bulk > 2 || o.max_ctas < 0) o.ok = false;
+    if (o.bulk < 0 || o.bulk > 2 || o.max_ctas < 0 || o.wait_limit < 0 || o.stream < 0 || o.stream > 2) o.ok = false;
+    if (o.form < -1 || o.form > 11) o.ok = false;
     return o;
 }
 
@@ -126,6 +131,7 @@ extern "C" int gbx_dist_graph_create_adjacent(gbx_comm_t comm, int64_t n_in_edge
                                               const int *out_ptr, const int *destinations, const int *destweights,
                                               const char *info, int reorder, void *stream, gbx_graph_t *graph) {
     (void)sourceweights; (void)destweights; (void)info; (void)reorder;
+    GbxRange range("gbx.setup.graph");
     if (!graph) return GBX_ERR_ARG;
     *graph = nullptr;
     if (!comm || n_in_edges < 0 || n_out_edges < 0 || !in_ptr || !out_ptr) return GBX_ERR_ARG;
@@ -185,6 +191,20 @@ static int vec_of_align(uint64_t align) {
     return v;
 }
 
+// The stream forms read the flat form's index arrays with the bulk-copy engine, in 16-byte
+// pieces that may run up to 3 entries past the end: the arrays must be 16-byte aligned and
+// padded by 4 entries (every flat index array the library builds is), and the vector width
+// at least 4 bytes.
+static int stream_ok_for(const gbx_request_s *req, const int32_t *g, const int32_t *gd, int max_vec) {
+    static int prepared = 0;
+    if (!req->allow_stream || max_vec < 4 || ((uintptr_t)g & 15) || ((uintptr_t)gd & 15)) return 0;
+    if (!prepared) {
+        if (gbx_stream_prepare() != GBX_SUCCESS) return 0;
+        prepared = 1;
+    }
+    return 1;
+}
+
 int gbx_make_copy_op(gbx_request_s *req, int level, const char *src, int src_role, char *dst, int dst_role,
                      const Seg *segs, int64_t nseg, const int32_t *idx, int64_t idx_len, int64_t nelem,
                      int64_t algo_bytes) {
@@ -223,6 +243,7 @@ int gbx_make_copy_op(gbx_request_s *req, int level, const char *src, int src_rol
     CopyDesc &d = op.cd;
     d.src = src; d.dst = dst; d.segs = segs; d.idx = idx; d.nseg = nseg; d.nelem = nelem;
     d.elem_size = req->elem_size; d.src_role = src_role; d.dst_role = dst_role;
+    d.status = req->status_dev; d.wait_limit = req->wait_limit;
     const int64_t max_tiles = ceil_div(nelem * (req->elem_size / op.min_vec), GBX_TILE);
     GBX_TRY(req->mem.get(&op.d_tile_seg, max_tiles + 1));
     GBX_TRY(req->mem.get(&op.d_tile_e0, max_tiles + 1));
@@ -236,6 +257,7 @@ int gbx_make_copy_op(gbx_request_s *req, int level, const char *src, int src_rol
         d.flat_idx = op.d_flat_idx;
         d.dst_flat0 = op.flat_dst0;
         op.algo_bytes_flat = 2 * nelem * req->elem_size + 4 * nelem;
+        op.stream_ok = op.flat_ok && stream_ok_for(req, op.d_flat_idx, nullptr, op.max_vec);
     }
     if (req->allow_bulk && !host_mem(src) && !host_mem(dst)) {
         GBX_TRY(gbx_make_bulk(req, segs, nseg, nelem, &op.d_bulk, &op.nbulk, &op.bulk_ok));
@@ -271,6 +293,8 @@ int gbx_make_flat_op(gbx_request_s *req, int level, const char *src, int src_rol
     d.src = src; d.dst = dst; d.segs = nullptr; d.idx = nullptr; d.nseg = 0; d.nelem = nelem;
     d.elem_size = req->elem_size; d.src_role = src_role; d.dst_role = dst_role;
     d.flat = 1; d.flat_idx = g; d.dst_flat0 = dst0; d.src2 = src2; d.src2_role = src2_role;
+    d.status = req->status_dev; d.wait_limit = req->wait_limit;
+    op.stream_ok = stream_ok_for(req, g, nullptr, op.max_vec);
     const int64_t max_tiles = ceil_div(nelem * (req->elem_size / op.min_vec), GBX_TILE);
     GBX_TRY(req->mem.get(&op.d_tile_e0, max_tiles + 1));
     d.tile_e0 = op.d_tile_e0;
@@ -294,6 +318,7 @@ int gbx_make_flat2_op(gbx_request_s *req, int level, const char *src, int src_ro
     HostOp &op = req->ops.back();
     op.cd.flat = 3;
     op.cd.flat_didx = gd;
+    op.stream_ok = op.stream_ok && stream_ok_for(req, gs, gd, op.max_vec);
     op.algo_bytes = op.algo_bytes_flat = 2 * nelem * req->elem_size + 8 * nelem;
     if (req->allow_bulk && pairs_in_source_order(req) && nelem > 0 && !host_mem(src) && !host_mem(dst)) {
         GBX_TRY(gbx_make_scatter(req, gs, nelem, &op.d_scat, &op.nscat, &op.scat_ok));
@@ -375,6 +400,8 @@ static int upload_desc(gbx_request_s *req, HostOp &op) {
 // Sets the op's vector width: chunk geometry, tiles, tile->segment table, descriptor.
 static int set_vec(gbx_request_s *req, HostOp &op, int vec) {
     const int64_t s = req->elem_size;
+    // the tile tables were allocated for min_vec; a narrower vector would need more tiles
+    if (vec < op.min_vec || vec > op.max_vec) return GBX_ERR_INTERNAL;
     const int cpe = (int)(s / vec);
     int shift = -1;
     if ((cpe & (cpe - 1)) == 0) { shift = 0; while ((1 << shift) < cpe) shift++; }
@@ -415,6 +442,7 @@ static int op_vec(const HostOp &op) { return op.kind == 0 ? op.cd.vec : op.fd.ve
 // grid covers them), which leaves room for other requests' kernels on other streams.
 static int grid_for(int kind, int dtype, int vec, int flat, int block, int persistent, int64_t tiles,
                     int max_ctas) {
+    if (kind == 0 && flat >= 10) persistent = 1;   // the stream kernel's ring wants resident CTAs
     int64_t g = persistent ? (int64_t)gbx_num_sms() * gbx_occupancy(kind, dtype, vec, block, flat)
                            : std::min<int64_t>(tiles, 1ll << 30);
     if (max_ctas > 0) g = std::min<int64_t>(g, max_ctas);
@@ -494,13 +522,15 @@ static int tune_op(gbx_request_s *req, HostOp &op) {
     key.nseg = op.kind == 0 ? op.cd.nseg : 0;
     key.nterms = op.kind == 1 ? op.fd.nchunks : 0;
     key.flat_ok = op.kind == 0 ? op.flat_ok + 2 * op.flat_only + 4 * ((op.cd.flat & 3) == 3) + 8 * op.bulk_ok +
-                                     16 * op.scat_ok + 32 * (req->allow_bulk == 2)   // forced forms tune apart
+                                     16 * op.scat_ok + 32 * (req->allow_bulk == 2) + 64 * op.stream_ok +
+                                     128 * (req->allow_stream == 2) + 256 * (req->forced_form + 1)   // forced forms tune apart
                                : 0;
     int blocks[4] = {128, 256, 512, 1024};
     if (!req->autotune || req->forced_block) {
         op.block = req->forced_block ? req->forced_block : 256;
         op.persistent = 1;
         if (op.kind == 0 && !op.flat_only) op.cd.flat = op.flat_ok && req->forced_flat != 0;
+        if (op.kind == 0 && op.stream_ok && req->allow_stream == 2) op.cd.flat = (op.cd.flat & 3) == 3 ? 11 : 10;
         if (op.kind == 0 && op.bulk_ok && req->allow_bulk == 2) op.cd.flat = 8;
         if (op.kind == 0 && op.scat_ok && req->allow_bulk == 2) op.cd.flat = 9;
         set_form_bytes(op);
@@ -535,17 +565,25 @@ static int tune_op(gbx_request_s *req, HostOp &op) {
     else if (op.flat_ok && req->forced_flat < 0) { forms.push_back(0); forms.push_back(1); forms.push_back(5); }
     else if (op.flat_ok && req->forced_flat > 0) { forms.push_back(1); forms.push_back(5); }
     else forms.push_back(0);
+    if (op.kind == 0 && op.stream_ok && (op.flat_only || (op.flat_ok && req->forced_flat != 0)))
+        forms.push_back((op.cd.flat & 3) == 3 ? 11 : 10);
     if (op.kind == 0 && op.bulk_ok && req->forced_flat != 1 && op.max_vec == 16) forms.push_back(8);
     if (op.kind == 0 && op.scat_ok && op.max_vec == 16) forms.push_back(9);
+    if (op.kind == 0 && op.stream_ok && req->allow_stream == 2) forms.assign(1, (op.cd.flat & 3) == 3 ? 11 : 10);
     if (op.kind == 0 && op.bulk_ok && req->allow_bulk == 2) forms.assign(1, 8);   // forced where it applies
     if (op.kind == 0 && op.scat_ok && req->allow_bulk == 2) forms.assign(1, 9);
+    if (op.kind == 0 && req->forced_form >= 0 &&   // one form, where the op offers it
+        std::find(forms.begin(), forms.end(), req->forced_form) != forms.end())
+        forms.assign(1, req->forced_form);
     for (int form : forms) {
         if (op.kind == 0) op.cd.flat = form;
-        const bool pipe = form >= 4 && form < 8, bulk = form >= 8;
-        for (int vec = op.max_vec; vec >= (bulk ? 16 : op.min_vec); vec >>= 1) {
+        const bool pipe = form >= 4 && form < 8, bulk = form == 8 || form == 9, strm = form >= 10;
+        // (the op's tile tables are sized for min_vec: no width below it)
+        for (int vec = op.max_vec; vec >= (bulk ? 16 : strm ? std::max(4, op.min_vec) : op.min_vec); vec >>= 1) {
             GBX_TRY(set_vec(req, op, vec));
-            for (int bi = pipe ? 2 : form == 8 ? 3 : 0; bi < 4; bi++)
-                for (int pers = 1; pers >= (pipe ? 1 : 0); pers--) {
+            // stream forms: two shapes (block 256, 512), persistent grid only
+            for (int bi = pipe ? 2 : form == 8 ? 3 : strm ? 1 : 0; bi < (strm ? 3 : 4); bi++)
+                for (int pers = 1; pers >= (pipe || strm ? 1 : 0); pers--) {
                     float ms = 0;
                     GBX_TRY(time_op(req, op, blocks[bi], pers, 3, &ms));
                     if (ms < best.ms) best = {vec, blocks[bi], pers, form, ms};
@@ -577,26 +615,32 @@ static int tune_launch(LevelLaunch &L, cudaStream_t st) {
     GBX_CUDA_TRY(cudaEventCreate(&b));
     const int blocks[4] = {128, 256, 512, 1024};
     float best = 1e30f;
-    int bb = L.block, bg = L.grid;
+    int bb = L.block, bg = L.grid, bf = L.flat;
     cudaError_t e = cudaSuccess;
-    for (int bi = 0; bi < 4 && e == cudaSuccess; bi++)
-        for (int pers = 1; pers >= 0 && e == cudaSuccess; pers--) {
-            const int blk = gbx_effective_block(L.vec, blocks[bi]);
-            const int grid = grid_for(L.kind, L.dtype, L.vec, L.flat, blk, pers, L.total_tiles, L.max_ctas);
-            e = launch_list(L.kind, L.dtype, L.vec, L.flat, L.d_ops, L.d_prefix, L.nops, L.total_tiles, blk, grid, st);
-            float t = 1e30f;
-            for (int r = 0; r < 3 && e == cudaSuccess; r++) {
-                cudaEventRecord(a, st);
-                e = launch_list(L.kind, L.dtype, L.vec, L.flat, L.d_ops, L.d_prefix, L.nops, L.total_tiles, blk,
-                                grid, st);
-                cudaEventRecord(b, st);
-                if (e == cudaSuccess) e = cudaEventSynchronize(b);
-                float x = 0;
-                if (e == cudaSuccess) cudaEventElapsedTime(&x, a, b);
-                t = std::min(t, x);
+    // a stream-form launch is also timed in the plain flat form (same tiles, same bytes)
+    const int nforms = (L.flat == 10 || L.flat == 11) ? 2 : 1;
+    for (int fi = 0; fi < nforms && e == cudaSuccess; fi++) {
+        const int fl = fi == 0 ? L.flat : (L.flat == 10 ? 1 : 3);
+        const bool strm = fl >= 10;
+        for (int bi = strm ? 1 : 0; bi < (strm ? 3 : 4) && e == cudaSuccess; bi++)
+            for (int pers = 1; pers >= (strm ? 1 : 0) && e == cudaSuccess; pers--) {
+                const int blk = gbx_effective_block(L.vec, blocks[bi]);
+                const int grid = grid_for(L.kind, L.dtype, L.vec, fl, blk, pers, L.total_tiles, L.max_ctas);
+                e = launch_list(L.kind, L.dtype, L.vec, fl, L.d_ops, L.d_prefix, L.nops, L.total_tiles, blk, grid, st);
+                float t = 1e30f;
+                for (int r = 0; r < 3 && e == cudaSuccess; r++) {
+                    cudaEventRecord(a, st);
+                    e = launch_list(L.kind, L.dtype, L.vec, fl, L.d_ops, L.d_prefix, L.nops, L.total_tiles, blk,
+                                    grid, st);
+                    cudaEventRecord(b, st);
+                    if (e == cudaSuccess) e = cudaEventSynchronize(b);
+                    float x = 0;
+                    if (e == cudaSuccess) cudaEventElapsedTime(&x, a, b);
+                    t = std::min(t, x);
+                }
+                if (t < best) { best = t; bb = blk; bg = grid; bf = fl; }
             }
-            if (t < best) { best = t; bb = blk; bg = grid; }
-        }
+    }
     cudaEventDestroy(a);
     cudaEventDestroy(b);
     if (e != cudaSuccess) {
@@ -605,11 +649,33 @@ static int tune_launch(LevelLaunch &L, cudaStream_t st) {
     }
     L.block = bb;
     L.grid = bg;
+    L.flat = bf;
     return GBX_SUCCESS;
 }
 
+// NVTX name of a launch: what = 0 standard forward, 1 locality forward (levels = its three
+// steps), 2 backward, 3 batch.
+static const char *phase_name(int what, int level, int kind) {
+    static const char *const fwd_loc[3] = {"gbx.locality.step1_gather", "gbx.locality.step2_node_pairs",
+                                           "gbx.locality.step3_redistribute"};
+    static const char *const bwd[2][3] = {{"gbx.backward.level0.copy", "gbx.backward.level1.copy",
+                                           "gbx.backward.level2.copy"},
+                                          {"gbx.backward.level0.fold", "gbx.backward.level1.fold",
+                                           "gbx.backward.level2.fold"}};
+    static const char *const bat[2][3] = {{"gbx.batch.level0.copy", "gbx.batch.level1.copy", "gbx.batch.level2.copy"},
+                                          {"gbx.batch.level0.fold", "gbx.batch.level1.fold", "gbx.batch.level2.fold"}};
+    const int lv = level < 0 ? 0 : level > 2 ? 2 : level, k = kind ? 1 : 0;
+    switch (what) {
+        case 0: return "gbx.standard.move";
+        case 1: return fwd_loc[lv];
+        case 2: return bwd[k][lv];
+        default: return bat[k][lv];
+    }
+}
+
 static int build_levels(DevPool &mem, const std::vector<HostOp *> &ops, const std::vector<int> &dtypes,
-                        std::vector<LevelLaunch> &out, int batch, cudaStream_t st, int tune = 0, int max_ctas = 0) {
+                        std::vector<LevelLaunch> &out, int batch, cudaStream_t st, int tune = 0, int max_ctas = 0,
+                        int what = 3) {
     int nlev = 0;
     for (HostOp *op : ops) nlev = std::max(nlev, op->level + 1);
     for (int lv = 0; lv < nlev; lv++)
@@ -623,8 +689,13 @@ static int build_levels(DevPool &mem, const std::vector<HostOp *> &ops, const st
                 // and (payload type, vector width) for folds; a batch fuses all patterns of a
                 // class, with every copy that has the flat form in one flat launch whatever form
                 // it was tuned to alone (fewer, larger launches)
-                const int form = !batch || op_flat(*op) >= 8 ? op_flat(*op)   // bulk / scatter ops pool only with their own kind
-                                        : (op->flat_ok ? ((op_flat(*op) & 3) == 3 ? 3 : 1) : 0);
+                // bulk / scatter ops pool only with their own kind (their tiles are pieces); every
+                // other flat-capable op joins the stream-form launch when all its index arrays allow
+                // it, else the plain flat launch
+                const int f0 = op_flat(*op);
+                const bool strm = op->stream_ok && op_vec(*op) >= 4;
+                const int form = !batch || f0 == 8 || f0 == 9 ? f0
+                               : op->flat_ok ? ((f0 & 3) == 3 ? (strm ? 11 : 3) : (strm ? 10 : 1)) : 0;
                 std::pair<int, int> k = kind ? std::make_pair(dtypes[i], op_vec(*op))
                                              : std::make_pair(form, op_vec(*op));
                 size_t g = 0;
@@ -658,6 +729,7 @@ static int build_levels(DevPool &mem, const std::vector<HostOp *> &ops, const st
                     if (op_tiles(*ops[i]) > op_tiles(*big)) big = ops[i];
                 }
                 L.total_tiles = pre.back();
+                L.phase = phase_name(batch ? 3 : what, lv, kind);
                 // the launch takes the tuned shape of its largest op
                 L.block = gbx_effective_block(L.vec, big->block);
                 L.max_ctas = max_ctas;
@@ -680,6 +752,7 @@ static int build_levels(DevPool &mem, const std::vector<HostOp *> &ops, const st
 
 static cudaError_t enqueue_levels(const std::vector<LevelLaunch> &levels, cudaStream_t st) {
     for (const LevelLaunch &L : levels) {
+        GbxRange r(L.phase);
         cudaError_t e = launch_list(L.kind, L.dtype, L.vec, L.flat, L.d_ops, L.d_prefix, L.nops, L.total_tiles,
                                     L.block, L.grid, st);
         if (e != cudaSuccess) return e;
@@ -734,12 +807,20 @@ static void fill_info(gbx_request_s *req) {
 }
 
 static int finalize(gbx_request_s *req) {
-    GBX_TRY(gbx_validate_program(req, req->agg ? 2 * req->U * req->elem_size : 0));
-    for (HostOp &op : req->ops) GBX_TRY(tune_op(req, op));
+    {
+        GbxRange r("gbx.setup.validate");
+        GBX_TRY(gbx_validate_program(req, req->agg ? 2 * req->U * req->elem_size : 0));
+    }
+    {
+        GbxRange r("gbx.setup.tune");
+        for (HostOp &op : req->ops) GBX_TRY(tune_op(req, op));
+    }
+    GbxRange r("gbx.setup.capture");
     std::vector<HostOp *> ptrs;
     std::vector<int> dts;
     for (HostOp &op : req->ops) { ptrs.push_back(&op); dts.push_back(req->dtype); }
-    GBX_TRY(build_levels(req->mem, ptrs, dts, req->launches, 0, req->stream, 0, req->max_ctas));
+    const int what = req->kind == 1 ? 2 : req->algorithm == GBX_ALG_LOCALITY ? 1 : 0;
+    GBX_TRY(build_levels(req->mem, ptrs, dts, req->launches, 0, req->stream, 0, req->max_ctas, what));
     if (req->use_graph && !req->launches.empty()) GBX_TRY(capture(req->launches, &req->exec));
     fill_info(req);
     return GBX_SUCCESS;
@@ -784,6 +865,7 @@ static void destroy_request(gbx_request_s *req) {
         if (s) cudaStreamDestroy(s);
     if (req->exec) cudaGraphExecDestroy(req->exec);
     if (req->done) cudaEventDestroy(req->done);
+    if (req->status_host) cudaFreeHost(req->status_host);
     gbx_graph_s *g = req->owned_graph;
     delete req;
     if (g) gbx_graph_free(&g);
@@ -808,9 +890,24 @@ static gbx_request_s *new_request(const Opts &o, void *stream) {
     req->check_dup = o.check_dup;
     req->allow_bulk = o.bulk;
     req->max_ctas = o.max_ctas;
+    req->wait_limit = o.wait_limit;
+    req->allow_stream = o.stream;
+    req->forced_form = o.form;
     if (cudaEventCreateWithFlags(&req->done, cudaEventDisableTiming) != cudaSuccess) {
         cudaGetLastError();
         req->done = nullptr;
+    }
+    // the status word (a failed allocation leaves the request unusable: done = null)
+    void *h = nullptr, *d = nullptr;
+    if (cudaHostAlloc(&h, 64, cudaHostAllocMapped) != cudaSuccess || cudaHostGetDevicePointer(&d, h, 0) != cudaSuccess) {
+        cudaGetLastError();
+        if (h) cudaFreeHost(h);
+        if (req->done) cudaEventDestroy(req->done);
+        req->done = nullptr;
+    } else {
+        memset(h, 0, 64);
+        req->status_host = (int *)h;
+        req->status_dev = (int *)d;
     }
     return req;
 }
@@ -857,6 +954,7 @@ extern "C" int gbx_neighbor_alltoallv_init(const void *sendbuf, int64_t sendbuf_
     if (!o.ok) return GBX_ERR_ARG;
 
     auto build = [&](int locality, gbx_request_s **out) -> int {
+        GbxRange range(locality ? "gbx.setup.forward_locality" : "gbx.setup.forward_standard");
         gbx_request_s *req = new_request(o, stream);
         if (!req->done) { destroy_request(req); return GBX_ERR_CUDA; }
         req->kind = 0;
@@ -910,6 +1008,7 @@ extern "C" int gbx_neighbor_alltoallw_init(const void *sendbuf, int64_t sendbuf_
     Opts o = parse_info(info);
     if (!o.ok) return GBX_ERR_ARG;
     if (o.algorithm != GBX_ALG_STANDARD || o.algorithm_auto) return GBX_ERR_UNSUPPORTED;
+    GbxRange range("gbx.setup.alltoallw");
     gbx_request_s *req = new_request(o, stream);
     if (!req->done) { destroy_request(req); return GBX_ERR_CUDA; }
     req->kind = 0;
@@ -946,6 +1045,7 @@ extern "C" int gbx_partitioned_init(gbx_request_t forward, int npart, const int6
     GBX_TRY(check_part_ptr(nrpart, rpart_ptr, forward->dst_bytes));
     Opts o = parse_info(info);
     if (!o.ok) return GBX_ERR_ARG;
+    GbxRange range("gbx.setup.partitioned");
     gbx_request_s *req = new_request(o, stream);
     if (!req->done) { destroy_request(req); return GBX_ERR_CUDA; }
     req->kind = 2;
@@ -1018,6 +1118,7 @@ extern "C" int gbx_partitioned_init(gbx_request_t forward, int npart, const int6
 
 extern "C" int gbx_pready(gbx_request_t req, int p, void *stream) {
     if (!req || req->kind != 2 || p < 0 || p >= req->npart) return GBX_ERR_ARG;
+    GbxRange range("gbx.pready");
     if (!req->active || req->part_ready[p]) return GBX_ERR_STATE;
     cudaStream_t st = stream ? (cudaStream_t)stream : req->stream;
     gbx_request_s *c = req->parts[p];
@@ -1076,6 +1177,7 @@ extern "C" int gbx_backward_init(gbx_request_t forward, const void *grad_recv, v
     GBX_TRY(gbx_check_data_buf(grad_send, forward->src_bytes));
     Opts o = parse_info(info);
     if (!o.ok) return GBX_ERR_ARG;
+    GbxRange range("gbx.setup.backward");
     gbx_request_s *req = new_request(o, stream);
     if (!req->done) { destroy_request(req); return GBX_ERR_CUDA; }
     req->kind = 1;
@@ -1098,6 +1200,8 @@ extern "C" int gbx_backward_init(gbx_request_t forward, const void *grad_recv, v
 
 // ------------------------------------------------------------- start / wait
 static int enqueue_start(gbx_request_s *req) {
+    GbxRange range(req->kind == 1 ? "gbx.start.backward"
+                   : req->algorithm == GBX_ALG_LOCALITY ? "gbx.start.locality" : "gbx.start.standard");
     // the exchange overwrites the bound destination: it follows the last host read-back of it
     if (req->host_down_pending) GBX_CUDA_TRY(cudaStreamWaitEvent(req->stream, req->host_down_ev, 0));
     if (req->use_graph && req->exec) {
@@ -1140,15 +1244,28 @@ static int parts_done(gbx_request_s *req, int *flag) {
     return GBX_SUCCESS;
 }
 
+// Reads and clears the request's status word once its kernels have finished:
+// GBX_ERR_DEVICE_WAIT when one of them gave up a bounded wait or skipped a bad piece.
+static int take_status(gbx_request_s *req) {
+    volatile int *w = req->status_host;
+    if (!w || *w == 0) return GBX_SUCCESS;
+    *w = 0;
+    return GBX_ERR_DEVICE_WAIT;
+}
+
 extern "C" int gbx_test(gbx_request_t req, int *flag) {
     if (!req || !flag) return GBX_ERR_ARG;
     *flag = 1;
-    if (!req->active) return GBX_SUCCESS;
+    if (!req->active) return take_status(req);   // e.g. completed by gbx_wait_stream
     if (req->kind == 2) {
         if (req->nready < req->npart) { *flag = 0; return GBX_ERR_STATE; }
         GBX_TRY(parts_done(req, flag));
-        if (*flag) req->active = 0;
-        return GBX_SUCCESS;
+        if (!*flag) return GBX_SUCCESS;
+        req->active = 0;
+        int rc = GBX_SUCCESS;
+        for (gbx_request_s *c : req->parts)
+            if (c && take_status(c) != GBX_SUCCESS) rc = GBX_ERR_DEVICE_WAIT;
+        return rc;
     }
     cudaError_t e = cudaEventQuery(pending_event(req));
     if (e == cudaErrorNotReady) { *flag = 0; return GBX_SUCCESS; }
@@ -1158,18 +1275,18 @@ extern "C" int gbx_test(gbx_request_t req, int *flag) {
     }
     req->active = 0;
     req->pending = nullptr;
-    return GBX_SUCCESS;
+    return take_status(req);
 }
 
 extern "C" int gbx_wait(gbx_request_t req) {
     if (!req) return GBX_ERR_ARG;
-    if (!req->active) return GBX_SUCCESS;
+    if (!req->active) return take_status(req);
     const auto t0 = std::chrono::steady_clock::now();
     int spins = 0;
     for (;;) {
         int flag = 0;
-        GBX_TRY(gbx_test(req, &flag));
-        if (flag) return GBX_SUCCESS;
+        const int rc = gbx_test(req, &flag);
+        if (rc != GBX_SUCCESS || flag) return rc;
         const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
         if (ms > req->timeout_ms) return GBX_ERR_TIMEOUT;
         if (++spins > 64) std::this_thread::sleep_for(std::chrono::microseconds(20));
@@ -1193,14 +1310,21 @@ extern "C" int gbx_wait_stream(gbx_request_t req, void *stream) {
     return GBX_SUCCESS;
 }
 
+// Waits for every request (each one is completed even when an earlier one reports an
+// error); returns the first error, in request order.
 extern "C" int gbx_waitall(int count, gbx_request_t *reqs) {
     if (count < 0 || (count > 0 && !reqs)) return GBX_ERR_ARG;
-    for (int i = 0; i < count; i++) GBX_TRY(gbx_wait(reqs[i]));
-    return GBX_SUCCESS;
+    int first = GBX_SUCCESS;
+    for (int i = 0; i < count; i++) {
+        const int rc = gbx_wait(reqs[i]);
+        if (rc != GBX_SUCCESS && first == GBX_SUCCESS) first = rc;
+    }
+    return first;
 }
 
 extern "C" int gbx_startall(int count, gbx_request_t *reqs) {
     if (count <= 0 || !reqs) return GBX_ERR_ARG;
+    GbxRange range("gbx.startall");
     for (int i = 0; i < count; i++) {
         if (!reqs[i]) return GBX_ERR_ARG;
         if (reqs[i]->kind == 2) return GBX_ERR_UNSUPPORTED;
@@ -1268,7 +1392,7 @@ extern "C" int gbx_request_bind(gbx_request_t req, const void *src, void *dst) {
         const int vec = op.kind == 0 ? op.cd.vec : op.fd.vec;
         if (((uintptr_t)ns & (uintptr_t)(vec - 1)) || ((uintptr_t)nd & (uintptr_t)(vec - 1))) return GBX_ERR_ARG;
         // an op tuned to a bulk-copy form cannot move to host memory
-        if (op.kind == 0 && op.cd.flat >= 8 &&
+        if (op.kind == 0 && (op.cd.flat == 8 || op.cd.flat == 9) &&
             ((ns_host && op.cd.src_role == ROLE_SRC) || (nd_host && op.cd.dst_role == ROLE_DST)))
             return GBX_ERR_UNSUPPORTED;
     }

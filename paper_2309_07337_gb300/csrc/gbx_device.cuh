@@ -58,7 +58,14 @@ struct CopyDesc {
     // scattered from shared memory by the threads
     const struct ScatterPiece *scat;
     int64_t nscat;
+    // the waiting kernels (bulk, scatter): the request's status word (host-mapped memory,
+    // read by gbx_wait / gbx_test), set to 1 when a bounded wait gave up and 2 when a piece
+    // failed its in-kernel check; and the spin limit of their main waits (the waits that
+    // drain copies already in flight keep GBX_WAIT_LIMIT)
+    int *status;
+    int32_t wait_limit;
 };
+#define GBX_WAIT_LIMIT (1 << 22)
 
 // One window of a scatter-form copy: the source elements of sorted pairs m0 .. m0+n-1 lie in
 // nrun runs of contiguous source bytes, run r at [src + run_off[r], src + run_off[r] +

@@ -17,6 +17,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <cstdint>
 #include <string>
@@ -45,6 +46,16 @@
 void gbx_note_cuda_error(cudaError_t e, const char *what, const char *file, int line);
 
 static inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+// NVTX range for the scope of a host call: setup stages, starts and (with graph=0) each
+// phase's kernel launch get a name a profiler can attribute time to.  NVTX v3 is header-only:
+// with no tool attached a push / pop is a call through a no-op function pointer.
+struct GbxRange {
+    explicit GbxRange(const char *name) { nvtxRangePushA(name); }
+    ~GbxRange() { nvtxRangePop(); }
+    GbxRange(const GbxRange &) = delete;
+    GbxRange &operator=(const GbxRange &) = delete;
+};
 static inline int bitlen_u64(uint64_t x) { int n = 0; while (x) { n++; x >>= 1; } return n; }
 
 // Device allocations owned by one object; freed together.
@@ -132,6 +143,8 @@ struct HostOp {
     int bulk_ok;            // every segment is contiguous on both sides and 16-byte aligned
     BulkTask *d_bulk;       // its pieces for the bulk form
     int64_t nbulk;
+    int stream_ok;          // the flat form's index arrays are 16-byte aligned and padded: the
+                            // stream forms (10 gather, 11 two-index) are available
     int scat_ok;            // two-index copy with the scatter form available
     ScatterPiece *d_scat;
     int64_t nscat;
@@ -151,6 +164,7 @@ struct LevelLaunch {
     int nops;
     int64_t total_tiles;
     int max_ctas;           // grid cap (0: none)
+    const char *phase;      // NVTX name of the launch (a string literal)
     void **d_ops;           // device array of descriptor pointers
     int64_t *d_prefix;      // device tile prefix (nops + 1)
 };
@@ -171,8 +185,16 @@ struct gbx_request_s {
     int split_order;         // single-term rows as copies: 0 in row (destination) order, 1 in source order
     int check_dup;           // locality form: compare every deduplicated value's bytes with its representative's at init
     int allow_bulk;          // offer the bulk form to the autotuner where it applies
+    int allow_stream;        // 0: no stream forms, 1: offered to the autotuner, 2: forced where they apply
+    int forced_form;         // -1, or the one copy form the tuner times where an op offers it
     int max_ctas;            // cap on every launch's grid (0: none)
     int timeout_ms;
+    int wait_limit;          // polls of the main waits of the bulk / scatter kernels
+    // the request's status word: pinned host memory mapped into the device, written by its
+    // kernels when a bounded wait gives up (1) or a piece fails its check (2), read and
+    // cleared by gbx_test / gbx_wait
+    int *status_host;
+    int *status_dev;
     gbx_graph_s *graph;
     gbx_request_s *forward;  // backward: its forward request
     gbx_graph_s *owned_graph;  // graph built for this request (dense all-to-all-v), freed with it
@@ -263,6 +285,7 @@ int gbx_make_bulk(gbx_request_s *req, const Seg *segs, int64_t nseg, int64_t nel
                   int *ok);
 int gbx_bulk_prepare(void);
 int gbx_scatter_prepare(void);
+int gbx_stream_prepare(void);
 int gbx_check_data_buf(const void *p, int64_t bytes);   // GBX_ERR_ARG unless the GPU can address p
 // Scatter-form windows of a two-index copy whose pairs are sorted by source (gs, the source
 // indices, decide the windows) and whose index arrays carry 4 elements of padding; *ok = 0

@@ -337,13 +337,26 @@ gbx_copy_pipe_kernel(const CopyDesc *const *__restrict__ ops, const int64_t *__r
 // thread per CTA drives a ring of GBX_BULK_STAGES buffers: a piece is loaded with
 // cp.async.bulk (completion counted on the stage's mbarrier), stored back with a bulk store,
 // and a stage is refilled once the store before it has read it, so several pieces per CTA
-// are always in flight.  Every mbarrier wait is bounded: a wait that gives up sets
-// gbx_bulk_status, waits (bounded again) for the stage loads still in flight and for the
-// stores, and leaves the kernel.
+// are always in flight.  Every mbarrier wait is bounded (the main waits by the op's
+// wait_limit, the drain waits by GBX_WAIT_LIMIT): a wait that gives up records status 1 for
+// every op of the launch (gbx_raise), waits (bounded again) for the stage loads still in
+// flight and for the stores, and leaves the kernel.
 __device__ int gbx_bulk_status;
 
-__device__ __forceinline__ bool bulk_wait(uint32_t bar, uint32_t parity) {
-    for (int it = 0; it < (1 << 22); it++) {
+// Records a status code (1: a bounded wait gave up, 2: a piece failed its check) in the
+// process-wide word and in the status word of every op of the launch: a launch that gives up
+// leaves pieces of any of its ops unfinished, so each request it serves must report it.
+__device__ __noinline__ void gbx_raise(const CopyDesc *const *__restrict__ ops, int nops, int code) {
+    atomicExch(&gbx_bulk_status, code);
+    for (int i = 0; i < nops; i++) {
+        int *w = ops[i]->status;
+        if (w) *reinterpret_cast<volatile int *>(w) = code;
+    }
+    __threadfence_system();
+}
+
+__device__ __forceinline__ bool bulk_wait(uint32_t bar, uint32_t parity, int limit = GBX_WAIT_LIMIT) {
+    for (int it = 0; it < limit; it++) {
         uint32_t done;
         asm volatile(
             "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
@@ -385,7 +398,7 @@ __global__ void __launch_bounds__(32) gbx_bulk_kernel(const CopyDesc *const *__r
         // units within one stage is recorded and skipped
         if (k.len <= 0 || k.len > GBX_BULK_BYTES || ((k.len | k.src | k.dst |
                                                       (int64_t)(uintptr_t)d->src | (int64_t)(uintptr_t)d->dst) & 15)) {
-            atomicExch(&gbx_bulk_status, 2);
+            gbx_raise(ops, nops, 2);
             dst_of[q] = nullptr;
             len_of[q] = 0;
             pend[q] = false;
@@ -404,13 +417,14 @@ __global__ void __launch_bounds__(32) gbx_bulk_kernel(const CopyDesc *const *__r
         const int64_t t = blockIdx.x + (int64_t)q * gridDim.x;
         if (t < ntasks) load(q, t);
     }
+    const int limit = ops[0]->wait_limit;
     bool failed = false;
     for (int64_t k = 0;; k++) {
         const int64_t t = blockIdx.x + k * gridDim.x;
         if (t >= ntasks) break;
         const int q = (int)(k % S);
         if (pend[q]) {
-            if (!bulk_wait(sbar + 8 * q, parity[q])) {
+            if (!bulk_wait(sbar + 8 * q, parity[q], limit)) {
                 failed = true;
                 break;
             }
@@ -432,7 +446,7 @@ __global__ void __launch_bounds__(32) gbx_bulk_kernel(const CopyDesc *const *__r
         }
     }
     if (failed) {
-        atomicExch(&gbx_bulk_status, 1);
+        gbx_raise(ops, nops, 1);
         for (int q = 0; q < S; q++)
             if (pend[q]) bulk_wait(sbar + 8 * q, parity[q]);
     }
@@ -499,12 +513,13 @@ __global__ void __launch_bounds__(NT) gbx_scatter_kernel(const CopyDesc *const *
         for (int q = 0; q < S; q++) last[q] = -1;
         bool stop = false;
         const CopyDesc *d = nullptr;
+        const int limit = ops[0]->wait_limit;
         if (blockIdx.x < npieces) fetch(blockIdx.x, d);
         for (int64_t k = 0;; k++) {
             const int64_t t = blockIdx.x + k * gridDim.x;
             if (t >= npieces) break;
             const int q = (int)(k % S);
-            if (k >= S && !bulk_wait(sempty + 8 * q, (uint32_t)((k / S - 1) & 1))) {
+            if (k >= S && !bulk_wait(sempty + 8 * q, (uint32_t)((k / S - 1) & 1), limit)) {
                 abort_flag = 1;
                 stop = true;
                 break;
@@ -532,7 +547,7 @@ __global__ void __launch_bounds__(NT) gbx_scatter_kernel(const CopyDesc *const *
             }
             const uint32_t fb = sfull + 8 * q;
             if (!good) {   // validated at init; recorded, and the consumers skip it
-                atomicExch(&gbx_bulk_status, 2);
+                gbx_raise(ops, nops, 2);
                 P.n = 0;
                 piece_s[q] = P;
                 desc_s[q] = pd;
@@ -561,7 +576,7 @@ __global__ void __launch_bounds__(NT) gbx_scatter_kernel(const CopyDesc *const *
         }
         asm volatile("cp.async.wait_all;" ::: "memory");
         if (stop) {   // leave no copy in flight: wait (bounded) for the last one issued on each stage
-            atomicExch(&gbx_bulk_status, 1);
+            gbx_raise(ops, nops, 1);
             for (int q = 0; q < S; q++)
                 if (last[q] >= 0) bulk_wait(sfull + 8 * q, (uint32_t)((last[q] / S) & 1));
         }
@@ -569,11 +584,12 @@ __global__ void __launch_bounds__(NT) gbx_scatter_kernel(const CopyDesc *const *
     }
     // -------------------------------------------------------------------- consumers
     const int ct = threadIdx.x - 32;
+    const int limit = ops[0]->wait_limit;
     for (int64_t k = 0;; k++) {
         const int64_t t = blockIdx.x + k * gridDim.x;
         if (t >= npieces) break;
         const int q = (int)(k % S);
-        if (!bulk_wait(sfull + 8 * q, (uint32_t)((k / S) & 1))) {
+        if (!bulk_wait(sfull + 8 * q, (uint32_t)((k / S) & 1), limit)) {
             abort_flag = 1;
             break;
         }
@@ -588,7 +604,7 @@ __global__ void __launch_bounds__(NT) gbx_scatter_kernel(const CopyDesc *const *
             const int j = i / cpe, c = i - j * cpe;
             const int64_t w = (int64_t)ps[j] * s - src0 + c * 16;
             if (w < 0 || w + 16 > len) {   // validated at init; recorded and skipped
-                atomicExch(&gbx_bulk_status, 2);
+                gbx_raise(ops, nops, 2);
                 continue;
             }
             const uint4 v = *reinterpret_cast<const uint4 *>(win + w);
@@ -634,6 +650,214 @@ int gbx_scatter_prepare(void) {
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(gbx_scatter_kernel<1024, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  8 * GBX_SCAT_STAGE);
+    return e == cudaSuccess ? GBX_SUCCESS : GBX_ERR_CUDA;
+}
+
+// ------------------------------------------------------------------ stream
+// Stream form of the flat copies (FORM 1: gather into a contiguous destination run; FORM 3:
+// two-index gather-scatter): the same tiles of GBX_TILE chunks, but the per-element index
+// arrays, the only data whose addresses are known in advance, are streamed into a ring of S
+// shared-memory stages by the bulk-copy engine, so that the payload loads never wait for an
+// index load from memory.  Warp 0 is the producer: its lane 0 finds the op of the CTA's next
+// tile, has the bulk-copy engine copy the tile's index range (rounded out to 16-byte
+// boundaries; the index arrays carry 4 entries of padding) into a stage, completing on the
+// stage's "full" mbarrier, and refills a stage once the consumers have released it on its
+// "empty" mbarrier.  The other warps are consumers: per tile, each thread gathers U chunks
+// (all loads issued before the stores) reading the indices from shared memory.  No CTA-wide
+// barrier after setup; every wait is bounded as in the scatter kernel (a consumer that gives
+// up raises `abort`, the producer stops issuing and drains its copies in flight).
+#define GBX_STREAM_IDX ((GBX_TILE + 8) * 4)   // bytes of one index array per stage
+
+template <int VEC, int FORM, int NT, int S, int U, int PS>
+__global__ void __launch_bounds__(NT, PS) gbx_stream_kernel(const CopyDesc *const *__restrict__ ops,
+                                                        const int64_t *__restrict__ prefix, int nops,
+                                                        int64_t ntiles) {
+    typedef typename VecT<VEC>::T V;
+    constexpr int NC = NT - 32, NCW = NC / 32;
+    constexpr int STAGE = GBX_STREAM_IDX * (FORM == 3 ? 2 : 1);
+    extern __shared__ __align__(128) unsigned char gbx_stream_smem[];
+    __shared__ __align__(8) uint64_t full[S], empty[S];
+    __shared__ const CopyDesc *desc_s[S];
+    __shared__ int64_t tile_s[S], efirst_s[S], ebase_s[S];
+    __shared__ volatile int abort_flag;
+    const uint32_t sbuf = (uint32_t)__cvta_generic_to_shared(gbx_stream_smem);
+    const uint32_t sfull = (uint32_t)__cvta_generic_to_shared(full);
+    const uint32_t sempty = (uint32_t)__cvta_generic_to_shared(empty);
+    if (threadIdx.x == 0) {
+        for (int q = 0; q < S; q++) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(sfull + 8 * q) : "memory");
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(sempty + 8 * q), "r"(NCW) : "memory");
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        abort_flag = 0;
+    }
+    __syncthreads();   // the only CTA-wide barrier
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int limit = ops[0]->wait_limit;
+    if (warp == 0) {
+        if (lane != 0) return;
+        // ---------------------------------------------------------------- producer
+        int64_t last[S];   // last tile issued on each stage (-1: none)
+#pragma unroll
+        for (int q = 0; q < S; q++) last[q] = -1;
+        bool stop = false;
+        for (int64_t k = 0;; k++) {
+            const int64_t t = blockIdx.x + k * gridDim.x;
+            if (t >= ntiles) break;
+            const int q = (int)(k % S);
+            if (k >= S && !bulk_wait(sempty + 8 * q, (uint32_t)((k / S - 1) & 1), limit)) {
+                abort_flag = 1;
+                stop = true;
+                break;
+            }
+            if (abort_flag) {
+                stop = true;
+                break;
+            }
+            const int op = nops > 1 ? find_op(prefix, nops, t) : 0;
+            const CopyDesc *d = ops[op];
+            const int64_t lt = t - __ldg(prefix + op);
+            const int64_t cpe = d->cpe;
+            const int64_t c0 = lt * GBX_TILE;
+            const int64_t c1 = min(d->nchunks, c0 + GBX_TILE);
+            const int64_t e_first = c0 / cpe, e_last = (c1 - 1) / cpe;
+            const int64_t e_al = e_first & ~(int64_t)3, e_end = (e_last + 4) & ~(int64_t)3;
+            const uint32_t bytes = (uint32_t)((e_end - e_al) * 4);
+            const uint32_t fb = sfull + 8 * q, stage = sbuf + q * STAGE;
+            desc_s[q] = d;
+            tile_s[q] = lt;
+            efirst_s[q] = e_first;
+            const uintptr_t al = (uintptr_t)d->flat_idx | (FORM == 3 ? (uintptr_t)d->flat_didx : 0);
+            if ((al & 15) || bytes > GBX_STREAM_IDX || c1 <= c0) {   // validated at init; recorded, skipped
+                gbx_raise(ops, nops, 2);
+                ebase_s[q] = -1;
+                asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(fb) : "memory");
+                continue;
+            }
+            ebase_s[q] = e_al;
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // consumers' reads before the refill
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(fb),
+                         "r"(bytes * (FORM == 3 ? 2u : 1u))
+                         : "memory");
+            asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                         ::"r"(stage), "l"(d->flat_idx + e_al), "r"(bytes), "r"(fb)
+                         : "memory");
+            if (FORM == 3)
+                asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                             ::"r"(stage + GBX_STREAM_IDX), "l"(d->flat_didx + e_al), "r"(bytes), "r"(fb)
+                             : "memory");
+            last[q] = k;
+        }
+        if (stop) {   // leave no copy in flight: wait (bounded) for the last one issued on each stage
+            gbx_raise(ops, nops, 1);
+            for (int q = 0; q < S; q++)
+                if (last[q] >= 0) bulk_wait(sfull + 8 * q, (uint32_t)((last[q] / S) & 1));
+        }
+        return;
+    }
+    // -------------------------------------------------------------------- consumers
+    const int ct = threadIdx.x - 32;
+    for (int64_t k = 0;; k++) {
+        const int64_t t = blockIdx.x + k * gridDim.x;
+        if (t >= ntiles) break;
+        const int q = (int)(k % S);
+        if (!bulk_wait(sfull + 8 * q, (uint32_t)((k / S) & 1), limit)) {
+            abort_flag = 1;
+            break;
+        }
+        const int64_t e_al = ebase_s[q];
+        if (e_al >= 0) {
+            const CopyDesc *d = desc_s[q];
+            const int cpe = d->cpe, sh = d->cpe_shift;
+            const uint32_t magic = d->cpe_magic;
+            const int64_t s = d->elem_size, e0 = efirst_s[q], c0 = tile_s[q] * GBX_TILE;
+            const int left = (int)min((int64_t)GBX_TILE, d->nchunks - c0);
+            const uint32_t r0 = (uint32_t)(c0 - e0 * cpe);   // chunk of element e0 where the tile starts
+            const int32_t *is = reinterpret_cast<const int32_t *>(gbx_stream_smem + q * STAGE);
+            const int32_t *ids = reinterpret_cast<const int32_t *>(gbx_stream_smem + q * STAGE + GBX_STREAM_IDX);
+            const char *src = d->src, *src2 = d->src2;
+            char *dst = d->dst;
+            for (int base = 0; base < left; base += NC * U) {
+                V val[U];
+                int64_t doff[U];
+#pragma unroll
+                for (int u = 0; u < U; u++) {
+                    const int x = base + u * NC + ct;
+                    if (x < left) {
+                        const uint32_t xx = r0 + (uint32_t)x;
+                        const uint32_t el = unit_of(xx, cpe, sh, magic);
+                        const int64_t j = (int64_t)(xx - el * (uint32_t)cpe) * VEC;
+                        const int64_t e = e0 + el;
+                        const int w = (int)(e - e_al);   // < GBX_TILE + 8: inside the stage's copy
+                        const uint32_t gi = (uint32_t)is[w];
+                        doff[u] = (FORM == 3 ? (int64_t)ids[w] * s : d->dst_flat0 + e * s) + j;
+                        const char *b = (gi & GBX_FLAT_SRC2) ? src2 : src;
+                        val[u] = ldv<VEC>(b + (int64_t)(gi & ~GBX_FLAT_SRC2) * s + j);
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < U; u++)
+                    if (base + u * NC + ct < left) stv<VEC>(dst + doff[u], val[u]);
+            }
+        }
+        __syncwarp();
+        if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(sempty + 8 * q) : "memory");
+        if (abort_flag) break;
+    }
+}
+
+// Shapes of the stream kernel, chosen by the launch's block value: threads per CTA (one
+// producer warp plus consumers), stages, chunks per consumer thread per pass, CTAs per SM
+// (the launch bounds hold the registers to what that many CTAs need; shared memory per SM
+// is at most 4 x 4 x 8,256 = 132 KB).
+struct StreamShape { int nt, stages, u, per_sm; };
+static StreamShape stream_shape(int block) {
+    if (block <= 256) return {288, 4, 4, 4};
+    return {544, 6, 2, 2};
+}
+
+template <int VEC, int FORM>
+static cudaError_t stream_launch_v(int block, int grid, cudaStream_t st, const CopyDesc *const *ops,
+                                   const int64_t *prefix, int nops, int64_t n) {
+    const StreamShape h = stream_shape(block);
+    const size_t smem = (size_t)h.stages * GBX_STREAM_IDX * (FORM == 3 ? 2 : 1);
+    if (h.nt == 288) gbx_stream_kernel<VEC, FORM, 288, 4, 4, 4><<<grid, 288, smem, st>>>(ops, prefix, nops, n);
+    else gbx_stream_kernel<VEC, FORM, 544, 6, 2, 2><<<grid, 544, smem, st>>>(ops, prefix, nops, n);
+    return cudaGetLastError();
+}
+
+static cudaError_t stream_launch(int vec, int flat, int block, int grid, cudaStream_t st, const CopyDesc *const *ops,
+                                 const int64_t *prefix, int nops, int64_t n) {
+    const bool two = flat == 11;
+    switch (vec) {
+        case 16: return two ? stream_launch_v<16, 3>(block, grid, st, ops, prefix, nops, n)
+                            : stream_launch_v<16, 1>(block, grid, st, ops, prefix, nops, n);
+        case 8: return two ? stream_launch_v<8, 3>(block, grid, st, ops, prefix, nops, n)
+                           : stream_launch_v<8, 1>(block, grid, st, ops, prefix, nops, n);
+        case 4: return two ? stream_launch_v<4, 3>(block, grid, st, ops, prefix, nops, n)
+                           : stream_launch_v<4, 1>(block, grid, st, ops, prefix, nops, n);
+        default: return cudaErrorInvalidValue;   // the stream form is offered for vectors of 4..16 bytes
+    }
+}
+
+template <int VEC, int FORM>
+static cudaError_t stream_attr_v() {
+    cudaError_t e = cudaFuncSetAttribute(gbx_stream_kernel<VEC, FORM, 288, 4, 4, 4>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         4 * GBX_STREAM_IDX * (FORM == 3 ? 2 : 1));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(gbx_stream_kernel<VEC, FORM, 544, 6, 2, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 6 * GBX_STREAM_IDX * (FORM == 3 ? 2 : 1));
+    return e;
+}
+
+int gbx_stream_prepare(void) {
+    cudaError_t e = stream_attr_v<16, 1>();
+    if (e == cudaSuccess) e = stream_attr_v<16, 3>();
+    if (e == cudaSuccess) e = stream_attr_v<8, 1>();
+    if (e == cudaSuccess) e = stream_attr_v<8, 3>();
+    if (e == cudaSuccess) e = stream_attr_v<4, 1>();
+    if (e == cudaSuccess) e = stream_attr_v<4, 3>();
     return e == cudaSuccess ? GBX_SUCCESS : GBX_ERR_CUDA;
 }
 
@@ -857,6 +1081,7 @@ static int pipe_block(int flat, int block) { return (flat == 5 || flat == 7) && 
 int gbx_occupancy(int kind, int dtype, int vec, int block, int flat) {
     if (kind == 0 && flat == 8) return 1;   // bulk kernel: one CTA per SM (its ring)
     if (kind == 0 && flat == 9) return scatter_shape(block).per_sm;
+    if (kind == 0 && (flat == 10 || flat == 11)) return stream_shape(block).per_sm;
     if (kind == 0) block = pipe_block(flat, block);
     const void *f = kind == 0 ? (const void *)copy_fn(vec, block, flat) : (const void *)fold_fn(dtype, vec, block);
     int n = 0;
@@ -880,6 +1105,8 @@ cudaError_t gbx_launch_copy(const CopyDesc *const *ops, const int64_t *tile_pref
     if (flat == 9) {   // scatter form: a "tile" is one source window
         return scatter_launch(block, clamp_grid(grid, total_tiles), st, ops, tile_prefix, nops, total_tiles);
     }
+    if (flat == 10 || flat == 11)   // stream forms: the flat forms' tiles, indices through shared memory
+        return stream_launch(vec, flat, block, clamp_grid(grid, total_tiles), st, ops, tile_prefix, nops, total_tiles);
     if ((flat == 5 || flat == 7) && (nops > 1 || vec == 0)) flat -= 4;   // the pipelined kernels take one op
     block = pipe_block(flat, block);
     CopyFn f = copy_fn(vec, block, flat);

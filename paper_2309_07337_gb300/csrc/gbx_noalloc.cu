@@ -104,8 +104,11 @@ __global__ void na_match_kernel(unsigned char *scratch, NaArgs a) {
         const int64_t cnt = a.recvcounts[i];
         if ((int64_t)a.sendcounts[e] != cnt || cnt < 0) { na_err(v, GBX_ERR_TRUNCATE); continue; }
         const int64_t sd = a.sdispls[e], rd = a.rdispls[i];
-        if (sd < 0 || rd < 0 || a.send_base[r] + (sd + cnt) * a.s > a.send_bytes ||
-            a.recv_base[d] + (rd + cnt) * a.s > a.recv_bytes) {
+        // bounds by division, so that no product can overflow whatever the element size:
+        // base + (disp + cnt) * s <= bytes  <=>  disp + cnt <= (bytes - base) / s
+        const int64_t sb = a.send_base[r], rb = a.recv_base[d];
+        if (sd < 0 || rd < 0 || sb > a.send_bytes || rb > a.recv_bytes || sd + cnt > (a.send_bytes - sb) / a.s ||
+            rd + cnt > (a.recv_bytes - rb) / a.s) {
             na_err(v, GBX_ERR_INDEX);
             continue;
         }
@@ -206,6 +209,7 @@ extern "C" int gbx_neighbor_alltoallv_noalloc(int P, int64_t n_in_edges, const i
     if (n_in_edges > 0 && (!sources || !recvcounts || !rdispls)) return GBX_ERR_ARG;
     if (n_out_edges > 0 && (!destinations || !sendcounts || !sdispls)) return GBX_ERR_ARG;
     if (n_in_edges > GBX_NOALLOC_MAX_EDGES || n_out_edges > GBX_NOALLOC_MAX_EDGES) return GBX_ERR_LIMIT;
+    GbxRange range("gbx.noalloc");
     GBX_TRY(gbx_check_data_buf(sendbuf, sendbuf_bytes));
     GBX_TRY(gbx_check_data_buf(recvbuf, recvbuf_bytes));
     unsigned char *scratch = nullptr;

@@ -1660,7 +1660,7 @@ int gbx_make_flat(gbx_request_s *req, const Seg *segs, int64_t nseg, const int32
     GBX_CUDA_TRY(cudaStreamSynchronize(st));
     if (hb) return GBX_SUCCESS;
     int32_t *g;
-    GBX_TRY(req->mem.get(&g, nelem));
+    GBX_TRY(req->mem.get(&g, nelem + 4));   // 4 entries of padding for the stream form's rounded copies
     flat_build_kernel<<<grid_of(nelem), SETUP_T, 0, st>>>(segs, nseg, idx, nelem, req->elem_size, g, bad);
     GBX_CUDA_TRY(cudaGetLastError());
     Seg first;

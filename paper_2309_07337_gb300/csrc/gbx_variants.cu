@@ -26,13 +26,17 @@ static unsigned vgrid(int64_t n) {
 }
 
 // mode 0: alltoall, 1: allgather, 2: allgatherv (per-rank send counts)
+// A derived displacement beyond the int32 range of the all-to-all-v arguments is refused
+// (GBX_ERR_UNSUPPORTED) on both sides, before any buffer is checked.
 __global__ void fill_out_kernel(const int *owner, const int *ptr, int64_t E, int mode, int count,
-                                const int *rank_count, int *sendcounts, int *sdispls) {
+                                const int *rank_count, int *sendcounts, int *sdispls, int *err) {
     FOR_ALL(e, E) {
         const int r = owner[e];
         const int64_t j = e - ptr[r];
+        const int64_t disp = mode == 0 ? j * (int64_t)count : 0;
+        if (disp > 0x7fffffffll) atomicMin(err, GBX_ERR_UNSUPPORTED);
         sendcounts[e] = mode == 2 ? rank_count[r] : count;
-        sdispls[e] = mode == 0 ? (int)(j * count) : 0;
+        sdispls[e] = disp > 0x7fffffffll ? 0 : (int)disp;
     }
 }
 
@@ -40,9 +44,10 @@ __global__ void fill_in_kernel(const int *owner, const int *ptr, int64_t E, int 
                                int *rdispls, int *err) {
     FOR_ALL(i, E) {
         const int64_t k = i - ptr[owner[i]];
-        if (k * (int64_t)count > 0x7fffffffll) atomicMin(err, GBX_ERR_UNSUPPORTED);
+        const int64_t disp = k * (int64_t)count;
+        if (disp > 0x7fffffffll) atomicMin(err, GBX_ERR_UNSUPPORTED);
         recvcounts[i] = count;
-        rdispls[i] = (int)(k * count);
+        rdispls[i] = disp > 0x7fffffffll ? 0 : (int)disp;
     }
 }
 
@@ -62,7 +67,8 @@ static int derived_init(gbx_graph_t graph, int mode, int count, const int *rank_
     GBX_TRY(ws.get(&err, 1));
     GBX_CUDA_TRY(cudaMemsetAsync(err, 0x7f, sizeof(int), st));
     if (E > 0) {
-        fill_out_kernel<<<vgrid(E), VT, 0, st>>>(graph->out_owner, graph->out_ptr, E, mode, count, rank_count, sc, sd);
+        fill_out_kernel<<<vgrid(E), VT, 0, st>>>(graph->out_owner, graph->out_ptr, E, mode, count, rank_count, sc, sd,
+                                                 err);
         if (mode != 2) fill_in_kernel<<<vgrid(E), VT, 0, st>>>(graph->in_owner, graph->in_ptr, E, count, rc, rd, err);
         GBX_CUDA_TRY(cudaGetLastError());
     }
