@@ -1,8 +1,12 @@
 """GPU: config 3 at full size -- 64 uneven SpMV halo patterns (rows 2^14..2^20, P 64..1024,
 8-32 nnz/row, fp32 and fp64) started together by one startall (one CUDA graph, fused
-launches per kernel class), in the launch configuration the benchmark times; every
-pattern's receive buffer is compared with the same pattern run alone, and a sample of
-patterns (the largest, the smallest and two more of each payload type) with the oracle."""
+launches per kernel class), in the launch configuration the benchmark times.  Every
+pattern's receive buffer is compared byte for byte with the oracle's exchange, and every
+pattern's gradient from the batched reverse exchange (one startall of the 64 backward
+requests) with the oracle's backward in the order of its form."""
+import os
+from concurrent.futures import ThreadPoolExecutor
+
 import numpy as np
 import pytest
 
@@ -30,30 +34,38 @@ def test_config3_batched_full_size():
     gen = torch.Generator(device="cuda")
     gen.manual_seed(pt.SEED + 30)
     items = []
-    for q in pats:
+    for j, q in enumerate(pats):
         dt = torch.float64 if q.dtype == "f64" else torch.float32
-        n = q.sendbuf_bytes // (8 if q.dtype == "f64" else 4)
-        sb = torch.randn(n, device="cuda", dtype=dt, generator=gen)
-        rb = torch.full((q.recvbuf_bytes // sb.element_size(),), -7.0, device="cuda", dtype=dt)
-        alone = rb.clone()
-        dq = gbx.DevicePattern(q)
-        ex = gbx.Exchange(q, sb, rb, "locality" if len(items) % 3 == 0 else "standard", dp=dq)
-        ex2 = gbx.Exchange(q, sb, alone, "standard", info="graph=0", dp=dq, graph=ex.graph)
-        ex2.start()
-        ex2.wait()
-        items.append((q, sb, rb, alone, ex, ex2))
-    reqs = [it[4].request for it in items]
-    for _ in range(2):
-        gbx.startall(reqs)
-        gbx.waitall(reqs)
-    for q, sb, rb, alone, *_ in items:
-        assert torch.equal(rb.view(torch.uint8), alone.view(torch.uint8)), q.name
-    by_size = sorted(range(64), key=lambda j: pats[j].volume)
-    f32 = [j for j in by_size if pats[j].dtype == "f32"]
-    f64 = [j for j in by_size if pats[j].dtype == "f64"]
-    sample = {by_size[0], by_size[-1], f32[len(f32) // 2], f32[-1], f64[len(f64) // 2], f64[0]}
-    for j in sorted(sample):
-        q, sb, rb = items[j][0], items[j][1], items[j][2]
-        init = np.full(q.recvbuf_bytes // sb.element_size(), -7.0, dtype=sb.cpu().numpy().dtype)
-        want = oracle.standard(q, sb.cpu().numpy(), init)
-        assert_bytes_equal(rb.cpu().numpy(), want, q.name)
+        esz = 8 if q.dtype == "f64" else 4
+        sb = torch.randn(q.sendbuf_bytes // esz, device="cuda", dtype=dt, generator=gen)
+        rb = torch.full((q.recvbuf_bytes // esz,), -7.0, device="cuda", dtype=dt)
+        gr = torch.randn(q.recvbuf_bytes // esz, device="cuda", dtype=dt, generator=gen)
+        gx = torch.full_like(sb, 3.0)   # elements no slot reads keep this value
+        alg = "locality" if j % 3 == 0 else "standard"
+        ex = gbx.Exchange(q, sb, rb, alg, dp=gbx.DevicePattern(q))
+        b = gbx.backward_init(ex.request, gr, gx)
+        items.append((q, sb, rb, gr, gx, ex, b, alg))
+    fwd = [it[5].request for it in items]
+    bwd = [it[6] for it in items]
+    for _ in range(2):                   # a second start must give the same bytes
+        gbx.startall(fwd)
+        gbx.waitall(fwd)
+        gbx.startall(bwd)
+        gbx.waitall(bwd)
+    host = [(q, sb.cpu().numpy(), rb.cpu().numpy(), gr.cpu().numpy(), gx.cpu().numpy(), alg)
+            for q, sb, rb, gr, gx, _, _, alg in items]
+    del items, fwd, bwd
+
+    def check(h):
+        q, x, got, g, got_g, alg = h
+        init = np.full(len(got), -7.0, dtype=got.dtype)
+        assert_bytes_equal(got, oracle.standard(q, x, init), q.name)
+        g0 = np.full(len(got_g), 3.0, dtype=got_g.dtype)
+        want_g = oracle.backward(q, g, g0, form=0 if alg == "standard" else 1)
+        assert_bytes_equal(got_g, want_g, q.name + " backward " + alg)
+        return q.volume
+
+    # the oracle is C called through ctypes, which releases the GIL: one pattern per thread
+    with ThreadPoolExecutor(max(1, min(16, os.cpu_count() or 1))) as pool:
+        vols = list(pool.map(check, host))
+    assert sum(vols) == sum(h[0].volume for h in host)

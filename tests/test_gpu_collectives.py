@@ -1,6 +1,6 @@
 """GPU: neighbor_alltoall / allgather / allgatherv and the dense alltoallv, each against the
-oracle's neighbourhood all-to-all-v run on the equivalent counts and displacements written
-out from the MPI definitions on the host."""
+oracle's derived collectives (oracle.neighbor_pattern / neighbor_allgatherv / alltoallv_pattern,
+whose counts and displacements come from the MPI definitions in oracle.c)."""
 import numpy as np
 import pytest
 
@@ -28,24 +28,17 @@ def _graph_of(p):
     return comm, gbx.DistGraph(comm, t(p.in_ptr), t(p.sources), t(p.out_ptr), t(p.dests))
 
 
-def _explicit(p, send_counts_of_edge, sdispl_of_edge, recvcount_of_edge, rdispl_of_edge, region_send, region_recv, s):
-    """The equivalent neighbourhood all-to-all-v problem (packed regions, byte bases)."""
-    q = pt.Pattern(**{k: getattr(p, k) for k in p.__dataclass_fields__})
-    q.sendcounts = send_counts_of_edge.astype(np.int32)
-    q.sdispls = sdispl_of_edge.astype(np.int32)
-    q.recvcounts = recvcount_of_edge.astype(np.int32)
-    q.rdispls = rdispl_of_edge.astype(np.int32)
-    q.elem_size = s
-    q.send_base = (np.concatenate([[0], np.cumsum(region_send)[:-1]]) * s).astype(np.int64)
-    q.recv_base = (np.concatenate([[0], np.cumsum(region_recv)[:-1]]) * s).astype(np.int64)
-    q.sendbuf_bytes = int(np.sum(region_send) * s)
-    q.recvbuf_bytes = int(np.sum(region_recv) * s)
-    q.send_slot_ptr = q.send_idx = q.recv_slot_ptr = q.global_sidx = q.global_ridx = None
-    return q
-
-
-def _pos_in_list(ptr):
-    return np.concatenate([np.arange(ptr[r + 1] - ptr[r]) for r in range(len(ptr) - 1)] + [np.zeros(0, int)]).astype(np.int64)
+def _problem(p, region_send, region_recv, s):
+    """p's graph with packed per-rank regions of the given sizes (in elements) and element
+    size s: the argument of the oracle's derived collectives."""
+    g = pt.Pattern(**{k: getattr(p, k) for k in p.__dataclass_fields__})
+    g.elem_size = s
+    g.dtype = "bytes"
+    g.send_base = (np.concatenate([[0], np.cumsum(region_send)[:-1]]) * s).astype(np.int64)
+    g.recv_base = (np.concatenate([[0], np.cumsum(region_recv)[:-1]]) * s).astype(np.int64)
+    g.sendbuf_bytes = int(np.sum(region_send) * s)
+    g.recvbuf_bytes = int(np.sum(region_recv) * s)
+    return g
 
 
 @pytest.mark.parametrize("seed", [1, 2, 3])
@@ -53,34 +46,28 @@ def _pos_in_list(ptr):
 def test_neighbor_alltoall_and_allgather(seed, kind):
     p = pt.random_pattern(seed)
     s, count = int([1, 8, 24][seed % 3]), 3 + seed
-    out_owner = np.repeat(np.arange(p.P), np.diff(p.out_ptr))
-    in_owner = np.repeat(np.arange(p.P), np.diff(p.in_ptr))
     deg_out = np.diff(p.out_ptr)
     deg_in = np.diff(p.in_ptr)
-    E = len(p.dests)
-    jo = _pos_in_list(p.out_ptr)
-    ji = _pos_in_list(p.in_ptr)
-    cnt = np.full(E, count)
-    sd = jo * count if kind == "alltoall" else np.zeros(E, np.int64)
     region_send = deg_out * count if kind == "alltoall" else np.full(p.P, count)
-    q = _explicit(p, cnt, sd, np.full(E, count), ji * count, np.maximum(region_send, 1), np.maximum(deg_in * count, 1), s)
-    x = pt.random_bytes(q.sendbuf_bytes, seed)
-    init = pt.random_bytes(q.recvbuf_bytes, seed + 9)
+    g = _problem(p, np.maximum(region_send, 1), np.maximum(deg_in * count, 1), s)
+    x = pt.random_bytes(g.sendbuf_bytes, seed)
+    init = pt.random_bytes(g.recvbuf_bytes, seed + 9)
+    q = oracle.neighbor_pattern(g, kind, count=count)
     want = oracle.standard(q, x, init)
-    comm, g = _graph_of(p)
+    comm, gr = _graph_of(p)
     send = torch.from_numpy(x.copy()).cuda()
     recv = torch.from_numpy(init.copy()).cuda()
-    sb = torch.from_numpy(q.send_base).cuda()
-    rb = torch.from_numpy(q.recv_base).cuda()
+    sb = torch.from_numpy(g.send_base).cuda()
+    rb = torch.from_numpy(g.recv_base).cuda()
     f = gbx.neighbor_alltoall_init if kind == "alltoall" else gbx.neighbor_allgather_init
-    r = f(send, sb, recv, rb, count, g, s)
+    r = f(send, sb, recv, rb, count, gr, s)
     r.start()
     r.wait()
     assert_bytes_equal(recv.cpu().numpy(), want, f"{kind} seed {seed}")
     # locality-aware form: values named by their source elements, so an allgather sends each
     # element once per remote node; same bytes, the oracle's statistics
     recv2 = torch.from_numpy(init.copy()).cuda()
-    r2 = f(send, sb, recv2, rb, count, g, s, info="algorithm=locality")
+    r2 = f(send, sb, recv2, rb, count, gr, s, info="algorithm=locality")
     r2.start()
     r2.wait()
     assert_bytes_equal(recv2.cpu().numpy(), want, f"{kind} seed {seed} locality")
@@ -88,7 +75,6 @@ def test_neighbor_alltoall_and_allgather(seed, kind):
     i = r2.info()
     assert {k: i[k] for k in ("U", "node_pairs", "V_inter", "msgs_step1", "msgs_step3")} == \
         {k: st[k] for k in ("U", "node_pairs", "V_inter", "msgs_step1", "msgs_step3")}
-    del out_owner, in_owner
 
 
 def test_neighbor_allgatherv():
@@ -97,35 +83,54 @@ def test_neighbor_allgatherv():
     rng = np.random.default_rng(4)
     rank_count = rng.integers(0, 6, size=p.P)
     E = len(p.dests)
-    in_owner = np.repeat(np.arange(p.P), np.diff(p.in_ptr))
     rc = rank_count[p.sources]                       # each in-edge receives its sender's count
     rd = np.zeros(E, np.int64)
     for d in range(p.P):                             # packed in in-list order
         lo, hi = p.in_ptr[d], p.in_ptr[d + 1]
         rd[lo:hi] = np.concatenate([[0], np.cumsum(rc[lo:hi])[:-1]]) if hi > lo else []
     region_recv = np.array([rc[p.in_ptr[d]:p.in_ptr[d + 1]].sum() for d in range(p.P)])
-    q = _explicit(p, rank_count[np.repeat(np.arange(p.P), np.diff(p.out_ptr))], np.zeros(E, np.int64), rc, rd,
-                  np.maximum(rank_count, 1), np.maximum(region_recv, 1), s)
-    x = pt.random_bytes(q.sendbuf_bytes, 2)
-    want = oracle.standard(q, x)
-    comm, g = _graph_of(p)
+    g = _problem(p, np.maximum(rank_count, 1), np.maximum(region_recv, 1), s)
+    x = pt.random_bytes(g.sendbuf_bytes, 2)
+    want = oracle.neighbor_allgatherv(g, rank_count, rc, rd, x)
+    comm, gr = _graph_of(p)
     send = torch.from_numpy(x.copy()).cuda()
-    recv = torch.zeros(q.recvbuf_bytes, dtype=torch.uint8, device="cuda")
+    recv = torch.zeros(g.recvbuf_bytes, dtype=torch.uint8, device="cuda")
     t32 = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.int32)).cuda()
-    r = gbx.neighbor_allgatherv_init(send, torch.from_numpy(q.send_base).cuda(), t32(rank_count), recv,
-                                     torch.from_numpy(q.recv_base).cuda(), t32(rc), t32(rd), g, s)
+    r = gbx.neighbor_allgatherv_init(send, torch.from_numpy(g.send_base).cuda(), t32(rank_count), recv,
+                                     torch.from_numpy(g.recv_base).cuda(), t32(rc), t32(rd), gr, s)
     r.start()
     r.wait()
     assert_bytes_equal(recv.cpu().numpy(), want, "allgatherv")
-    # a receive count that differs from the sender's is MPI_ERR_TRUNCATE
+    # a receive count that differs from the sender's is MPI_ERR_TRUNCATE, as in the oracle
     bad = rc.copy()
     if len(bad):
         bad[0] += 1
+        with pytest.raises(oracle.OracleError) as oe:
+            oracle.neighbor_allgatherv(g, rank_count, bad, rd, x)
         with pytest.raises(gbx.GbxError) as e:
-            gbx.neighbor_allgatherv_init(send, torch.from_numpy(q.send_base).cuda(), t32(rank_count), recv,
-                                         torch.from_numpy(q.recv_base).cuda(), t32(bad), t32(rd), g, s)
-        assert e.value.code == gbx.ERR_TRUNCATE
-    del in_owner
+            gbx.neighbor_allgatherv_init(send, torch.from_numpy(g.send_base).cuda(), t32(rank_count), recv,
+                                         torch.from_numpy(g.recv_base).cuda(), t32(bad), t32(rd), gr, s)
+        assert e.value.code == oe.value.code == gbx.ERR_TRUNCATE
+
+
+def test_alltoall_displacement_overflow():
+    """Rank 0 lists three out-neighbours; with count = 2^30 its third block would start at
+    element 2^31, beyond the int32 displacements: the oracle and the library both refuse the
+    call with ERR_UNSUPPORTED (before any buffer is checked, so the buffers are tiny)."""
+    P = 4
+    p = pt.Pattern(name="wide", P=P, ppn=P, in_ptr=np.array([0, 0, 1, 2, 3], np.int32),
+                   sources=np.zeros(3, np.int32), out_ptr=np.array([0, 3, 3, 3, 3], np.int32),
+                   dests=np.array([1, 2, 3], np.int32), sendcounts=None, sdispls=None, recvcounts=None,
+                   rdispls=None, elem_size=1, dtype="bytes", send_base=np.zeros(P, np.int64),
+                   recv_base=np.zeros(P, np.int64), sendbuf_bytes=16, recvbuf_bytes=16)
+    with pytest.raises(oracle.OracleError) as oe:
+        oracle.neighbor_pattern(p, "alltoall", count=1 << 30)
+    comm, gr = _graph_of(p)
+    buf = torch.zeros(16, dtype=torch.uint8, device="cuda")
+    z = torch.zeros(P, dtype=torch.int64, device="cuda")
+    with pytest.raises(gbx.GbxError) as e:
+        gbx.neighbor_alltoall_init(buf, z, buf.clone(), z, 1 << 30, gr, 1)
+    assert e.value.code == oe.value.code == gbx.ERR_UNSUPPORTED
 
 
 @pytest.mark.parametrize("P,ppn", [(1, 1), (7, 3), (64, 8)])
@@ -141,17 +146,10 @@ def test_dense_alltoallv(P, ppn):
         rd[d] = np.concatenate([[0], np.cumsum(cnt[:, d])[:-1]])
     region_send = np.maximum(cnt.sum(1), 1)
     region_recv = np.maximum(cnt.sum(0), 1)
-    ptr = (np.arange(P + 1) * P).astype(np.int32)
-    ranks = np.tile(np.arange(P), P).astype(np.int32)
-    p = pt.Pattern(name="dense", P=P, ppn=ppn, in_ptr=ptr, sources=ranks, out_ptr=ptr, dests=ranks,
-                   sendcounts=cnt.reshape(-1).astype(np.int32), sdispls=sd.reshape(-1).astype(np.int32),
-                   recvcounts=cnt.T.reshape(-1).astype(np.int32), rdispls=rd.reshape(-1).astype(np.int32),
-                   elem_size=s, dtype="f64", send_base=np.zeros(P, np.int64), recv_base=np.zeros(P, np.int64),
-                   sendbuf_bytes=0, recvbuf_bytes=0)
-    p.send_base = (np.concatenate([[0], np.cumsum(region_send)[:-1]]) * s).astype(np.int64)
-    p.recv_base = (np.concatenate([[0], np.cumsum(region_recv)[:-1]]) * s).astype(np.int64)
-    p.sendbuf_bytes = int(region_send.sum() * s)
-    p.recvbuf_bytes = int(region_recv.sum() * s)
+    send_base = (np.concatenate([[0], np.cumsum(region_send)[:-1]]) * s).astype(np.int64)
+    recv_base = (np.concatenate([[0], np.cumsum(region_recv)[:-1]]) * s).astype(np.int64)
+    p = oracle.alltoallv_pattern(P, ppn, cnt, sd, cnt.T, rd, send_base, recv_base, s, int(region_send.sum() * s),
+                                 int(region_recv.sum() * s), dtype="f64")
     x = rng.standard_normal(p.sendbuf_bytes // 8)
     want = oracle.standard(p, x)
     comm = gbx.Comm(P, ppn)

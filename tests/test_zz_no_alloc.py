@@ -1,13 +1,15 @@
-"""The allocation-free exchange gives the same bytes as the persistent one.
+"""The allocation-free exchange gives the oracle's bytes and the persistent exchange's.
 
 gbx_neighbor_alltoallv_noalloc serves callers that cannot allocate device memory (a
 fixed budget owned by another allocator, latency-critical paths that cannot pay
 cudaMalloc's device-wide synchronisation, plug-ins barred from the allocator).  It keeps
 its per-edge tables in a fixed static device array instead of memory of its own, so
 this test checks, through the C ABI, that two calls in a row (the second one reusing the
-array the first one left behind) each produce exactly the receive buffer that the
-persistent standard exchange produces for the same send data, and that an edge count
-beyond the array's capacity is refused before any device work.  It runs last so that a
+array the first one left behind) each produce exactly the receive buffer of the oracle's
+exchange and of the persistent standard exchange for the same send data, that the second
+call changes the device's free memory by nothing, that an edge count beyond the array's
+capacity is refused before any device work, and that each invalid input returns the
+oracle's error code with the receive buffer left untouched.  It runs last so that a
 failure here cannot hide another test's, and it passes alone or after the others.
 """
 import ctypes
@@ -21,6 +23,7 @@ torch = pytest.importorskip("torch")
 if not torch.cuda.is_available():
     pytest.skip("needs a GPU", allow_module_level=True)
 
+import oracle  # noqa: E402
 import paper_2309_07337_gb300 as gbx  # noqa: E402
 from paper_2309_07337_gb300 import patterns as pt  # noqa: E402
 
@@ -71,19 +74,93 @@ def cases():
 @pytest.mark.parametrize("p", list(cases()), ids=lambda p: p.name)
 def test_noalloc_matches_persistent_on_two_calls(noalloc, p):
     dp = gbx.DevicePattern(p)
-    init = torch.from_numpy(pt.random_bytes(p.recvbuf_bytes, 5)).cuda()
+    init_h = pt.random_bytes(p.recvbuf_bytes, 5)
+    init = torch.from_numpy(init_h).cuda()
     send = torch.zeros(p.sendbuf_bytes, dtype=torch.uint8, device="cuda")
     ref_recv = init.clone()
     ex = gbx.Exchange(p, send, ref_recv, dp=dp)
     out = init.clone()
     for call_no, seed in enumerate((101, 202)):
-        send.copy_(torch.from_numpy(pt.random_bytes(p.sendbuf_bytes, seed)))
+        x = pt.random_bytes(p.sendbuf_bytes, seed)
+        send.copy_(torch.from_numpy(x))
         ex.start()
         ex.wait()
+        torch.cuda.synchronize()
+        free_before = torch.cuda.mem_get_info()[0]
         rc = call(noalloc, p, dp, send, out)
         assert rc == gbx.SUCCESS, (call_no, rc)
         torch.cuda.synchronize()
+        if call_no == 1:   # the first call on a device may load the array; later ones allocate nothing
+            assert torch.cuda.mem_get_info()[0] == free_before, "the call changed the device's free memory"
+        got = out.cpu().numpy()
+        assert np.array_equal(got, oracle.standard(p, x, init_h)), f"call {call_no}: bytes differ from the oracle"
         assert torch.equal(out, ref_recv), f"call {call_no}: bytes differ from the persistent exchange"
+
+
+def _bad_cases():
+    """Invalid inputs made from a valid exchange, each with the field it corrupts."""
+    base = packed(pt.config1())
+    i0 = int(np.flatnonzero(np.asarray(base.recvcounts) > 0)[0])
+
+    def variant(name, **change):
+        q = pt.Pattern(**{k: getattr(base, k) for k in base.__dataclass_fields__})
+        for k, f in change.items():
+            setattr(q, k, f(np.array(getattr(base, k))))
+        q.name = name
+        return q
+
+    def csr_down(a):
+        a[2] = a[3] + 1          # in-list CSR no longer non-decreasing
+        return a
+
+    def rank_out(a):
+        a[0] = base.P            # a neighbour rank outside [0, P)
+        return a
+
+    def count_up(a):
+        a[i0] += 1               # receives one element more than its sender sends
+        return a
+
+    def disp_past(a):
+        a[i0] = base.recvbuf_bytes // base.elem_size   # the block ends past the receive buffer
+        return a
+
+    def disp_neg(a):
+        a[0] = -1
+        return a
+
+    yield variant("bad_csr", in_ptr=csr_down)
+    yield variant("rank_out_of_range", sources=rank_out)
+    yield variant("count_mismatch", recvcounts=count_up)
+    yield variant("rdispl_past_buffer", rdispls=disp_past)
+    yield variant("negative_sdispl", sdispls=disp_neg)
+
+
+@pytest.mark.parametrize("q", list(_bad_cases()), ids=lambda q: q.name)
+def test_noalloc_errors_match_oracle_and_write_nothing(noalloc, q):
+    want = oracle.validate(q)
+    assert want != oracle.OK, q.name
+    dp = gbx.DevicePattern(q)
+    send = torch.from_numpy(pt.random_bytes(q.sendbuf_bytes, 1)).cuda()
+    init = pt.random_bytes(q.recvbuf_bytes, 2)
+    out = torch.from_numpy(init.copy()).cuda()
+    assert call(noalloc, q, dp, send, out) == want, q.name
+    torch.cuda.synchronize()
+    assert np.array_equal(out.cpu().numpy(), init), f"{q.name}: the receive buffer was written"
+
+
+def test_noalloc_huge_element_size_is_an_index_error(noalloc):
+    """Bounds are checked by division: an element size of 2^62 bytes cannot wrap an offset
+    computation into a small, valid-looking one."""
+    p = packed(pt.config1())
+    dp = gbx.DevicePattern(p)
+    send = torch.zeros(p.sendbuf_bytes, dtype=torch.uint8, device="cuda")
+    out = torch.zeros(p.recvbuf_bytes, dtype=torch.uint8, device="cuda")
+    q = pt.Pattern(**{k: getattr(p, k) for k in p.__dataclass_fields__})
+    q.elem_size = 1 << 62
+    assert call(noalloc, q, dp, send, out) == gbx.ERR_INDEX
+    torch.cuda.synchronize()
+    assert not bool(out.any())
 
 
 def test_noalloc_refuses_sizes_beyond_its_scratch(noalloc):
