@@ -79,6 +79,14 @@ def parse_args():
                    help="instead of the step: message-size sweep, comps 1..16 x block edge 8..32 at P=4096")
     a.add_argument("--bwd-forms", action="store_true",
                    help="time the backward in each program shape (own JSON line)")
+    a.add_argument("--spmv", action="store_true",
+                   help="instead of the step: the SpMV halo exchange (2^20 rows, P=1024) standard vs locality")
+    a.add_argument("--batched", action="store_true",
+                   help="instead of the step: the uneven 64-pattern batch, plain vs startall")
+    a.add_argument("--reps", type=int, default=20, help="repetitions of the --spmv / --batched timings")
+    a.add_argument("--count", type=int, default=64, help="patterns of the --batched batch (64 = the workload)")
+    a.add_argument("--info", default="", help="extra info keys for the timed requests (e.g. form=10 to pin a "
+                                             "copy form for a profiler run)")
     a.add_argument("--faces", action="store_true",
                    help="instead of the step: standard exchange per face / edge+corner subset of the 512^3 "
                         "stencil, with the 128-byte-line DRAM floor of each")
@@ -91,11 +99,13 @@ def workload(edge=32):
     return p
 
 
-def workload_config(p, edge):
+def workload_config(p, edge, world=1):
+    """The workload's description, the same dict in both arms."""
     return {"workload": f"stencil3d_27pt_{16 * edge}^3_P4096_ppn64_8xf64",
             "grid": [16 * edge] * 3, "ranks": 4096, "ranks_per_node": 64, "elem_bytes": p.elem_size,
             "V": p.volume, "E": p.n_edges, "l2": "inputs larger than L2 (8.59 GB field), no flush"
-            if edge == 32 else "reduced size", "seed": pt.SEED + 5}
+            if edge == 32 else "reduced size", "seed": pt.SEED + 5,
+            "parallelism": "replicas" if world > 1 else "single"}
 
 
 def measured_peaks():
@@ -138,10 +148,22 @@ class Clocks:
         self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
         try:
             self.p = subprocess.Popen(["nvidia-smi", f"--id={index}", f"--query-gpu={self.Q}",
-                                       "--format=csv,noheader,nounits", "-lms", "100"],
+                                       "--format=csv,noheader,nounits", "-lms", "20"],
                                       stdout=self.f, stderr=subprocess.DEVNULL)
         except Exception:
             self.p = None
+
+    def ready(self, timeout_s=3.0):
+        """Waits (at most timeout_s) until nvidia-smi has written its first sample, so that
+        the samples cover the region timed next rather than the tool's start-up."""
+        if self.p is None:
+            return
+        t0 = time.perf_counter()
+        while time.perf_counter() - t0 < timeout_s:
+            self.f.flush()
+            if os.path.getsize(self.f.name) > 0:
+                return
+            time.sleep(0.01)
 
     def stop(self):
         if self.p is None:
@@ -239,7 +261,7 @@ def distinct_sources(q):
         (np.arange(int(cnt.sum())) - np.repeat(np.cumsum(cnt) - cnt, cnt))
     el = q.send_idx[slot] if q.send_idx is not None else slot - np.repeat(q.send_slot_ptr[owner], cnt)
     off = np.repeat(q.send_base[owner], cnt) + el.astype(np.int64) * q.elem_size
-    return int(len(np.unique(off)))
+    return int(len(sorted_unique(off)))
 
 
 # ---------------------------------------------------------------- reference arm
@@ -268,7 +290,7 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": workload_config(p, args.edge),
+            "data": "synthetic", "config": workload_config(p, args.edge, int(os.environ.get("WORLD_SIZE", "1"))),
             "cpu_baseline": {"value": val, "unit": UNIT, "cores": n, "kind": "oracle",
                              "sample": f"the three exchanges over all {p.P} receivers each step, split into {n} "
                                        f"receiver slices, one oracle process per core"},
@@ -365,9 +387,9 @@ def run_ours(args):
     grad_field = torch.zeros_like(field)
     dp = gbx.DevicePattern(p)
     t_init = time.perf_counter()
-    ex_std = gbx.Exchange(p, field, halo_std, "standard", dp=dp)
-    ex_loc = gbx.Exchange(p, field, halo_loc, "locality", dp=dp, graph=ex_std.graph)
-    bwd = gbx.backward_init(ex_std.request, grad_halo, grad_field)
+    ex_std = gbx.Exchange(p, field, halo_std, "standard", dp=dp, info=args.info)
+    ex_loc = gbx.Exchange(p, field, halo_loc, "locality", dp=dp, graph=ex_std.graph, info=args.info)
+    bwd = gbx.backward_init(ex_std.request, grad_halo, grad_field, info=args.info)
     torch.cuda.synchronize()
     t_init = time.perf_counter() - t_init
     reqs = [ex_std.request, ex_loc.request, bwd]
@@ -391,6 +413,7 @@ def run_ours(args):
     K = args.steps
     evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(K)]
     clocks = Clocks(local)
+    clocks.ready()
     barrier()
     torch.cuda.nvtx.range_push("timed")
     t0 = torch.cuda.Event(enable_timing=True)
@@ -422,19 +445,29 @@ def run_ours(args):
     forms["locality"].update({"U": infos[1]["U"], "node_pairs": infos[1]["node_pairs"],
                               "V_direct": infos[1]["V_direct"], "V_inter": infos[1]["V_inter"]})
     forms["backward"].update({"rows": rows, "terms": infos[2]["terms"]})
+    bfl = bwd_line_floor(p, infos[2])
+    forms["backward"].update({"line_floor_bytes": bfl["total"], "line_floor": bfl,
+                              "frac_of_line_floor": bfl["total"] / (per[2] * 1e-3) / 1e9 / peak})
+    for name, info in zip(("standard", "locality", "backward"), infos):
+        forms[name]["copy_forms"] = form_names(info)
     # dominant kernel: the standard exchange's single move kernel
     std_ms = per[0]
     achieved = infos[0]["algo_bytes"] / (std_ms * 1e-3) / 1e9
+    fl = line_floor(p)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": profiled_traffic("gbx_copy_kernel_std_stencil512"),
-                "kernel": "gbx_copy_pipe_kernel<16,1,1> (standard exchange, one launch per start)",
-                "peak_source": f"{peak_kind} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"}
+                "kernel": f"the standard exchange's move kernel ({form_names(infos[0])}, one launch per start)",
+                "peak_source": f"{peak_kind} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
+                "line_floor_bytes": fl["total"], "frac_of_line_floor": fl["total"] / (std_ms * 1e-3) / 1e9 / peak,
+                "traffic_note": "DRAM traffic above the algorithmic bytes is the 128-byte-line floor of the x-face "
+                                "points (isolated 64-byte elements 2 KB apart, each fetched as a whole line): "
+                                "line_floor_bytes counts the lines the exchange must touch"}
     launches = sum(i["launches"] for i in infos) * K
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": dict(workload_config(p, args.edge), parallelism="replicas" if world > 1 else "single"),
+            "config": workload_config(p, args.edge, world),
             "roofline": roofline, "gpu_launches": launches, "clocks": clk, "forms": forms,
             "init_s": t_init}
 
@@ -580,20 +613,46 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
-def _time_loop(torch, fn, reps):
-    fn()
-    torch.cuda.synchronize()
-    t = time.perf_counter()
+def paired(torch, fa, fb, reps=24, warm=3, flush=None):
+    """Times two ways of doing the same work interleaved (a, b, a, b, ...), so that both see
+    the same clocks and the same state: each repetition starts from an idle device (and a
+    flushed L2 when `flush` is given) and is bracketed by CUDA events on the current stream,
+    host waits included.  Returns the spread of a, of b and of the per-pair ratio a / b."""
+    for _ in range(warm):
+        fa()
+        fb()
+    ta, tb = [], []
     for _ in range(reps):
-        fn()
-    torch.cuda.synchronize()
-    return (time.perf_counter() - t) / reps * 1e3
+        for f, ts in ((fa, ta), (fb, tb)):
+            if flush is not None:
+                flush.fill_(1)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            f()
+            e1.record()
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+    return spread(ta), spread(tb), spread([a / b for a, b in zip(ta, tb)])
 
 
-def _partitioned(gbx, torch, p, field, ex_std, n=8, reps=10):
+def factor_entry(name_a, name_b, res):
+    """JSON of a paired timing: both spreads and the factor a / b with its 10th-90th
+    percentile band over the repetitions."""
+    a, b, r = res
+    return {f"{name_a}_ms": a, f"{name_b}_ms": b, "speedup": r["median"], "speedup_p10": r["p10"],
+            "speedup_p90": r["p90"], "reps": r["n"]}
+
+
+def _partitioned(gbx, torch, p, field, ex_std, n=8):
     pc = np.array([p.send_base[k * p.P // n] for k in range(n)] + [p.sendbuf_bytes], np.int64)
     rc = np.array([p.recv_base[k * p.P // n] for k in range(n)] + [p.recvbuf_bytes], np.int64)
-    pr = gbx.partitioned_init(ex_std.request, pc, rc)
+    # the partitions' moves leave four SMs to the producer (a persistent move grid would
+    # otherwise hold every SM until it ends, and the next slab's production would queue behind it)
+    import torch as _t
+    sms = _t.cuda.get_device_properties(0).multi_processor_count
+    pr = gbx.partitioned_init(ex_std.request, pc, rc, info=f"max_ctas={2 * (sms - 4)}")
     base = field.clone()
     lo = [int(pc[k]) // 8 for k in range(n + 1)]
     prod, xch = torch.cuda.Stream(), torch.cuda.Stream()
@@ -634,27 +693,22 @@ def _partitioned(gbx, torch, p, field, ex_std, n=8, reps=10):
             for k in range(n):
                 produce(k)
 
-    def timed(fn):
-        for _ in range(3):
-            fn()
-        torch.cuda.synchronize()
-        ts = []
-        for _ in range(reps):
-            torch.cuda.synchronize()
-            t = time.perf_counter()
-            fn()
-            torch.cuda.synchronize()
-            ts.append((time.perf_counter() - t) * 1e3)
-        return statistics.median(ts)
-    res = {"slabs": n, "launches_per_epoch": pr.info()["launches"]}
+    res = {"slabs": n, "launches_per_epoch": pr.info()["launches"], "move_grid_cap": 2 * (sms - 4),
+           "timing": "interleaved pairs (sequential, early-bird), CUDA events, median and p10/p90 of 24"}
     what = {"hbm": "one elementwise kernel per slab rewriting 512 ranks' blocks (1.07 GB read + write)",
             "compute": "one 8192x4096x8192 bf16 GEMM per slab (0.55 TFLOP)",
             "latency": "one single-block kernel per slab busy for 600k cycles (~0.3 ms), most SMs idle"}
     for k_ in ("hbm", "compute", "latency"):
         kind[0] = k_
-        r = {"sequential_ms": timed(sequential), "early_bird_ms": timed(early_bird),
-             "produce_only_ms": timed(produce_only)}
-        r["speedup"] = r["sequential_ms"] / r["early_bird_ms"]
+        r = factor_entry("sequential", "early_bird", paired(torch, sequential, early_bird, reps=24))
+        ts = []
+        for _ in range(12):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            produce_only()
+            torch.cuda.synchronize()
+            ts.append((time.perf_counter() - t0) * 1e3)
+        r["produce_only_ms"] = spread(ts)
         r["producer"] = what[k_]
         res[k_] = r
     del pr, base, ga, gb, gc
@@ -758,50 +812,13 @@ def extras(gbx, torch, p, field, halo, grad_halo, grad_field, dp, ex_std, bwd):
     def fused():
         gbx.startall([ex_std.request, bwd])
         gbx.waitall([ex_std.request, bwd])
-    tp = _time_loop(torch, plain, 10)
-    tf = _time_loop(torch, fused, 10)
-    out["fwd_bwd_cfg5"] = {"plain_ms": tp, "fused_ms": tf, "speedup": tp / tf,
-                           "plain": "eager launches, start+wait per exchange",
-                           "fused": "startall of forward+backward: one CUDA graph, fused launches"}
+    out["fwd_bwd_cfg5"] = dict(factor_entry("plain", "fused", paired(torch, plain, fused, reps=24)),
+                               plain="eager launches, start+wait per exchange",
+                               fused="startall of forward+backward: one CUDA graph, fused launches",
+                               timing="interleaved pairs, CUDA events, median and p10/p90 of 24")
     del plain_f, plain_b
     # batched uneven patterns (config 3) vs plain
-    t = time.perf_counter()
-    pats = pt.config3_torch(64, device="cuda")
-    gen_s = time.perf_counter() - t
-    bufs, g_reqs, p_reqs = [], [], []
-    for j, q in enumerate(pats):
-        n = q.sendbuf_bytes // (8 if q.dtype == "f64" else 4)
-        sb = torch.randn(n, device="cuda", dtype=torch.float64 if q.dtype == "f64" else torch.float32)
-        rb = torch.zeros(q.recvbuf_bytes // sb.element_size(), device="cuda", dtype=sb.dtype)
-        rb2 = torch.zeros_like(rb)
-        dq = gbx.DevicePattern(q)
-        e1 = gbx.Exchange(q, sb, rb, "standard", dp=dq)
-        e2 = gbx.Exchange(q, sb, rb2, "standard", info="graph=0", dp=dq, graph=e1.graph)
-        bufs.append((sb, rb, rb2, e1, e2))
-        g_reqs.append(e1.request)
-        p_reqs.append(e2.request)
-    Vtot = sum(q.volume for q in pats)
-    Btot = sum(q.user_bytes() for q in pats)
-
-    def plain3():
-        for r in p_reqs:
-            r.start()
-            r.wait()
-
-    def batched3():
-        gbx.startall(g_reqs)
-        gbx.waitall(g_reqs)
-    tp = _time_loop(torch, plain3, 5)
-    tb = _time_loop(torch, batched3, 5)
-    same = all(torch.equal(b[1], b[2]) for b in bufs)
-    out["batched_cfg3"] = {"patterns": len(pats), "V_total": Vtot, "plain_ms": tp, "batched_ms": tb,
-                           "speedup": tp / tb, "batched_user_GBps": Btot / (tb * 1e-3) / 1e9,
-                           "identical_results": same, "generation_s": gen_s,
-                           "dtypes": {d: sum(1 for q in pats if q.dtype == d) for d in ("f32", "f64")},
-                           "plain": "eager launches, start+wait per pattern",
-                           "batched": "startall of 64 requests: one CUDA graph, one fused launch per phase"}
-    del bufs, g_reqs, p_reqs
-    torch.cuda.empty_cache()
+    out["batched_cfg3"] = _batched(gbx, torch, measured_peaks()[0], 24, nvtx=False)
     # fused forward + backward on the differentiable SpMV halo (config 4: 2^20 rows, fp32)
     q4 = pt.config4()
     dq4 = gbx.DevicePattern(q4)
@@ -823,11 +840,10 @@ def extras(gbx, torch, p, field, halo, grad_halo, grad_field, dp, ex_std, bwd):
     def fused4():
         gbx.startall([f_graph.request, b_graph])
         gbx.waitall([f_graph.request, b_graph])
-    tp = _time_loop(torch, plain4, 50)
-    tf = _time_loop(torch, fused4, 50)
-    out["fwd_bwd_cfg4"] = {"plain_ms": tp, "fused_ms": tf, "speedup": tp / tf, "V": q4.volume,
-                           "plain": "eager launches, start+wait per exchange",
-                           "fused": "startall of forward+backward: one CUDA graph"}
+    out["fwd_bwd_cfg4"] = dict(factor_entry("plain", "fused", paired(torch, plain4, fused4, reps=48)), V=q4.volume,
+                               plain="eager launches, start+wait per exchange",
+                               fused="startall of forward+backward: one CUDA graph",
+                               timing="interleaved pairs, CUDA events, median and p10/p90 of 48")
     del f_graph, b_graph, f_plain, b_plain
     # the same stencil exchange through per-edge datatypes (neighbourhood all-to-all-w) over the
     # point-major field and over a component-major copy of it, L2 flushed between repetitions
@@ -873,21 +889,14 @@ def extras(gbx, torch, p, field, halo, grad_halo, grad_field, dp, ex_std, bwd):
     a = gbx.Exchange(q, xs, r1, "standard", dp=dq)
     b = gbx.Exchange(q, xs, r2, "locality", dp=dq, graph=a.graph)
     res = {}
+    peak = measured_peaks()[0]
     for name, ex in (("standard", a), ("locality", b)):
-        ts = []
-        for _ in range(10):
-            flush.fill_(1)
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record()
-            ex.request.start()
-            e1.record()
-            ex.request.wait()
-            e1.synchronize()
-            ts.append(e0.elapsed_time(e1))
-        ms = statistics.median(ts)
-        res[name] = {"ms": ms, "user_GBps": q.user_bytes() / (ms * 1e-3) / 1e9,
-                     "algo_bytes": ex.info()["algo_bytes"]}
+        st = spread(_cold_times(torch, ex.request.start, ex.request.wait, flush, reps=20))
+        ms = st["median"]
+        info = ex.info()
+        res[name] = {"ms": st, "user_GBps": q.user_bytes() / (ms * 1e-3) / 1e9, "algo_bytes": info["algo_bytes"],
+                     "frac_of_measured_hbm": info["algo_bytes"] / (ms * 1e-3) / 1e9 / peak,
+                     "copy_forms": form_names(info)}
     res["identical"] = bool(torch.equal(r1, r2))
     res["V"] = q.volume
     res["E"] = q.n_edges
@@ -898,23 +907,146 @@ def extras(gbx, torch, p, field, halo, grad_halo, grad_field, dp, ex_std, bwd):
     return out
 
 
-def _cold_ms(torch, req, flush, reps=20, warm=3):
-    """Median CUDA-event time of start() with L2 flushed (a 256 MB write) before each rep."""
+def _cold_times(torch, start, wait, flush, reps=20, warm=3):
+    """CUDA-event times (ms) of `start()` over `reps` repetitions, L2 flushed (a 256 MB
+    write) before each; `wait()` completes each one outside the timed interval."""
     for _ in range(warm):
-        req.start()
-        req.wait()
+        start()
+        wait()
     ts = []
     for _ in range(reps):
-        flush.fill_(1)
+        if flush is not None:
+            flush.fill_(1)
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record()
-        req.start()
+        start()
         e1.record()
-        req.wait()
+        wait()
         e1.synchronize()
         ts.append(e0.elapsed_time(e1))
-    return statistics.median(ts)
+    return ts
+
+
+def _cold_ms(torch, req, flush, reps=20, warm=3):
+    """Median CUDA-event time of start() with L2 flushed (a 256 MB write) before each rep."""
+    return statistics.median(_cold_times(torch, req.start, req.wait, flush, reps, warm))
+
+
+def spread(ts):
+    """median, 10th and 90th percentile of a list of times."""
+    q = np.percentile(np.asarray(ts, dtype=np.float64), [10, 50, 90])
+    return {"median": float(q[1]), "p10": float(q[0]), "p90": float(q[2]), "n": len(ts)}
+
+
+def run_spmv(args):
+    """The SpMV halo exchange (2^20 rows, P = 1024 at 32 per node, 20 nnz per row, fp64 x),
+    standard and locality forms, L2 flushed before each of 20 repetitions; then one more
+    start of each inside an NVTX range (cfg2_standard, cfg2_locality) for ncu --nvtx-include."""
+    import torch
+    import paper_2309_07337_gb300 as gbx
+    peak, peak_kind = measured_peaks()
+    q = pt.config2()
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(pt.SEED + 2)
+    xs = torch.randn(q.meta["n"], device="cuda", dtype=torch.float64, generator=gen)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    dq = gbx.DevicePattern(q)
+    outs = {}
+    res = {"workload": "spmv_halo_2^20rows_P1024_ppn32_nnz20_f64", "V": q.volume, "E": q.n_edges,
+           "l2": "flushed (256 MB write) before every repetition", "peak_GBps": peak, "peak_kind": peak_kind}
+    graph = None
+    keep = []
+    for name in ("standard", "locality"):
+        outs[name] = torch.zeros(q.recvbuf_bytes // 8, device="cuda", dtype=torch.float64)
+        ex = gbx.Exchange(q, xs, outs[name], name, dp=dq, graph=graph, info=args.info)
+        graph = ex.graph
+        st = spread(_cold_times(torch, ex.start, ex.wait, flush, reps=args.reps))
+        info = ex.info()
+        ms = st["median"]
+        res[name] = {"ms": st, "user_GBps": q.user_bytes() / (ms * 1e-3) / 1e9, "algo_bytes": info["algo_bytes"],
+                     "algo_GBps": info["algo_bytes"] / (ms * 1e-3) / 1e9,
+                     "frac_of_measured_hbm": info["algo_bytes"] / (ms * 1e-3) / 1e9 / peak,
+                     "launches": info["launches"], "vec": info["vec_bytes"], "block": info["block"],
+                     "copy_forms": [COPY_FORM_NAMES.get(f, str(f)) for f in range(16) if info["copy_forms"] >> f & 1],
+                     "U": info["U"], "node_pairs": info["node_pairs"]}
+        flush.fill_(1)
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_push(f"cfg2_{name}")
+        ex.start()
+        torch.cuda.nvtx.range_pop()
+        ex.wait()
+        keep.append(ex)   # the locality request shares the standard one's graph
+    res["identical"] = bool(torch.equal(outs["standard"], outs["locality"]))
+    print(json.dumps(res))
+
+
+def run_batched(args):
+    """The uneven batch (64 SpMV halo patterns, P 64..1024, 2^14..2^20 rows, 8..32 nnz per
+    row, fp32 or fp64): one start+wait per pattern (eager launches) against gbx_startall of
+    all 64 (one CUDA graph), each timed over `reps` repetitions; then one more batched start
+    inside the NVTX range cfg3_batched for ncu --nvtx-include.  The batch's buffers exceed L2."""
+    import torch
+    import paper_2309_07337_gb300 as gbx
+    peak, peak_kind = measured_peaks()
+    out = _batched(gbx, torch, peak, args.reps, count=args.count, info=args.info)
+    print(json.dumps(out))
+
+
+def _batched(gbx, torch, peak, reps, nvtx=True, count=64, info=""):
+    t = time.perf_counter()
+    pats = pt.config3_torch(count, device="cuda")
+    gen_s = time.perf_counter() - t
+    bufs, g_reqs, p_reqs = [], [], []
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(pt.SEED + 3)
+    for q in pats:
+        dt = torch.float64 if q.dtype == "f64" else torch.float32
+        sb = torch.randn(q.sendbuf_bytes // (8 if q.dtype == "f64" else 4), device="cuda", dtype=dt, generator=gen)
+        rb = torch.zeros(q.recvbuf_bytes // sb.element_size(), device="cuda", dtype=dt)
+        rb2 = torch.zeros_like(rb)
+        dq = gbx.DevicePattern(q)
+        e1 = gbx.Exchange(q, sb, rb, "standard", dp=dq, info=info)
+        e2 = gbx.Exchange(q, sb, rb2, "standard", info="graph=0" + (";" + info if info else ""), dp=dq,
+                          graph=e1.graph)
+        bufs.append((sb, rb, rb2, e1, e2))
+        g_reqs.append(e1.request)
+        p_reqs.append(e2.request)
+    Vtot = sum(q.volume for q in pats)
+    Btot = sum(q.user_bytes() for q in pats)
+    algo = sum(r.info()["algo_bytes"] for r in g_reqs)
+
+    def plain3():
+        for r in p_reqs:
+            r.start()
+            r.wait()
+
+    def batched3():
+        gbx.startall(g_reqs)
+        gbx.waitall(g_reqs)
+    tp, tb, ratio = paired(torch, plain3, batched3, reps=reps)
+    same = all(torch.equal(b[1], b[2]) for b in bufs)
+    if nvtx:
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_push("cfg3_batched")
+        gbx.startall(g_reqs)
+        torch.cuda.nvtx.range_pop()
+        gbx.waitall(g_reqs)
+    ms = tb["median"]
+    res = {"patterns": len(pats), "V_total": Vtot, "user_bytes": Btot, "algo_bytes": algo,
+           "plain_ms": tp, "batched_ms": tb, "speedup": ratio["median"], "speedup_p10": ratio["p10"],
+           "speedup_p90": ratio["p90"],
+           "batched_user_GBps": Btot / (ms * 1e-3) / 1e9, "batched_algo_GBps": algo / (ms * 1e-3) / 1e9,
+           "frac_of_measured_hbm": algo / (ms * 1e-3) / 1e9 / peak,
+           "identical_results": same, "generation_s": gen_s,
+           "dtypes": {d: sum(1 for q in pats if q.dtype == d) for d in ("f32", "f64")},
+           "plain": "eager launches, start+wait per pattern (host wait each)",
+           "batched": "startall of 64 requests: one CUDA graph, one fused launch per kernel class",
+           "timing": "interleaved pairs (plain, batched), CUDA events around each including the host waits; "
+                     "median and p10/p90; the batch's buffers exceed L2"}
+    del bufs, g_reqs, p_reqs
+    torch.cuda.empty_cache()
+    return res
 
 
 def run_sweep(args):
@@ -955,6 +1087,12 @@ def run_sweep(args):
                       "l2": "flushed (256 MB write) before every repetition; median of 20", "rows": rows}))
 
 
+def sorted_unique(a):
+    """np.unique by a sort and a neighbour test (np.unique is far slower on 10^7 values)."""
+    a = np.sort(np.asarray(a), kind="stable")
+    return a[np.concatenate([[True], a[1:] != a[:-1]])] if len(a) else a
+
+
 def line_floor(p):
     """DRAM bytes a standard exchange of `p` cannot avoid when memory moves in 128-byte
     lines: every 128-byte line holding a sent element is read once, the receive buffer is
@@ -967,9 +1105,35 @@ def line_floor(p):
     r = np.repeat(owner, sc)
     el = slot if p.send_idx is None else np.asarray(p.send_idx)[np.asarray(p.send_slot_ptr)[r] + slot]
     off = np.asarray(p.send_base)[r] + el.astype(np.int64) * p.elem_size
-    lines = np.unique(np.concatenate([off >> 7, (off + p.elem_size - 1) >> 7]))
+    lines = sorted_unique(np.concatenate([off >> 7, (off + p.elem_size - 1) >> 7]))
     return {"read_lines_bytes": int(len(lines)) * 128, "index_bytes": 4 * V, "write_bytes": V * p.elem_size,
             "total": int(len(lines)) * 128 + 4 * V + V * p.elem_size}
+
+
+def bwd_line_floor(p, info):
+    """DRAM bytes the standard-order reverse exchange of `p` cannot avoid when memory moves
+    in 128-byte lines: every incoming gradient is read once (the receive buffer, in whole
+    lines), the index and record bytes of the program are read, and every 128-byte line
+    holding a written source element is written once (an isolated 64-byte x-face gradient
+    costs a whole line, the mirror image of the forward's reads)."""
+    sc = np.asarray(p.sendcounts, dtype=np.int64)
+    owner = np.repeat(np.arange(p.P), np.diff(np.asarray(p.out_ptr)))
+    V = int(sc.sum())
+    first = np.cumsum(sc) - sc
+    slot = np.repeat(np.asarray(p.sdispls, dtype=np.int64), sc) + (np.arange(V) - np.repeat(first, sc))
+    r = np.repeat(owner, sc)
+    el = slot if p.send_idx is None else np.asarray(p.send_idx)[np.asarray(p.send_slot_ptr)[r] + slot]
+    off = sorted_unique(np.asarray(p.send_base)[r] + el.astype(np.int64) * p.elem_size)
+    lines = sorted_unique(np.concatenate([off >> 7, (off + p.elem_size - 1) >> 7]))
+    read = V * p.elem_size
+    index = max(0, int(info["algo_bytes"]) - read - len(off) * p.elem_size)
+    return {"read_bytes": read, "index_bytes": index, "write_lines_bytes": int(len(lines)) * 128,
+            "rows": int(len(off)), "total": read + index + int(len(lines)) * 128}
+
+
+def form_names(info):
+    """The copy forms a request's program runs in, by name."""
+    return [COPY_FORM_NAMES.get(f, str(f)) for f in range(16) if info["copy_forms"] >> f & 1]
 
 
 def run_faces(args):
@@ -1025,7 +1189,7 @@ def run_faces(args):
 
 
 COPY_FORM_NAMES = {0: "segments", 1: "gather", 3: "two-index", 5: "gather pipelined", 7: "two-index pipelined",
-                   8: "bulk pieces", 9: "scatter windows"}
+                   8: "bulk pieces", 9: "scatter windows", 10: "gather streamed", 11: "two-index streamed"}
 
 
 def run_bwd_forms(args):
@@ -1095,6 +1259,10 @@ def main():
         run_sweep(args)
     elif args.faces:
         run_faces(args)
+    elif args.spmv:
+        run_spmv(args)
+    elif args.batched:
+        run_batched(args)
     elif args.bwd_forms:
         run_bwd_forms(args)
     else:
