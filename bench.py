@@ -75,6 +75,9 @@ def parse_args():
     a.add_argument("--no-e2e", action="store_true")
     a.add_argument("--no-cpu", action="store_true")
     a.add_argument("--edge", type=int, default=32, help="block edge (32 = the 512^3 workload)")
+    a.add_argument("--ranks", type=int, default=16, help="ranks per dimension (16 = the workload; 8 keeps the "
+                                                         "32^3 blocks of the 512^3 case on a 256^3 grid, for "
+                                                         "counter captures of a few GB)")
     a.add_argument("--sweep", action="store_true",
                    help="instead of the step: message-size sweep, comps 1..16 x block edge 8..32 at P=4096")
     a.add_argument("--bwd-forms", action="store_true",
@@ -94,17 +97,19 @@ def parse_args():
 
 
 # ------------------------------------------------------------------- helpers
-def workload(edge=32):
-    p = pt.config5(edge=edge)
+def workload(edge=32, ranks=16):
+    p = pt.config5(edge=edge, R=ranks)
     return p
 
 
-def workload_config(p, edge, world=1):
+def workload_config(p, edge, world=1, ranks=16):
     """The workload's description, the same dict in both arms."""
-    return {"workload": f"stencil3d_27pt_{16 * edge}^3_P4096_ppn64_8xf64",
-            "grid": [16 * edge] * 3, "ranks": 4096, "ranks_per_node": 64, "elem_bytes": p.elem_size,
+    g = ranks * edge
+    full = edge == 32 and ranks == 16
+    return {"workload": f"stencil3d_27pt_{g}^3_P{ranks ** 3}_ppn64_8xf64",
+            "grid": [g] * 3, "ranks": ranks ** 3, "ranks_per_node": 64, "elem_bytes": p.elem_size,
             "V": p.volume, "E": p.n_edges, "l2": "inputs larger than L2 (8.59 GB field), no flush"
-            if edge == 32 else "reduced size", "seed": pt.SEED + 5,
+            if full else "reduced size", "seed": pt.SEED + 5,
             "parallelism": "replicas" if world > 1 else "single"}
 
 
@@ -271,7 +276,7 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    p = workload(args.edge)
+    p = workload(args.edge, args.ranks)
     x = pt.stencil_field(p, pt.SEED + 5)
     g = np.random.default_rng(pt.SEED + 6).standard_normal(p.recvbuf_bytes // 8)
     pool = CpuPool(p, x, g, max(1, len(os.sched_getaffinity(0))))
@@ -290,7 +295,8 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": workload_config(p, args.edge, int(os.environ.get("WORLD_SIZE", "1"))),
+            "data": "synthetic",
+            "config": workload_config(p, args.edge, int(os.environ.get("WORLD_SIZE", "1")), args.ranks),
             "cpu_baseline": {"value": val, "unit": UNIT, "cores": n, "kind": "oracle",
                              "sample": f"the three exchanges over all {p.P} receivers each step, split into {n} "
                                        f"receiver slices, one oracle process per core"},
@@ -357,7 +363,7 @@ def run_ours(args):
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
-    p = workload(args.edge)
+    p = workload(args.edge, args.ranks)
     x = pt.stencil_field(p, pt.SEED + 5)                          # host fp64
     g_cpu = np.random.default_rng(pt.SEED + 6).standard_normal(p.recvbuf_bytes // 8)
     cpu_pool = None
@@ -467,7 +473,7 @@ def run_ours(args):
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": workload_config(p, args.edge, world),
+            "config": workload_config(p, args.edge, world, args.ranks),
             "roofline": roofline, "gpu_launches": launches, "clocks": clk, "forms": forms,
             "init_s": t_init}
 
@@ -1144,7 +1150,8 @@ def run_faces(args):
     import torch
     import paper_2309_07337_gb300 as gbx
     peak, peak_kind = measured_peaks()
-    g = 16 * args.edge
+    R = args.ranks
+    g = R * args.edge
     gen = torch.Generator(device="cuda")
     gen.manual_seed(pt.SEED + 5)
     field = torch.rand(g ** 3 * 8, dtype=torch.float64, device="cuda", generator=gen)
@@ -1154,7 +1161,7 @@ def run_faces(args):
              ("edges_corners", [d for d in dirs_all if sum(map(abs, d)) >= 2])]
     rows = []
     for name, dirs in cases:
-        p = pt.stencil((g, g, g), (16, 16, 16), ppn=64, comps=8, dtype="f64", neighbors="all", directions=dirs)
+        p = pt.stencil((g, g, g), (R, R, R), ppn=64, comps=8, dtype="f64", neighbors="all", directions=dirs)
         h = torch.zeros(p.recvbuf_bytes // 8, dtype=torch.float64, device="cuda")
         ex = gbx.Exchange(p, field, h, "standard")
         for _ in range(3):
@@ -1184,12 +1191,13 @@ def run_faces(args):
         print(json.dumps(row), file=sys.stderr)
         del ex, h
         torch.cuda.empty_cache()
-    print(json.dumps({"faces": f"stencil27_{g}cube_P4096_c8_standard", "peak_GBps": peak, "peak_kind": peak_kind,
+    print(json.dumps({"faces": f"stencil27_{g}cube_P{R ** 3}_c8_standard", "peak_GBps": peak, "peak_kind": peak_kind,
                       "rows": rows}))
 
 
 COPY_FORM_NAMES = {0: "segments", 1: "gather", 3: "two-index", 5: "gather pipelined", 7: "two-index pipelined",
-                   8: "bulk pieces", 9: "scatter windows", 10: "gather streamed", 11: "two-index streamed"}
+                   8: "bulk pieces", 9: "scatter windows", 10: "gather streamed", 11: "two-index streamed",
+                   12: "fold streamed"}
 
 
 def run_bwd_forms(args):
@@ -1204,7 +1212,8 @@ def run_bwd_forms(args):
     x = torch.rand(p.sendbuf_bytes // 8, dtype=torch.float64, device="cuda", generator=gen)
     h = torch.zeros(p.recvbuf_bytes // 8, dtype=torch.float64, device="cuda")
     g = torch.randn(p.recvbuf_bytes // 8, dtype=torch.float64, device="cuda", generator=gen)
-    shapes = ["", "bulk=0", "bulk=2", "single_split=0", "split_order=dest"]
+    shapes = ["", "bulk=0", "bulk=2", "single_split=0", "split_order=dest", "stream=0", "stream=2;bulk=0",
+              "stream=0;single_split=0", "stream=2;single_split=0"]
     rows = []
     for alg in ("standard", "locality"):
         ex = gbx.Exchange(p, x, h, alg)

@@ -122,8 +122,9 @@ typedef struct {
     int64_t device_bytes;   /* device memory the request owns                         */
     int64_t copy_forms;     /* bit f set when some copy runs in form f: 0 segments,
                                1 gather, 3 two-index, 5/7 pipelined 1/3, 8 bulk pieces,
-                               9 source windows scattered, 10/11 stream forms of 1/3
-                               (fixed at init by the tuner) */
+                               9 source windows scattered, 10/11 stream forms of 1/3;
+                               bit 12: a fold runs in its stream form (fixed at init by
+                               the tuner) */
 } gbx_request_info_t;
 
 const char *gbx_error_string(int code);

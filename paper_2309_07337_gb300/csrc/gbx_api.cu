@@ -374,12 +374,23 @@ int gbx_make_fold_op(gbx_request_s *req, int level, char *out, int out_role, con
     d.out = out; d.bufA = bufA; d.bufB = bufB; d.row_ptr = row_ptr; d.row_out = row_out; d.terms = terms;
     d.nrows = nrows; d.elem_size = s; d.dtype = req->dtype; d.accumulate = accumulate;
     d.out_role = out_role; d.a_role = a_role; d.b_role = b_role;
+    d.status = req->status_dev; d.wait_limit = req->wait_limit;
     const int64_t max_tiles = ceil_div(nrows * (s / op.min_vec), GBX_TILE);
     GBX_TRY(req->mem.get(&op.d_tile_e0, max_tiles + 1));
     d.tile_e0 = op.d_tile_e0;
     GBX_TRY(req->mem.get(&op.d_rec, nrows));
     GBX_TRY(gbx_build_fold_records(row_ptr, row_out, terms, nrows, op.d_rec, req->stream));
     d.rec = op.d_rec;
+    // the stream form copies records (16-byte entries) and term lists rounded out to 16 bytes
+    // (every term array the library builds is 16-byte aligned with 2 entries of padding)
+    {
+        static int prepared = 0;
+        op.sfold_ok = req->allow_stream && !(((uintptr_t)terms | (uintptr_t)op.d_rec) & 15);
+        if (op.sfold_ok && !prepared) {
+            if (gbx_sfold_prepare() == GBX_SUCCESS) prepared = 1;
+            else op.sfold_ok = 0;
+        }
+    }
     GBX_TRY(req->mem.alloc(&op.d_desc, sizeof(FoldDesc)));
     GBX_TRY(req->mem.get(&op.d_self, 1));
     GBX_TRY(req->mem.get(&op.d_self_prefix, 2));
@@ -442,27 +453,32 @@ static int op_vec(const HostOp &op) { return op.kind == 0 ? op.cd.vec : op.fd.ve
 // grid covers them), which leaves room for other requests' kernels on other streams.
 static int grid_for(int kind, int dtype, int vec, int flat, int block, int persistent, int64_t tiles,
                     int max_ctas) {
-    if (kind == 0 && flat >= 10) persistent = 1;   // the stream kernel's ring wants resident CTAs
+    if ((kind == 0 && flat >= 10) || (kind == 1 && flat == 1)) persistent = 1;   // stream kernels: resident rings
     int64_t g = persistent ? (int64_t)gbx_num_sms() * gbx_occupancy(kind, dtype, vec, block, flat)
                            : std::min<int64_t>(tiles, 1ll << 30);
     if (max_ctas > 0) g = std::min<int64_t>(g, max_ctas);
     return (int)std::max<int64_t>(1, std::min<int64_t>(g, tiles));
 }
 
+// one: every op of the launch has one chunk per element (the stream forms then run their
+// specialised kernel, launch codes 12 / 13)
 static cudaError_t launch_list(int kind, int dtype, int vec, int flat, void **d_ops, int64_t *d_prefix, int nops,
-                               int64_t tiles, int block, int grid, cudaStream_t st) {
+                               int64_t tiles, int block, int grid, cudaStream_t st, int one = 0) {
     if (kind == 0)
-        return gbx_launch_copy((const CopyDesc *const *)d_ops, d_prefix, nops, tiles, vec, flat, block, grid, st);
-    return gbx_launch_fold((const FoldDesc *const *)d_ops, d_prefix, nops, tiles, dtype, vec, block, grid, st);
+        return gbx_launch_copy((const CopyDesc *const *)d_ops, d_prefix, nops, tiles, vec,
+                               (flat == 10 || flat == 11) && one ? flat + 2 : flat, block, grid, st);
+    return gbx_launch_fold((const FoldDesc *const *)d_ops, d_prefix, nops, tiles, dtype, vec, block, grid, st, flat);
 }
 
-static int op_flat(const HostOp &op) { return op.kind == 0 ? op.cd.flat : 0; }
+// a copy's form, or a fold's (0 the fold kernel, 1 its stream form)
+static int op_flat(const HostOp &op) { return op.kind == 0 ? op.cd.flat : op.fold_form; }
 
 static cudaError_t launch_op_alone(gbx_request_s *req, HostOp &op, int block, int persistent) {
     int64_t tiles = op_tiles(op);
     const int vec = op_vec(op), flat = op_flat(op);
     return launch_list(op.kind, req->dtype, vec, flat, op.d_self, op.d_self_prefix, 1, tiles, block,
-                       grid_for(op.kind, req->dtype, vec, flat, block, persistent, tiles, req->max_ctas), req->stream);
+                       grid_for(op.kind, req->dtype, vec, flat, block, persistent, tiles, req->max_ctas), req->stream,
+                       op.kind == 0 && op.cd.cpe == 1);
 }
 
 // ------------------------------------------------------------------ autotuner
@@ -521,14 +537,16 @@ static int tune_op(gbx_request_s *req, HostOp &op) {
     key.units = op.units; key.elem_size = req->elem_size;
     key.nseg = op.kind == 0 ? op.cd.nseg : 0;
     key.nterms = op.kind == 1 ? op.fd.nchunks : 0;
-    key.flat_ok = op.kind == 0 ? op.flat_ok + 2 * op.flat_only + 4 * ((op.cd.flat & 3) == 3) + 8 * op.bulk_ok +
+    key.flat_ok = op.kind == 1 ? op.sfold_ok + 2 * (req->forced_form + 1)
+                : op.kind == 0 ? op.flat_ok + 2 * op.flat_only + 4 * ((op.cd.flat & 3) == 3) + 8 * op.bulk_ok +
                                      16 * op.scat_ok + 32 * (req->allow_bulk == 2) + 64 * op.stream_ok +
                                      128 * (req->allow_stream == 2) + 256 * (req->forced_form + 1)   // forced forms tune apart
-                               : 0;
+                : 0;
     int blocks[4] = {128, 256, 512, 1024};
     if (!req->autotune || req->forced_block) {
         op.block = req->forced_block ? req->forced_block : 256;
         op.persistent = 1;
+        if (op.kind == 1) op.fold_form = op.sfold_ok && req->allow_stream == 2;
         if (op.kind == 0 && !op.flat_only) op.cd.flat = op.flat_ok && req->forced_flat != 0;
         if (op.kind == 0 && op.stream_ok && req->allow_stream == 2) op.cd.flat = (op.cd.flat & 3) == 3 ? 11 : 10;
         if (op.kind == 0 && op.bulk_ok && req->allow_bulk == 2) op.cd.flat = 8;
@@ -543,6 +561,7 @@ static int tune_op(gbx_request_s *req, HostOp &op) {
         auto it = g_tune_cache.find(key);
         op.block = it != g_tune_cache.end() ? it->second.block : 256;
         op.persistent = it != g_tune_cache.end() ? it->second.persistent : 1;
+        op.fold_form = it != g_tune_cache.end() ? it->second.flat : 0;
         return set_vec(req, op, it != g_tune_cache.end() ? it->second.vec : op.max_vec);
     }
     {
@@ -553,6 +572,7 @@ static int tune_op(gbx_request_s *req, HostOp &op) {
             op.persistent = it->second.persistent;
             op.tuned_ms = it->second.ms;
             if (op.kind == 0) op.cd.flat = it->second.flat;
+            else op.fold_form = it->second.flat;
             set_form_bytes(op);
             return set_vec(req, op, it->second.vec);
         }
@@ -560,7 +580,11 @@ static int tune_op(gbx_request_s *req, HostOp &op) {
     TuneVal best = {op.max_vec, 256, 1, 0, 1e30f};
     // candidate forms: segments, flat (gather or two-index), and the pipelined flat form
     std::vector<int> forms;
-    if (op.kind == 1) forms.push_back(0);
+    if (op.kind == 1) {
+        forms.push_back(0);
+        if (op.sfold_ok) forms.push_back(1);   // the fold's stream form
+        if (op.sfold_ok && (req->allow_stream == 2 || req->forced_form == 1)) forms.assign(1, 1);
+    }
     else if (op.flat_only) { forms.push_back(op.cd.flat & 3); forms.push_back((op.cd.flat & 3) + 4); }
     else if (op.flat_ok && req->forced_flat < 0) { forms.push_back(0); forms.push_back(1); forms.push_back(5); }
     else if (op.flat_ok && req->forced_flat > 0) { forms.push_back(1); forms.push_back(5); }
@@ -577,7 +601,9 @@ static int tune_op(gbx_request_s *req, HostOp &op) {
         forms.assign(1, req->forced_form);
     for (int form : forms) {
         if (op.kind == 0) op.cd.flat = form;
-        const bool pipe = form >= 4 && form < 8, bulk = form == 8 || form == 9, strm = form >= 10;
+        else op.fold_form = form;
+        const bool pipe = op.kind == 0 && form >= 4 && form < 8, bulk = op.kind == 0 && (form == 8 || form == 9);
+        const bool strm = op.kind == 0 ? form >= 10 : form == 1;
         // (the op's tile tables are sized for min_vec: no width below it)
         for (int vec = op.max_vec; vec >= (bulk ? 16 : strm ? std::max(4, op.min_vec) : op.min_vec); vec >>= 1) {
             GBX_TRY(set_vec(req, op, vec));
@@ -586,7 +612,9 @@ static int tune_op(gbx_request_s *req, HostOp &op) {
                 for (int pers = 1; pers >= (pipe || strm ? 1 : 0); pers--) {
                     float ms = 0;
                     GBX_TRY(time_op(req, op, blocks[bi], pers, 3, &ms));
-                    if (ms < best.ms) best = {vec, blocks[bi], pers, form, ms};
+                    // a narrower vector must win clearly: it adds a kernel class to any batch
+                    // the op joins, and tiny ops time within noise
+                    if (ms < best.ms * (vec < best.vec ? 0.97f : 1.0f)) best = {vec, blocks[bi], pers, form, ms};
                 }
             if (vec == 1) break;
         }
@@ -595,6 +623,7 @@ static int tune_op(gbx_request_s *req, HostOp &op) {
     op.persistent = best.persistent;
     op.tuned_ms = best.ms;
     if (op.kind == 0) op.cd.flat = best.flat;
+    else op.fold_form = best.flat;
     set_form_bytes(op);
     GBX_TRY(set_vec(req, op, best.vec));
     std::lock_guard<std::mutex> lk(g_tune_mu);
@@ -626,12 +655,13 @@ static int tune_launch(LevelLaunch &L, cudaStream_t st) {
             for (int pers = 1; pers >= (strm ? 1 : 0) && e == cudaSuccess; pers--) {
                 const int blk = gbx_effective_block(L.vec, blocks[bi]);
                 const int grid = grid_for(L.kind, L.dtype, L.vec, fl, blk, pers, L.total_tiles, L.max_ctas);
-                e = launch_list(L.kind, L.dtype, L.vec, fl, L.d_ops, L.d_prefix, L.nops, L.total_tiles, blk, grid, st);
+                e = launch_list(L.kind, L.dtype, L.vec, fl, L.d_ops, L.d_prefix, L.nops, L.total_tiles, blk, grid, st,
+                                L.one);
                 float t = 1e30f;
                 for (int r = 0; r < 3 && e == cudaSuccess; r++) {
                     cudaEventRecord(a, st);
                     e = launch_list(L.kind, L.dtype, L.vec, fl, L.d_ops, L.d_prefix, L.nops, L.total_tiles, blk,
-                                    grid, st);
+                                    grid, st, L.one);
                     cudaEventRecord(b, st);
                     if (e == cudaSuccess) e = cudaEventSynchronize(b);
                     float x = 0;
@@ -696,8 +726,11 @@ static int build_levels(DevPool &mem, const std::vector<HostOp *> &ops, const st
                 const bool strm = op->stream_ok && op_vec(*op) >= 4;
                 const int form = !batch || f0 == 8 || f0 == 9 ? f0
                                : op->flat_ok ? ((f0 & 3) == 3 ? (strm ? 11 : 3) : (strm ? 10 : 1)) : 0;
-                std::pair<int, int> k = kind ? std::make_pair(dtypes[i], op_vec(*op))
-                                             : std::make_pair(form, op_vec(*op));
+                // stream-form copies with one chunk per element get a launch of their own, which
+                // runs the specialised kernel (one op with more chunks would hold back the rest)
+                const int one = kind == 0 && form >= 10 && op->cd.cpe == 1 ? 16 : 0;
+                std::pair<int, int> k = kind ? std::make_pair(dtypes[i] + 8 * op->fold_form, op_vec(*op))
+                                             : std::make_pair(form + one, op_vec(*op));
                 size_t g = 0;
                 while (g < keys.size() && keys[g] != k) g++;
                 if (g == keys.size()) { keys.push_back(k); groups.emplace_back(); }
@@ -710,7 +743,8 @@ static int build_levels(DevPool &mem, const std::vector<HostOp *> &ops, const st
                 // common payload type, vector width and form, or 0 / 2 (= mixed)
                 int dt = dtypes[groups[g][0]], vec = op_vec(*ops[groups[g][0]]);
                 // (a pooled class of one op keeps the form it was tuned to, pipelined included)
-                int fl = kind ? 0 : (groups[g].size() == 1 ? op_flat(*ops[groups[g][0]]) : keys[g].first);
+                int fl = kind ? ops[groups[g][0]]->fold_form
+                              : (groups[g].size() == 1 ? op_flat(*ops[groups[g][0]]) : keys[g].first & 15);
                 for (size_t i : groups[g]) {
                     if (dtypes[i] != dt) dt = -1;
                     if (op_vec(*ops[i]) != vec) vec = 0;
@@ -720,6 +754,9 @@ static int build_levels(DevPool &mem, const std::vector<HostOp *> &ops, const st
                 L.dtype = dt < 0 ? GBX_F32 : dt;
                 L.vec = vec;
                 L.flat = vec == 0 ? 2 : fl;
+                L.one = 1;
+                for (size_t i : groups[g])
+                    if (kind != 0 || ops[i]->cd.cpe != 1) L.one = 0;
                 std::vector<void *> ptrs;
                 std::vector<int64_t> pre(1, 0);
                 const HostOp *big = ops[groups[g][0]];
@@ -754,7 +791,7 @@ static cudaError_t enqueue_levels(const std::vector<LevelLaunch> &levels, cudaSt
     for (const LevelLaunch &L : levels) {
         GbxRange r(L.phase);
         cudaError_t e = launch_list(L.kind, L.dtype, L.vec, L.flat, L.d_ops, L.d_prefix, L.nops, L.total_tiles,
-                                    L.block, L.grid, st);
+                                    L.block, L.grid, st, L.one);
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
@@ -792,6 +829,7 @@ static void fill_info(gbx_request_s *req) {
         nlev = std::max(nlev, op.level + 1);
         algo += op.algo_bytes;
         if (op.kind == 0) I.copy_forms |= (int64_t)1 << op.cd.flat;
+        else if (op.fold_form) I.copy_forms |= (int64_t)1 << 12;   // a fold in its stream form
         if (!big || op.algo_bytes > big->algo_bytes) big = &op;
     }
     I.levels = nlev;

@@ -109,4 +109,6 @@ struct FoldDesc {
     uint32_t cpe_magic;
     int32_t dtype, accumulate;
     int32_t out_role, a_role, b_role;
+    int *status;              // the request's status word (see CopyDesc)
+    int32_t wait_limit;
 };

@@ -91,9 +91,11 @@ int gbx_occupancy(int kind, int dtype, int vec, int block, int flat);   // resid
 // flat: 0 every op in segment form, 1 every op in flat form, 2 decided per op
 cudaError_t gbx_launch_copy(const CopyDesc *const *ops, const int64_t *tile_prefix, int nops,
                             int64_t total_tiles, int vec, int flat, int block, int grid, cudaStream_t st);
+// form 0: the fold kernel; 1: its stream form (records and terms staged in shared memory)
 cudaError_t gbx_launch_fold(const FoldDesc *const *ops, const int64_t *tile_prefix, int nops,
                             int64_t total_tiles, int dtype, int vec, int block, int grid,
-                            cudaStream_t st);
+                            cudaStream_t st, int form);
+int gbx_sfold_prepare(void);
 // Per-tile metadata: first unit (element / row) of each tile and, for copy ops, the
 // segment holding it (segs may be NULL for fold ops).
 int gbx_build_tile_meta(const Seg *segs, int64_t nseg, int cpe, int64_t ntiles, int64_t *tile_seg,
@@ -145,6 +147,9 @@ struct HostOp {
     int64_t nbulk;
     int stream_ok;          // the flat form's index arrays are 16-byte aligned and padded: the
                             // stream forms (10 gather, 11 two-index) are available
+    int sfold_ok;           // fold: records and terms aligned and padded, one payload class: the
+                            // stream form of the fold is available
+    int fold_form;          // fold: 0 the fold kernel, 1 its stream form (tuned)
     int scat_ok;            // two-index copy with the scatter form available
     ScatterPiece *d_scat;
     int64_t nscat;
@@ -165,6 +170,7 @@ struct LevelLaunch {
     int64_t total_tiles;
     int max_ctas;           // grid cap (0: none)
     const char *phase;      // NVTX name of the launch (a string literal)
+    int one;                // copies: every op has one chunk per element (stream kernels specialise)
     void **d_ops;           // device array of descriptor pointers
     int64_t *d_prefix;      // device tile prefix (nops + 1)
 };

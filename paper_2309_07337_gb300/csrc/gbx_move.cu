@@ -346,7 +346,8 @@ __device__ int gbx_bulk_status;
 // Records a status code (1: a bounded wait gave up, 2: a piece failed its check) in the
 // process-wide word and in the status word of every op of the launch: a launch that gives up
 // leaves pieces of any of its ops unfinished, so each request it serves must report it.
-__device__ __noinline__ void gbx_raise(const CopyDesc *const *__restrict__ ops, int nops, int code) {
+template <typename D>
+__device__ __noinline__ void gbx_raise(const D *const *__restrict__ ops, int nops, int code) {
     atomicExch(&gbx_bulk_status, code);
     for (int i = 0; i < nops; i++) {
         int *w = ops[i]->status;
@@ -668,7 +669,7 @@ int gbx_scatter_prepare(void) {
 // up raises `abort`, the producer stops issuing and drains its copies in flight).
 #define GBX_STREAM_IDX ((GBX_TILE + 8) * 4)   // bytes of one index array per stage
 
-template <int VEC, int FORM, int NT, int S, int U, int PS>
+template <int VEC, int FORM, int NT, int S, int U, int PS, bool ONE>
 __global__ void __launch_bounds__(NT, PS) gbx_stream_kernel(const CopyDesc *const *__restrict__ ops,
                                                         const int64_t *__restrict__ prefix, int nops,
                                                         int64_t ntiles) {
@@ -766,7 +767,38 @@ __global__ void __launch_bounds__(NT, PS) gbx_stream_kernel(const CopyDesc *cons
             break;
         }
         const int64_t e_al = ebase_s[q];
-        if (e_al >= 0) {
+        if (ONE && e_al >= 0) {
+            // ONE (every op of the launch has one chunk per element, elem_size == VEC): chunk x
+            // of the tile is element e0 + x, every offset a multiple of VEC
+            const CopyDesc *d = desc_s[q];
+            const int64_t e0 = efirst_s[q];
+            const int left = (int)min((int64_t)GBX_TILE, d->nchunks - tile_s[q] * GBX_TILE);
+            const int32_t *is = reinterpret_cast<const int32_t *>(gbx_stream_smem + q * STAGE) + (e0 - e_al);
+            const int32_t *ids =
+                reinterpret_cast<const int32_t *>(gbx_stream_smem + q * STAGE + GBX_STREAM_IDX) + (e0 - e_al);
+            const char *src = d->src, *src2 = d->src2;
+            char *dst = d->dst;
+            char *dtile = dst + (FORM == 3 ? 0 : d->dst_flat0 + e0 * VEC);
+            for (int base = 0; base < left; base += NC * U) {
+                V val[U];
+                int32_t di[U];
+#pragma unroll
+                for (int u = 0; u < U; u++) {
+                    const int x = base + u * NC + ct;
+                    if (x < left) {
+                        const uint32_t gi = (uint32_t)is[x];
+                        if (FORM == 3) di[u] = ids[x];
+                        const char *b = (gi & GBX_FLAT_SRC2) ? src2 : src;
+                        val[u] = ldv<VEC>(b + (int64_t)(gi & ~GBX_FLAT_SRC2) * VEC);
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < U; u++) {
+                    const int x = base + u * NC + ct;
+                    if (x < left) stv<VEC>(FORM == 3 ? dst + (int64_t)di[u] * VEC : dtile + (int64_t)x * VEC, val[u]);
+                }
+            }
+        } else if (!ONE && e_al >= 0) {
             const CopyDesc *d = desc_s[q];
             const int cpe = d->cpe, sh = d->cpe_shift;
             const uint32_t magic = d->cpe_magic;
@@ -816,39 +848,54 @@ static StreamShape stream_shape(int block) {
     return {544, 6, 2, 2};
 }
 
-template <int VEC, int FORM>
+template <int VEC, int FORM, bool ONE>
 static cudaError_t stream_launch_v(int block, int grid, cudaStream_t st, const CopyDesc *const *ops,
                                    const int64_t *prefix, int nops, int64_t n) {
     const StreamShape h = stream_shape(block);
     const size_t smem = (size_t)h.stages * GBX_STREAM_IDX * (FORM == 3 ? 2 : 1);
-    if (h.nt == 288) gbx_stream_kernel<VEC, FORM, 288, 4, 4, 4><<<grid, 288, smem, st>>>(ops, prefix, nops, n);
-    else gbx_stream_kernel<VEC, FORM, 544, 6, 2, 2><<<grid, 544, smem, st>>>(ops, prefix, nops, n);
+    if (h.nt == 288) gbx_stream_kernel<VEC, FORM, 288, 4, 4, 4, ONE><<<grid, 288, smem, st>>>(ops, prefix, nops, n);
+    else gbx_stream_kernel<VEC, FORM, 544, 6, 2, 2, ONE><<<grid, 544, smem, st>>>(ops, prefix, nops, n);
     return cudaGetLastError();
 }
 
+template <int VEC>
+static cudaError_t stream_launch_f(int flat, int block, int grid, cudaStream_t st, const CopyDesc *const *ops,
+                                   const int64_t *prefix, int nops, int64_t n) {
+    switch (flat) {
+        case 10: return stream_launch_v<VEC, 1, false>(block, grid, st, ops, prefix, nops, n);
+        case 11: return stream_launch_v<VEC, 3, false>(block, grid, st, ops, prefix, nops, n);
+        case 12: return stream_launch_v<VEC, 1, true>(block, grid, st, ops, prefix, nops, n);
+        default: return stream_launch_v<VEC, 3, true>(block, grid, st, ops, prefix, nops, n);
+    }
+}
+
+// flat 10 / 11: the stream forms; 12 / 13: the same when every op of the launch has one chunk
+// per element (the kernel then skips the element / chunk split)
 static cudaError_t stream_launch(int vec, int flat, int block, int grid, cudaStream_t st, const CopyDesc *const *ops,
                                  const int64_t *prefix, int nops, int64_t n) {
-    const bool two = flat == 11;
     switch (vec) {
-        case 16: return two ? stream_launch_v<16, 3>(block, grid, st, ops, prefix, nops, n)
-                            : stream_launch_v<16, 1>(block, grid, st, ops, prefix, nops, n);
-        case 8: return two ? stream_launch_v<8, 3>(block, grid, st, ops, prefix, nops, n)
-                           : stream_launch_v<8, 1>(block, grid, st, ops, prefix, nops, n);
-        case 4: return two ? stream_launch_v<4, 3>(block, grid, st, ops, prefix, nops, n)
-                           : stream_launch_v<4, 1>(block, grid, st, ops, prefix, nops, n);
+        case 16: return stream_launch_f<16>(flat, block, grid, st, ops, prefix, nops, n);
+        case 8: return stream_launch_f<8>(flat, block, grid, st, ops, prefix, nops, n);
+        case 4: return stream_launch_f<4>(flat, block, grid, st, ops, prefix, nops, n);
         default: return cudaErrorInvalidValue;   // the stream form is offered for vectors of 4..16 bytes
     }
 }
 
-template <int VEC, int FORM>
-static cudaError_t stream_attr_v() {
-    cudaError_t e = cudaFuncSetAttribute(gbx_stream_kernel<VEC, FORM, 288, 4, 4, 4>,
+template <int VEC, int FORM, bool ONE>
+static cudaError_t stream_attr_o() {
+    cudaError_t e = cudaFuncSetAttribute(gbx_stream_kernel<VEC, FORM, 288, 4, 4, 4, ONE>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          4 * GBX_STREAM_IDX * (FORM == 3 ? 2 : 1));
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(gbx_stream_kernel<VEC, FORM, 544, 6, 2, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 6 * GBX_STREAM_IDX * (FORM == 3 ? 2 : 1));
+        e = cudaFuncSetAttribute(gbx_stream_kernel<VEC, FORM, 544, 6, 2, 2, ONE>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, 6 * GBX_STREAM_IDX * (FORM == 3 ? 2 : 1));
     return e;
+}
+
+template <int VEC, int FORM>
+static cudaError_t stream_attr_v() {
+    cudaError_t e = stream_attr_o<VEC, FORM, false>();
+    return e == cudaSuccess ? stream_attr_o<VEC, FORM, true>() : e;
 }
 
 int gbx_stream_prepare(void) {
@@ -960,6 +1007,208 @@ __device__ __forceinline__ void fold_tile(const FoldDesc *__restrict__ d, int64_
         if (d->accumulate) r = padd(*o, r);
         *o = r;
     }
+}
+
+// Stream form of the fold (the reverse exchange's sums): the fold's tiles, with each tile's
+// row records and its rows' term lists (both contiguous ranges, the terms rounded out to
+// 16-byte boundaries; the term arrays carry 2 entries of padding) copied into a ring of S
+// shared-memory stages by the bulk-copy engine from one producer lane, completing on the
+// stage's "full" mbarrier.  Each consumer thread then holds one chunk of one row: it reads
+// the record and terms from shared memory and issues up to GBX_SFOLD_K gradient loads of
+// the row at once before adding them in the row's fixed order, so a row costs one memory
+// latency instead of two per term.  A tile whose terms do not fit a stage reads them from
+// global memory.  Waits bounded as in the stream copy.
+#define GBX_SFOLD_REC ((GBX_TILE + 2) * 16)   // bytes of records per stage
+#define GBX_SFOLD_TERMS 2048                   // term entries per stage
+#define GBX_SFOLD_STAGE (GBX_SFOLD_REC + GBX_SFOLD_TERMS * 8)
+// gradient loads in flight per thread: 8 of 4 or 8 bytes, 4 of 16 bytes (the registers of
+// 2 CTAs of 544 threads per SM)
+
+template <typename T, int VEC, int NT, int S, int PS>
+__global__ void __launch_bounds__(NT, PS) gbx_sfold_kernel(const FoldDesc *const *__restrict__ ops,
+                                                           const int64_t *__restrict__ prefix, int nops,
+                                                           int64_t ntiles) {
+    typedef typename PackT<T, VEC>::T PK;
+    constexpr int NC = NT - 32, NCW = NC / 32;
+    constexpr int GBX_SFOLD_K = VEC == 16 ? 4 : 8;
+    extern __shared__ __align__(128) unsigned char gbx_sfold_smem[];
+    __shared__ __align__(8) uint64_t full[S], empty[S];
+    __shared__ const FoldDesc *desc_s[S];
+    __shared__ int64_t tile_s[S], rfirst_s[S], tbase_s[S];
+    __shared__ volatile int abort_flag;
+    const uint32_t sbuf = (uint32_t)__cvta_generic_to_shared(gbx_sfold_smem);
+    const uint32_t sfull = (uint32_t)__cvta_generic_to_shared(full);
+    const uint32_t sempty = (uint32_t)__cvta_generic_to_shared(empty);
+    if (threadIdx.x == 0) {
+        for (int q = 0; q < S; q++) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(sfull + 8 * q) : "memory");
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(sempty + 8 * q), "r"(NCW) : "memory");
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        abort_flag = 0;
+    }
+    __syncthreads();   // the only CTA-wide barrier
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int limit = ops[0]->wait_limit;
+    if (warp == 0) {
+        if (lane != 0) return;
+        // ---------------------------------------------------------------- producer
+        int64_t last[S];
+#pragma unroll
+        for (int q = 0; q < S; q++) last[q] = -1;
+        bool stop = false;
+        for (int64_t k = 0;; k++) {
+            const int64_t t = blockIdx.x + k * gridDim.x;
+            if (t >= ntiles) break;
+            const int q = (int)(k % S);
+            if (k >= S && !bulk_wait(sempty + 8 * q, (uint32_t)((k / S - 1) & 1), limit)) {
+                abort_flag = 1;
+                stop = true;
+                break;
+            }
+            if (abort_flag) {
+                stop = true;
+                break;
+            }
+            const int op = nops > 1 ? find_op(prefix, nops, t) : 0;
+            const FoldDesc *d = ops[op];
+            const int64_t lt = t - __ldg(prefix + op);
+            const int64_t cpe = d->cpe, c0 = lt * GBX_TILE, c1 = min(d->nchunks, c0 + GBX_TILE);
+            const int64_t r_first = c0 / cpe, r_last = (c1 - 1) / cpe;
+            const uint32_t rbytes = (uint32_t)((r_last - r_first + 1) * 16);
+            const int64_t tb = __ldg(d->row_ptr + r_first), te = __ldg(d->row_ptr + r_last + 1);
+            const int64_t tb_al = tb & ~(int64_t)1, te_al = (te + 1) & ~(int64_t)1;
+            const bool inl = (te_al - tb_al) <= GBX_SFOLD_TERMS;
+            const uint32_t tbytes = inl ? (uint32_t)((te_al - tb_al) * 8) : 0u;
+            const uint32_t fb = sfull + 8 * q, stage = sbuf + q * GBX_SFOLD_STAGE;
+            desc_s[q] = d;
+            tile_s[q] = lt;
+            rfirst_s[q] = r_first;
+            tbase_s[q] = inl ? tb_al : -1;
+            const uintptr_t al = (uintptr_t)d->rec | (uintptr_t)d->terms;
+            if ((al & 15) || rbytes > GBX_SFOLD_REC || c1 <= c0) {   // validated at init; recorded, skipped
+                gbx_raise(ops, nops, 2);
+                rfirst_s[q] = -1;
+                asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(fb) : "memory");
+                continue;
+            }
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(fb), "r"(rbytes + tbytes)
+                         : "memory");
+            asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                         ::"r"(stage), "l"(d->rec + r_first), "r"(rbytes), "r"(fb)
+                         : "memory");
+            if (tbytes)
+                asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                             ::"r"(stage + GBX_SFOLD_REC), "l"(d->terms + tb_al), "r"(tbytes), "r"(fb)
+                             : "memory");
+            last[q] = k;
+        }
+        if (stop) {
+            gbx_raise(ops, nops, 1);
+            for (int q = 0; q < S; q++)
+                if (last[q] >= 0) bulk_wait(sfull + 8 * q, (uint32_t)((last[q] / S) & 1));
+        }
+        return;
+    }
+    // -------------------------------------------------------------------- consumers
+    const int ct = threadIdx.x - 32;
+    for (int64_t k = 0;; k++) {
+        const int64_t t = blockIdx.x + k * gridDim.x;
+        if (t >= ntiles) break;
+        const int q = (int)(k % S);
+        if (!bulk_wait(sfull + 8 * q, (uint32_t)((k / S) & 1), limit)) {
+            abort_flag = 1;
+            break;
+        }
+        const int64_t r_first = rfirst_s[q];
+        if (r_first >= 0) {
+            const FoldDesc *d = desc_s[q];
+            const int cpe = d->cpe, sh = d->cpe_shift;
+            const uint32_t magic = d->cpe_magic;
+            const int64_t c0 = tile_s[q] * GBX_TILE, tb_al = tbase_s[q];
+            const int left = (int)min((int64_t)GBX_TILE, d->nchunks - c0);
+            const uint32_t r0 = (uint32_t)(c0 - r_first * cpe);
+            const longlong2 *rs = reinterpret_cast<const longlong2 *>(gbx_sfold_smem + q * GBX_SFOLD_STAGE);
+            const int64_t *ts = reinterpret_cast<const int64_t *>(gbx_sfold_smem + q * GBX_SFOLD_STAGE + GBX_SFOLD_REC);
+            const char *bufA = d->bufA, *bufB = d->bufB;
+            for (int x = ct; x < left; x += NC) {
+                const uint32_t xx = r0 + (uint32_t)x;
+                const uint32_t el = unit_of(xx, cpe, sh, magic);
+                const int64_t jv = (int64_t)(xx - el * (uint32_t)cpe) * VEC;
+                const longlong2 rec = rs[el];
+                const uint64_t oa = (uint64_t)rec.x, ob = (uint64_t)rec.y;
+                PK res;
+                if (oa & GBX_ROW_SINGLE) {
+                    res = pload<PK>(((ob & GBX_TERM_BUFB) ? bufB : bufA) + (int64_t)(ob & GBX_TERM_MASK) + jv);
+                } else {
+                    const int64_t b = (int64_t)(ob >> GBX_ROW_CNT_BITS);
+                    const int n = (int)(ob & ((1ull << GBX_ROW_CNT_BITS) - 1));
+                    const int64_t *tw = tb_al >= 0 ? ts + (b - tb_al) : d->terms + b;
+                    PK grp, tot;
+                    bool has = false;
+                    for (int m0 = 0; m0 < n; m0 += GBX_SFOLD_K) {
+                        const int cnt = min(GBX_SFOLD_K, n - m0);
+                        PK xv[GBX_SFOLD_K];
+                        uint32_t gbit = 0;
+#pragma unroll
+                        for (int i = 0; i < GBX_SFOLD_K; i++)
+                            if (i < cnt) {
+                                const uint64_t w = (uint64_t)tw[m0 + i];
+                                gbit |= (w & GBX_TERM_GROUP) ? (1u << i) : 0u;
+                                xv[i] = pload<PK>(((w & GBX_TERM_BUFB) ? bufB : bufA) + (int64_t)(w & GBX_TERM_MASK) + jv);
+                            }
+#pragma unroll
+                        for (int i = 0; i < GBX_SFOLD_K; i++)
+                            if (i < cnt) {
+                                if (m0 + i == 0) {
+                                    grp = xv[i];
+                                } else if (gbit & (1u << i)) {
+                                    tot = has ? padd(tot, grp) : grp;
+                                    has = true;
+                                    grp = xv[i];
+                                } else {
+                                    grp = padd(grp, xv[i]);
+                                }
+                            }
+                    }
+                    res = has ? padd(tot, grp) : grp;
+                }
+                PK *o = reinterpret_cast<PK *>(d->out + (int64_t)(oa & ~GBX_ROW_SINGLE) + jv);
+                if (d->accumulate) res = padd(*o, res);
+                *o = res;
+            }
+        }
+        __syncwarp();
+        if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(sempty + 8 * q) : "memory");
+        if (abort_flag) break;
+    }
+}
+
+#define GBX_SFOLD_NT 544
+#define GBX_SFOLD_S 3
+
+template <typename T, int VEC>
+static cudaError_t sfold_launch_v(int grid, cudaStream_t st, const FoldDesc *const *ops, const int64_t *prefix,
+                                  int nops, int64_t n) {
+    gbx_sfold_kernel<T, VEC, GBX_SFOLD_NT, GBX_SFOLD_S, 2>
+        <<<grid, GBX_SFOLD_NT, GBX_SFOLD_S * GBX_SFOLD_STAGE, st>>>(ops, prefix, nops, n);
+    return cudaGetLastError();
+}
+
+template <typename T, int VEC>
+static cudaError_t sfold_attr_v() {
+    return cudaFuncSetAttribute(gbx_sfold_kernel<T, VEC, GBX_SFOLD_NT, GBX_SFOLD_S, 2>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, GBX_SFOLD_S * GBX_SFOLD_STAGE);
+}
+
+int gbx_sfold_prepare(void) {
+    cudaError_t e = sfold_attr_v<double, 16>();
+    if (e == cudaSuccess) e = sfold_attr_v<double, 8>();
+    if (e == cudaSuccess) e = sfold_attr_v<float, 16>();
+    if (e == cudaSuccess) e = sfold_attr_v<float, 8>();
+    if (e == cudaSuccess) e = sfold_attr_v<float, 4>();
+    return e == cudaSuccess ? GBX_SUCCESS : GBX_ERR_CUDA;
 }
 
 // CLS 1..5: every op of the launch is (f64,16) (f64,8) (f32,16) (f32,8) (f32,4);
@@ -1079,9 +1328,10 @@ int gbx_effective_block(int vec_class, int block) { return (vec_class == 0 && bl
 static int pipe_block(int flat, int block) { return (flat == 5 || flat == 7) && block < 512 ? 512 : block; }
 
 int gbx_occupancy(int kind, int dtype, int vec, int block, int flat) {
+    if (kind == 1 && flat == 1) return 2;   // stream fold: two CTAs of 544 threads per SM
     if (kind == 0 && flat == 8) return 1;   // bulk kernel: one CTA per SM (its ring)
     if (kind == 0 && flat == 9) return scatter_shape(block).per_sm;
-    if (kind == 0 && (flat == 10 || flat == 11)) return stream_shape(block).per_sm;
+    if (kind == 0 && flat >= 10 && flat <= 13) return stream_shape(block).per_sm;
     if (kind == 0) block = pipe_block(flat, block);
     const void *f = kind == 0 ? (const void *)copy_fn(vec, block, flat) : (const void *)fold_fn(dtype, vec, block);
     int n = 0;
@@ -1105,7 +1355,7 @@ cudaError_t gbx_launch_copy(const CopyDesc *const *ops, const int64_t *tile_pref
     if (flat == 9) {   // scatter form: a "tile" is one source window
         return scatter_launch(block, clamp_grid(grid, total_tiles), st, ops, tile_prefix, nops, total_tiles);
     }
-    if (flat == 10 || flat == 11)   // stream forms: the flat forms' tiles, indices through shared memory
+    if (flat >= 10 && flat <= 13)   // stream forms: the flat forms' tiles, indices through shared memory
         return stream_launch(vec, flat, block, clamp_grid(grid, total_tiles), st, ops, tile_prefix, nops, total_tiles);
     if ((flat == 5 || flat == 7) && (nops > 1 || vec == 0)) flat -= 4;   // the pipelined kernels take one op
     block = pipe_block(flat, block);
@@ -1115,8 +1365,19 @@ cudaError_t gbx_launch_copy(const CopyDesc *const *ops, const int64_t *tile_pref
 }
 
 cudaError_t gbx_launch_fold(const FoldDesc *const *ops, const int64_t *tile_prefix, int nops, int64_t total_tiles,
-                            int dtype, int vec, int block, int grid, cudaStream_t st) {
+                            int dtype, int vec, int block, int grid, cudaStream_t st, int form) {
     if (total_tiles <= 0) return cudaSuccess;
+    if (form == 1 && vec != 0) {   // stream form: one payload class per launch
+        const int g = clamp_grid(grid, total_tiles);
+        switch (fold_cls(dtype, vec)) {
+            case 1: return sfold_launch_v<double, 16>(g, st, ops, tile_prefix, nops, total_tiles);
+            case 2: return sfold_launch_v<double, 8>(g, st, ops, tile_prefix, nops, total_tiles);
+            case 3: return sfold_launch_v<float, 16>(g, st, ops, tile_prefix, nops, total_tiles);
+            case 4: return sfold_launch_v<float, 8>(g, st, ops, tile_prefix, nops, total_tiles);
+            case 5: return sfold_launch_v<float, 4>(g, st, ops, tile_prefix, nops, total_tiles);
+            default: return cudaErrorInvalidValue;
+        }
+    }
     FoldFn f = fold_fn(dtype, vec, block);
     f<<<clamp_grid(grid, total_tiles), gbx_effective_block(vec, block), 0, st>>>(ops, tile_prefix, nops, total_tiles);
     return cudaGetLastError();

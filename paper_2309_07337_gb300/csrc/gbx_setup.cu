@@ -990,7 +990,7 @@ int gbx_setup_backward(gbx_request_s *bwd, int accumulate) {
         GBX_TRY(gbx_read_i64(rowid + V, &nrows, st));
         GBX_TRY(bwd->mem.get(&row_ptr, nrows + 1));
         GBX_TRY(bwd->mem.get(&row_out, nrows));
-        GBX_TRY(bwd->mem.get(&terms, V));
+        GBX_TRY(bwd->mem.get(&terms, V + 2));   // 2 entries of padding: the stream fold rounds its copies to 16 bytes
         bwd_terms_kernel<<<grid_of(V), SETUP_T, 0, st>>>(k, v, flag, rowid, V, f->segs_std, segv0, nseg, s, 0, 1,
                                                          terms, row_ptr, row_out);
         GBX_CUDA_TRY(cudaGetLastError());
@@ -1026,7 +1026,7 @@ int gbx_setup_backward(gbx_request_s *bwd, int accumulate) {
         GBX_TRY(gbx_scan_i64(flag, rowid, Vx, st, ws));
         GBX_TRY(bwd->mem.get(&row_ptr, U + 1));
         GBX_TRY(bwd->mem.get(&row_out, U));
-        GBX_TRY(bwd->mem.get(&terms, Vx));
+        GBX_TRY(bwd->mem.get(&terms, Vx + 2));
         // rows write the receive-aggregate half (gR) at U*s + slot*s
         bwd_terms_kernel<<<grid_of(Vx), SETUP_T, 0, st>>>(k, v, flag, rowid, Vx, f->segs_std, segv0, nseg, s, U * s,
                                                           s, terms, row_ptr, row_out);
@@ -1082,7 +1082,7 @@ int gbx_setup_backward(gbx_request_s *bwd, int accumulate) {
         GBX_TRY(gbx_read_i64(rowid + M, &nrows, st));
         GBX_TRY(bwd->mem.get(&row_ptr, nrows + 1));
         GBX_TRY(bwd->mem.get(&row_out, nrows));
-        GBX_TRY(bwd->mem.get(&terms, M));
+        GBX_TRY(bwd->mem.get(&terms, M + 2));
         rev1_terms_kernel<<<grid_of(M), SETUP_T, 0, st>>>(sk, sx, flag, rowid, M, V, f->segs_std, segv0, nseg,
                                                           f->seg_dst_rank, f->agg_dst_node, ppn, s, terms, row_ptr,
                                                           row_out);
@@ -1745,7 +1745,7 @@ int gbx_split_single_rows(gbx_request_s *req, const int64_t *row_ptr, const int6
     GBX_TRY(gbx_read_i64(mterm + nrows, &nt, st));
     if (ns == 0) return GBX_SUCCESS;
     GBX_TRY(req->mem.get(gs, ns + 4)); GBX_TRY(req->mem.get(gd, ns + 4));   // padding for the scatter form
-    GBX_TRY(req->mem.get(row_ptr2, nm + 1)); GBX_TRY(req->mem.get(row_out2, nm)); GBX_TRY(req->mem.get(terms2, nt));
+    GBX_TRY(req->mem.get(row_ptr2, nm + 1)); GBX_TRY(req->mem.get(row_out2, nm)); GBX_TRY(req->mem.get(terms2, nt + 2));
     row_split_kernel<<<grid_of(nrows), SETUP_T, 0, st>>>(row_ptr, row_out, terms, nrows, req->elem_size, sidx, mrow,
                                                          mterm, *gs, *gd, *row_ptr2, *row_out2, *terms2, bad);
     GBX_CUDA_TRY(cudaGetLastError());

@@ -122,3 +122,34 @@ def test_stencil_256cube_forward_backward():
     gs, b = backward(ex, g, info="stream=2;bulk=0")
     assert b.info()["copy_forms"] & STREAM2
     assert_bytes_equal(gs, oracle.backward(p, g, form=0), "backward")
+
+
+@pytest.mark.parametrize("seed", range(10))
+def test_stream_fold_every_row(seed):
+    """The stream form of the fold (records and term lists staged in shared memory, a row's
+    gradient loads issued together) with every row folded (single_split=0), in both orders,
+    and accumulating."""
+    dt = "f64" if seed % 2 else "f32"
+    p = pt.random_pattern(3500 + seed, dtype=dt, max_count=40)
+    x = payload(p, seed)
+    g = grad_payload(p, seed + 5)
+    old = payload(p, seed + 9)
+    for alg, form in (("standard", 0), ("locality", 1)):
+        _, ex = forward(p, x, alg)
+        got, b = backward(ex, g, info="stream=2;single_split=0")
+        assert_bytes_equal(got, oracle.backward(p, g, form=form), f"{p.name} {alg}")
+        got, b = backward(ex, g, grad_send_init=old, accumulate=True, info="stream=2;autotune=0")
+        assert_bytes_equal(got, oracle.backward(p, g, grad_send=old, form=form, accumulate=True),
+                           f"{p.name} {alg} accumulate")
+
+
+@pytest.mark.parametrize("alg,form", [("standard", 0), ("locality", 1)])
+def test_stream_fold_spmv_and_stencil(alg, form):
+    """fp32 one-element rows (the SpMV halo's reverse, many terms per row) and 64-byte fp64
+    rows (the 256^3 stencil's edges and corners), stream fold forced."""
+    for p, seed in ((pt.config4(n=1 << 16, P=128, ppn=32), 21), (pt.config5(edge=16), 22)):
+        x = payload(p, seed)
+        g = grad_payload(p, seed + 1)
+        _, ex = forward(p, x, alg)
+        got, b = backward(ex, g, info="stream=2")
+        assert_bytes_equal(got, oracle.backward(p, g, form=form), f"{p.name} {alg}")
