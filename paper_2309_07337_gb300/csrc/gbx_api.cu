@@ -607,14 +607,17 @@ static int tune_op(gbx_request_s *req, HostOp &op) {
         // (the op's tile tables are sized for min_vec: no width below it)
         for (int vec = op.max_vec; vec >= (bulk ? 16 : strm ? std::max(4, op.min_vec) : op.min_vec); vec >>= 1) {
             GBX_TRY(set_vec(req, op, vec));
-            // stream forms: two shapes (block 256, 512), persistent grid only
-            for (int bi = pipe ? 2 : form == 8 ? 3 : strm ? 1 : 0; bi < (strm ? 3 : 4); bi++)
+            // stream forms: persistent grid only; block 256 and 512 select the two wide shapes,
+            // block 128 the narrow one, offered only with one chunk per element (cpe == 1)
+            const int b0 = pipe ? 2 : form == 8 ? 3 : strm ? (op.kind == 0 && op.cd.cpe == 1 && vec <= 8 ? 0 : 1) : 0;
+            for (int bi = b0; bi < (strm ? 3 : 4); bi++)
                 for (int pers = 1; pers >= (pipe || strm ? 1 : 0); pers--) {
                     float ms = 0;
                     GBX_TRY(time_op(req, op, blocks[bi], pers, 3, &ms));
                     // a narrower vector must win clearly: it adds a kernel class to any batch
-                    // the op joins, and tiny ops time within noise
-                    if (ms < best.ms * (vec < best.vec ? 0.97f : 1.0f)) best = {vec, blocks[bi], pers, form, ms};
+                    // the op joins, and small ops (under two waves of tiles) time within noise
+                    const float margin = op_tiles(op) < 2 * 4 * gbx_num_sms() ? 0.85f : 0.97f;
+                    if (ms < best.ms * (vec < best.vec ? margin : 1.0f)) best = {vec, blocks[bi], pers, form, ms};
                 }
             if (vec == 1) break;
         }
@@ -651,7 +654,7 @@ static int tune_launch(LevelLaunch &L, cudaStream_t st) {
     for (int fi = 0; fi < nforms && e == cudaSuccess; fi++) {
         const int fl = fi == 0 ? L.flat : (L.flat == 10 ? 1 : 3);
         const bool strm = fl >= 10;
-        for (int bi = strm ? 1 : 0; bi < (strm ? 3 : 4) && e == cudaSuccess; bi++)
+        for (int bi = strm ? (L.one && L.vec <= 8 ? 0 : 1) : 0; bi < (strm ? 3 : 4) && e == cudaSuccess; bi++)
             for (int pers = 1; pers >= (strm ? 1 : 0) && e == cudaSuccess; pers--) {
                 const int blk = gbx_effective_block(L.vec, blocks[bi]);
                 const int grid = grid_for(L.kind, L.dtype, L.vec, fl, blk, pers, L.total_tiles, L.max_ctas);
@@ -909,6 +912,12 @@ static void destroy_request(gbx_request_s *req) {
     if (g) gbx_graph_free(&g);
 }
 
+// Events that other streams wait on (cudaStreamWaitEvent: gbx_wait_stream, gbx_parrived_stream,
+// the host-buffer copy streams, batches) are created with timing enabled: on GB300 a stream
+// waiting on a disable-timing event held back the work queued behind the wait (an early-bird
+// exchange of 8 partitions took 2.99 ms against 2.47 ms with timing-enabled events).
+static cudaError_t gbx_event_create(cudaEvent_t *ev) { return cudaEventCreateWithFlags(ev, cudaEventDefault); }
+
 static gbx_request_s *new_request(const Opts &o, void *stream) {
     gbx_request_s *req = new gbx_request_s();
     cudaGetDevice(&req->device);
@@ -931,7 +940,7 @@ static gbx_request_s *new_request(const Opts &o, void *stream) {
     req->wait_limit = o.wait_limit;
     req->allow_stream = o.stream;
     req->forced_form = o.form;
-    if (cudaEventCreateWithFlags(&req->done, cudaEventDisableTiming) != cudaSuccess) {
+    if (gbx_event_create(&req->done) != cudaSuccess) {
         cudaGetLastError();
         req->done = nullptr;
     }
@@ -1135,7 +1144,7 @@ extern "C" int gbx_partitioned_init(gbx_request_t forward, int npart, const int6
     }
     for (int k = 0; k < npart && rc == GBX_SUCCESS; k++) {
         cudaEvent_t ev;
-        if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) { rc = GBX_ERR_CUDA; break; }
+        if (gbx_event_create(&ev) != cudaSuccess) { rc = GBX_ERR_CUDA; break; }
         req->part_ev.push_back(ev);
     }
     if (rc != GBX_SUCCESS) {
@@ -1389,7 +1398,7 @@ extern "C" int gbx_startall(int count, gbx_request_t *reqs) {
             if (r->max_ctas > 0) cap = cap > 0 ? std::min(cap, r->max_ctas) : r->max_ctas;
         }
         int rc = build_levels(b->mem, ops, dts, b->launches, 1, st, tune, cap);
-        if (rc == GBX_SUCCESS && cudaEventCreateWithFlags(&b->done, cudaEventDisableTiming) != cudaSuccess)
+        if (rc == GBX_SUCCESS && gbx_event_create(&b->done) != cudaSuccess)
             rc = GBX_ERR_CUDA;
         if (rc == GBX_SUCCESS && !b->launches.empty()) rc = capture(b->launches, &b->exec);
         if (rc != GBX_SUCCESS) {
@@ -1453,9 +1462,9 @@ static int host_streams(gbx_request_s *req) {
     if (req->host_up) return GBX_SUCCESS;
     GBX_CUDA_TRY(cudaStreamCreateWithFlags(&req->host_up, cudaStreamNonBlocking));
     GBX_CUDA_TRY(cudaStreamCreateWithFlags(&req->host_down, cudaStreamNonBlocking));
-    GBX_CUDA_TRY(cudaEventCreateWithFlags(&req->host_up_ev, cudaEventDisableTiming));
-    GBX_CUDA_TRY(cudaEventCreateWithFlags(&req->host_down_ev, cudaEventDisableTiming));
-    GBX_CUDA_TRY(cudaEventCreateWithFlags(&req->host_mark, cudaEventDisableTiming));
+    GBX_CUDA_TRY(gbx_event_create(&req->host_up_ev));
+    GBX_CUDA_TRY(gbx_event_create(&req->host_down_ev));
+    GBX_CUDA_TRY(gbx_event_create(&req->host_mark));
     return GBX_SUCCESS;
 }
 

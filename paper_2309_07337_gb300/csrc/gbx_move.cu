@@ -842,8 +842,13 @@ __global__ void __launch_bounds__(NT, PS) gbx_stream_kernel(const CopyDesc *cons
 // producer warp plus consumers), stages, chunks per consumer thread per pass, CTAs per SM
 // (the launch bounds hold the registers to what that many CTAs need; shared memory per SM
 // is at most 4 x 4 x 8,256 = 132 KB).
+// Block 128 selects the narrow shape, 160 threads x 4 stages (3 for two-index copies) x 8
+// CTAs per SM with 8 chunks per thread in flight: offered only where every op has one chunk
+// per element (ONE) of at most 8 bytes, whose kernel fits its 48 registers; the tuner never
+// gives it other ops.
 struct StreamShape { int nt, stages, u, per_sm; };
 static StreamShape stream_shape(int block) {
+    if (block <= 128) return {160, 4, 8, 8};
     if (block <= 256) return {288, 4, 4, 4};
     return {544, 6, 2, 2};
 }
@@ -852,9 +857,17 @@ template <int VEC, int FORM, bool ONE>
 static cudaError_t stream_launch_v(int block, int grid, cudaStream_t st, const CopyDesc *const *ops,
                                    const int64_t *prefix, int nops, int64_t n) {
     const StreamShape h = stream_shape(block);
-    const size_t smem = (size_t)h.stages * GBX_STREAM_IDX * (FORM == 3 ? 2 : 1);
-    if (h.nt == 288) gbx_stream_kernel<VEC, FORM, 288, 4, 4, 4, ONE><<<grid, 288, smem, st>>>(ops, prefix, nops, n);
-    else gbx_stream_kernel<VEC, FORM, 544, 6, 2, 2, ONE><<<grid, 544, smem, st>>>(ops, prefix, nops, n);
+    constexpr int SC = FORM == 3 ? 3 : 4;   // stages of the narrow shape
+    const size_t smem = (size_t)(h.nt == 160 ? SC : h.stages) * GBX_STREAM_IDX * (FORM == 3 ? 2 : 1);
+    if (h.nt == 160) {
+        if constexpr (ONE && VEC <= 8)
+            gbx_stream_kernel<VEC, FORM, 160, SC, 8, 8, ONE><<<grid, 160, smem, st>>>(ops, prefix, nops, n);
+        else
+            return cudaErrorInvalidValue;   // never chosen: only one-chunk ops of vectors up to 8 bytes
+    } else if (h.nt == 288)
+        gbx_stream_kernel<VEC, FORM, 288, 4, 4, 4, ONE><<<grid, 288, smem, st>>>(ops, prefix, nops, n);
+    else
+        gbx_stream_kernel<VEC, FORM, 544, 6, 2, 2, ONE><<<grid, 544, smem, st>>>(ops, prefix, nops, n);
     return cudaGetLastError();
 }
 
@@ -889,6 +902,13 @@ static cudaError_t stream_attr_o() {
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(gbx_stream_kernel<VEC, FORM, 544, 6, 2, 2, ONE>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, 6 * GBX_STREAM_IDX * (FORM == 3 ? 2 : 1));
+    if constexpr (ONE && VEC <= 8) {
+        constexpr int SC = FORM == 3 ? 3 : 4;
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(gbx_stream_kernel<VEC, FORM, 160, SC, 8, 8, ONE>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     SC * GBX_STREAM_IDX * (FORM == 3 ? 2 : 1));
+    }
     return e;
 }
 
@@ -1355,8 +1375,10 @@ cudaError_t gbx_launch_copy(const CopyDesc *const *ops, const int64_t *tile_pref
     if (flat == 9) {   // scatter form: a "tile" is one source window
         return scatter_launch(block, clamp_grid(grid, total_tiles), st, ops, tile_prefix, nops, total_tiles);
     }
-    if (flat >= 10 && flat <= 13)   // stream forms: the flat forms' tiles, indices through shared memory
+    if (flat >= 10 && flat <= 13) {   // stream forms: the flat forms' tiles, indices through shared memory
+        if (block <= 128 && !(flat >= 12 && vec <= 8)) block = 256;   // the narrow shape needs ONE, vec <= 8
         return stream_launch(vec, flat, block, clamp_grid(grid, total_tiles), st, ops, tile_prefix, nops, total_tiles);
+    }
     if ((flat == 5 || flat == 7) && (nops > 1 || vec == 0)) flat -= 4;   // the pipelined kernels take one op
     block = pipe_block(flat, block);
     CopyFn f = copy_fn(vec, block, flat);

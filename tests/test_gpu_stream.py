@@ -46,7 +46,7 @@ def test_random_standard_forward(seed):
     x = pt.random_bytes(p.sendbuf_bytes, seed)
     init = pt.random_bytes(p.recvbuf_bytes, seed + 1)
     want = oracle.standard(p, x, init)
-    for info in ("stream=2", "stream=2;block=512", "stream=2;graph=0;max_ctas=3"):
+    for info in ("stream=2", "stream=2;block=512", "stream=2;block=128", "stream=2;graph=0;max_ctas=3"):
         got, ex = forward(p, x, "standard", info=info, recv_init=init)
         assert_bytes_equal(got, want, f"{p.name} {info}")
         if packed and p.volume > 0:
@@ -108,9 +108,10 @@ def test_spmv_halo_full_size():
     x = pt.spmv_x(p, 3)
     want = oracle.standard(p, x)
     for alg in ("standard", "locality"):
-        got, ex = forward(p, x, alg, info="stream=2")
-        assert ex.info()["copy_forms"] & STREAM
-        assert_bytes_equal(got, want, alg)
+        for info in ("stream=2", "stream=2;block=128"):   # tuned shape; the narrow one-chunk shape
+            got, ex = forward(p, x, alg, info=info)
+            assert ex.info()["copy_forms"] & STREAM
+            assert_bytes_equal(got, want, f"{alg} {info}")
 
 
 def test_stencil_256cube_forward_backward():
