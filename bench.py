@@ -1051,6 +1051,22 @@ def _batched(gbx, torch, peak, reps, nvtx=True, count=64, info=""):
         gbx.startall(g_reqs)
         gbx.waitall(g_reqs)
     tp, tb, ratio = paired(torch, plain3, batched3, reps=reps)
+    # the batch's device time alone: a bounded sleep kernel holds the stream while the host
+    # enqueues the start, so the first event is stamped when the sleep ends and the batch's
+    # graph begins right after it (no host latency inside the interval)
+    td = []
+    for _ in range(max(reps, 5)):
+        torch.cuda.synchronize()
+        torch.cuda._sleep(400_000)   # about 0.2 ms at 2 GHz
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        gbx.startall(g_reqs)
+        e1.record()
+        gbx.waitall(g_reqs)
+        e1.synchronize()
+        td.append(e0.elapsed_time(e1))
+    td = spread(td)
     same = all(torch.equal(b[1], b[2]) for b in bufs)
     if nvtx:
         torch.cuda.synchronize()
@@ -1064,12 +1080,15 @@ def _batched(gbx, torch, peak, reps, nvtx=True, count=64, info=""):
            "speedup_p90": ratio["p90"],
            "batched_user_GBps": Btot / (ms * 1e-3) / 1e9, "batched_algo_GBps": algo / (ms * 1e-3) / 1e9,
            "frac_of_measured_hbm": algo / (ms * 1e-3) / 1e9 / peak,
+           "batched_device_ms": td, "device_algo_GBps": algo / (td["median"] * 1e-3) / 1e9,
+           "device_frac_of_measured_hbm": algo / (td["median"] * 1e-3) / 1e9 / peak,
            "identical_results": same, "generation_s": gen_s,
            "dtypes": {d: sum(1 for q in pats if q.dtype == d) for d in ("f32", "f64")},
            "plain": "eager launches, start+wait per pattern (host wait each)",
            "batched": "startall of 64 requests: one CUDA graph, one fused launch per kernel class",
            "timing": "interleaved pairs (plain, batched), CUDA events around each including the host waits; "
-                     "median and p10/p90; the batch's buffers exceed L2"}
+                     "median and p10/p90; the batch's buffers exceed L2; batched_device_ms: the batch's graph "
+                     "alone on the stream (events around startall behind a sleep kernel, no host latency)"}
     del bufs, g_reqs, p_reqs
     torch.cuda.empty_cache()
     return res

@@ -420,8 +420,9 @@ int gbx_backward_init(gbx_request_t forward, const void *grad_recv, void *grad_s
 int gbx_start(gbx_request_t request);
 
 /* MPIX_Wait (section 2.2, Listing 4): blocks the host until the started exchange has
- * finished on the GPU, polling with a limit of timeout_ms; returns GBX_ERR_TIMEOUT
- * (request still active) when the limit passes.  An inactive request returns at once.
+ * finished on the GPU, polling with a limit of timeout_ms (the calling thread polls
+ * without sleeping for the first 20 ms, then sleeps 20 us between polls); returns
+ * GBX_ERR_TIMEOUT (request still active) when the limit passes.  An inactive request returns at once.
  * When the exchange finished but one of its kernels gave up a bounded wait (see
  * GBX_ERR_DEVICE_WAIT and info wait_limit), returns GBX_ERR_DEVICE_WAIT and clears the
  * request's status word; the request is inactive either way.  On an inactive request it

@@ -17,6 +17,8 @@ struct Batch {
     std::vector<gbx_request_s *> members;
     DevPool mem;
     std::vector<LevelLaunch> launches;
+    std::vector<HostOp> widened;   // batch-owned copies of ops re-cut to their widest vector
+    std::vector<std::pair<gbx_request_s *, size_t>> widened_of;   // (request, op index) of each
     cudaGraphExec_t exec = nullptr;
     cudaEvent_t done = nullptr;
 };
@@ -1325,18 +1327,22 @@ extern "C" int gbx_test(gbx_request_t req, int *flag) {
     return take_status(req);
 }
 
+#define GBX_WAIT_SPIN_MS 20.0
+
 extern "C" int gbx_wait(gbx_request_t req) {
     if (!req) return GBX_ERR_ARG;
     if (!req->active) return take_status(req);
+    // polls (yielding the core) for the first GBX_WAIT_SPIN_MS, then sleeps between polls: a
+    // sleeping thread wakes tens of microseconds after the work ends (the kernel's timer
+    // slack), which would show in every start + wait of a millisecond-long exchange
     const auto t0 = std::chrono::steady_clock::now();
-    int spins = 0;
     for (;;) {
         int flag = 0;
         const int rc = gbx_test(req, &flag);
         if (rc != GBX_SUCCESS || flag) return rc;
         const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
         if (ms > req->timeout_ms) return GBX_ERR_TIMEOUT;
-        if (++spins > 64) std::this_thread::sleep_for(std::chrono::microseconds(20));
+        if (ms > GBX_WAIT_SPIN_MS) std::this_thread::sleep_for(std::chrono::microseconds(20));
         else std::this_thread::yield();
     }
 }
@@ -1369,6 +1375,36 @@ extern "C" int gbx_waitall(int count, gbx_request_t *reqs) {
     return first;
 }
 
+// A batch pools copies by vector width.  An op whose own tuning kept a narrower vector than its
+// alignment allows (common for small ops, whose timings are noise) would add a launch of its own;
+// in a batch it runs at its widest vector instead, through a batch-owned descriptor (same
+// elements, same bytes, its own tile table), so that it joins its dtype's main launch.
+static int widen_candidate(const HostOp &op) {
+    const uintptr_t a = (uintptr_t)op.cd.src | (uintptr_t)op.cd.dst | (uintptr_t)op.cd.src2;
+    return op.kind == 0 && op.flat_ok && op.cd.flat != 8 && op.cd.flat != 9 && op.cd.vec < op.max_vec &&
+           op.max_vec >= 4 && (a & (uintptr_t)(op.max_vec - 1)) == 0;
+}
+
+static int widen_op(DevPool &mem, HostOp &c, int64_t s, cudaStream_t st) {
+    const int vec = c.max_vec, cpe = (int)(s / vec);
+    int shift = -1;
+    if ((cpe & (cpe - 1)) == 0) { shift = 0; while ((1 << shift) < cpe) shift++; }
+    CopyDesc &d = c.cd;
+    d.vec = vec; d.cpe = cpe; d.cpe_shift = shift;
+    d.cpe_magic = shift >= 0 ? 0u : (uint32_t)(((1ull << 32) + (uint64_t)cpe - 1) / (uint64_t)cpe);
+    d.nchunks = d.nelem * cpe;
+    d.ntiles = ceil_div(d.nchunks, GBX_TILE);
+    // segment and pipelined forms run as the plain flat form the op also has (stream forms stay)
+    if (d.flat < 10) d.flat = (d.flat & 3) == 3 ? 3 : 1;
+    GBX_TRY(mem.get(&c.d_tile_e0, d.ntiles + 1));
+    d.tile_e0 = c.d_tile_e0;
+    d.tile_seg = nullptr;
+    GBX_TRY(gbx_build_tile_meta(nullptr, 0, cpe, d.ntiles, nullptr, c.d_tile_e0, st));
+    GBX_TRY(mem.alloc(&c.d_desc, sizeof(CopyDesc)));
+    GBX_CUDA_TRY(cudaMemcpyAsync(c.d_desc, &d, sizeof(CopyDesc), cudaMemcpyHostToDevice, st));
+    return GBX_SUCCESS;
+}
+
 extern "C" int gbx_startall(int count, gbx_request_t *reqs) {
     if (count <= 0 || !reqs) return GBX_ERR_ARG;
     GbxRange range("gbx.startall");
@@ -1390,8 +1426,27 @@ extern "C" int gbx_startall(int count, gbx_request_t *reqs) {
         cudaStream_t st = reqs[0]->stream;
         std::vector<HostOp *> ops;
         std::vector<int> dts;
+        int rc0 = GBX_SUCCESS;
+        size_t nwide = 0;
         for (gbx_request_s *r : key)
-            for (HostOp &op : r->ops) { ops.push_back(&op); dts.push_back(r->dtype); }
+            for (HostOp &op : r->ops) nwide += widen_candidate(op);
+        b->widened.reserve(nwide);   // stable addresses for the pointers below
+        for (gbx_request_s *r : key)
+            for (HostOp &op : r->ops) {
+                HostOp *use = &op;
+                if (rc0 == GBX_SUCCESS && widen_candidate(op)) {
+                    b->widened.push_back(op);
+                    b->widened_of.emplace_back(r, (size_t)(&op - r->ops.data()));
+                    rc0 = widen_op(b->mem, b->widened.back(), r->elem_size, st);
+                    use = &b->widened.back();
+                }
+                ops.push_back(use);
+                dts.push_back(r->dtype);
+            }
+        if (rc0 != GBX_SUCCESS) {
+            delete b;
+            return rc0;
+        }
         int tune = 1, cap = 0;
         for (gbx_request_s *r : key) {
             tune &= r->autotune && !r->forced_block;
@@ -1455,6 +1510,25 @@ extern "C" int gbx_request_bind(gbx_request_t req, const void *src, void *dst) {
     }
     req->src = ns;
     req->dst = nd;
+    // cached batches hold their own widened copies of some of these ops: they follow the new
+    // buffers, and a batch whose copy the new buffers no longer align is rebuilt at the next
+    // gbx_startall
+    std::vector<Batch *> stale;
+    for (Batch *b : req->batches)
+        for (size_t k = 0; k < b->widened.size(); k++) {
+            if (b->widened_of[k].first != req) continue;
+            const HostOp &o = req->ops[b->widened_of[k].second];
+            HostOp &c = b->widened[k];
+            c.cd.src = o.cd.src;
+            c.cd.dst = o.cd.dst;
+            if (((uintptr_t)c.cd.src | (uintptr_t)c.cd.dst) & (uintptr_t)(c.cd.vec - 1)) {
+                stale.push_back(b);
+                break;
+            }
+            GBX_CUDA_TRY(cudaMemcpyAsync(c.d_desc, &c.cd, sizeof(CopyDesc), cudaMemcpyHostToDevice, req->stream));
+        }
+    for (Batch *b : stale) destroy_batch(b);
+    GBX_CUDA_TRY(cudaStreamSynchronize(req->stream));
     return GBX_SUCCESS;
 }
 

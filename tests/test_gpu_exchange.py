@@ -223,6 +223,50 @@ def test_startall_mixed_sizes_matches_individual():
             assert_bytes_equal(e.recv.cpu().numpy(), oracle.standard(p, x), f"batched {p.name}")
 
 
+def test_startall_rebind_moves_batch_to_new_buffers():
+    """A batch keeps its launches across rebinds: every request of a started batch is rebound
+    to new buffers, first as aligned as the old ones, then offset by half an element (accepted
+    only where the request's tuned vector allows it); each start writes the oracle's bytes into
+    the buffers bound at that moment."""
+    pats = [pt.random_pattern(540 + i, elem_size=[8, 16, 64, 4][i % 4]) for i in range(8)]
+    xs = [pt.random_bytes(p.sendbuf_bytes, 40 + i) for i, p in enumerate(pats)]
+    bound = [torch.zeros(p.recvbuf_bytes, dtype=torch.uint8, device="cuda") for p in pats]
+    exs = [gbx.Exchange(p, dev_bytes(x), r, algorithm="locality" if i % 2 else "standard")
+           for i, (p, x, r) in enumerate(zip(pats, xs, bound))]
+    reqs = [e.request for e in exs]
+
+    def run(tag):
+        for r in bound:
+            r.fill_(0x5A)
+        gbx.startall(reqs)
+        gbx.waitall(reqs)
+        for p, x, r in zip(pats, xs, bound):
+            init = np.full(p.recvbuf_bytes, 0x5A, dtype=np.uint8)   # gaps keep this byte
+            assert_bytes_equal(r.cpu().numpy(), oracle.standard(p, x, init), f"{tag} {p.name}")
+
+    run("first")
+    for i, (p, x) in enumerate(zip(pats, xs)):
+        s2 = dev_bytes(x)
+        r2 = torch.empty(p.recvbuf_bytes, dtype=torch.uint8, device="cuda")
+        reqs[i].bind(s2, r2)
+        bound[i] = r2
+    run("rebound")
+    moved = 0
+    for i, (p, x) in enumerate(zip(pats, xs)):
+        off = p.elem_size // 2
+        s3 = torch.empty(p.sendbuf_bytes + off, dtype=torch.uint8, device="cuda")
+        r3 = torch.empty(p.recvbuf_bytes + off, dtype=torch.uint8, device="cuda")
+        s3[off:].copy_(dev_bytes(x))
+        try:
+            reqs[i].bind(s3[off:], r3[off:])
+        except gbx.GbxError as e:
+            assert e.code == gbx.ERR_ARG   # the request's vector needs more alignment
+            continue
+        bound[i] = r3[off:]
+        moved += 1
+    run(f"offset ({moved} of {len(reqs)} moved)")
+
+
 def test_host_buffers_end_to_end():
     p = pt.config1()
     x = payload(p, 5)
