@@ -1124,6 +1124,9 @@ def run_sweep(args):
                              "frac_of_measured_hbm": info["algo_bytes"] / (ms * 1e-3) / 1e9 / peak,
                              "vec": info["vec_bytes"], "block": info["block"], "launches": info["launches"]}
             row["identical"] = bool(torch.equal(h1.view(torch.uint8), h2.view(torch.uint8)))
+            lf = line_floor(p)["total"]
+            row["line_floor_bytes"] = lf
+            row["standard"]["frac_of_line_floor"] = lf / (row["standard"]["ms"] * 1e-3) / 1e9 / peak
             rows.append(row)
             print(json.dumps(row), file=sys.stderr)
             del a, b, dp, field, h1, h2
