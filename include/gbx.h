@@ -451,8 +451,13 @@ int gbx_waitall(int count, gbx_request_t *requests);
 
 /* Re-binds the data buffers of an inactive request without redoing setup: `src` is the
  * new send buffer (grad_recv for a backward request), `dst` the new receive buffer
- * (grad_send); NULL keeps the old one.  The new buffers must have the sizes and at
- * least the alignment of the old ones.  Stream-ordered on the request's stream. */
+ * (grad_send); NULL keeps the old one.  The new buffers must have the sizes of the old
+ * ones; one aligned below the vector width a move program of the request was tuned to
+ * gives GBX_ERR_ARG (the old binding stays).  Batches of gbx_startall that hold their own
+ * wider copies of the request's programs move them to the new buffers, and a batch whose
+ * copies the new buffers no longer align is rebuilt at its next gbx_startall.  The new
+ * descriptors are uploaded on the request's stream; a request that belongs to a cached
+ * batch (which may run on another request's stream) synchronises that stream first. */
 int gbx_request_bind(gbx_request_t request, const void *src, void *dst);
 
 /* One exchange on HOST buffers: copies host_src (the whole bound source buffer, pinned

@@ -1527,8 +1527,10 @@ extern "C" int gbx_request_bind(gbx_request_t req, const void *src, void *dst) {
             }
             GBX_CUDA_TRY(cudaMemcpyAsync(c.d_desc, &c.cd, sizeof(CopyDesc), cudaMemcpyHostToDevice, req->stream));
         }
+    // a batch may run on another request's stream: its next start must see the new descriptors
+    const bool batched = !req->batches.empty();
     for (Batch *b : stale) destroy_batch(b);
-    GBX_CUDA_TRY(cudaStreamSynchronize(req->stream));
+    if (batched) GBX_CUDA_TRY(cudaStreamSynchronize(req->stream));
     return GBX_SUCCESS;
 }
 
