@@ -451,6 +451,10 @@ def run_ours(args):
     forms["locality"].update({"U": infos[1]["U"], "node_pairs": infos[1]["node_pairs"],
                               "V_direct": infos[1]["V_direct"], "V_inter": infos[1]["V_inter"]})
     forms["backward"].update({"rows": rows, "terms": infos[2]["terms"]})
+    lfl = locality_line_floor(p)
+    if lfl is not None:
+        forms["locality"].update({"line_floor_bytes": lfl["total"], "line_floor": lfl,
+                                  "frac_of_line_floor": lfl["total"] / (per[1] * 1e-3) / 1e9 / peak})
     bfl = bwd_line_floor(p, infos[2])
     forms["backward"].update({"line_floor_bytes": bfl["total"], "line_floor": bfl,
                               "frac_of_line_floor": bfl["total"] / (per[2] * 1e-3) / 1e9 / peak,
@@ -1156,6 +1160,48 @@ def line_floor(p):
     lines = sorted_unique(np.concatenate([off >> 7, (off + p.elem_size - 1) >> 7]))
     return {"read_lines_bytes": int(len(lines)) * 128, "index_bytes": 4 * V, "write_bytes": V * p.elem_size,
             "total": int(len(lines)) * 128 + 4 * V + V * p.elem_size}
+
+
+def locality_line_floor(p):
+    """The same floor for the locality form's three launches: (1) every 128-byte line of the
+    send buffer holding a value some node pair carries is read once, 4 bytes of index per
+    aggregate slot, the send aggregates written; (2) the aggregates read and written once
+    (contiguous blocks); (3) every line holding a value sent within its node read once, the
+    receive aggregates read, 4 bytes of index per receive slot, the receive buffer written.
+    The aggregate slots are the distinct (sender node, receiver node, global index) triples.
+    None for a pattern without global indices."""
+    if p.global_sidx is None or p.send_slot_ptr is None:
+        return None
+    s = p.elem_size
+    sc = np.asarray(p.sendcounts, dtype=np.int64)
+    owner = np.repeat(np.arange(p.P), np.diff(np.asarray(p.out_ptr)))
+    V = int(sc.sum())
+    first = np.cumsum(sc) - sc
+    slot = np.repeat(np.asarray(p.sdispls, dtype=np.int64), sc) + (np.arange(V) - np.repeat(first, sc))
+    r = np.repeat(owner, sc)
+    d = np.repeat(np.asarray(p.dests, dtype=np.int64), sc)
+    sp = np.asarray(p.send_slot_ptr, dtype=np.int64)[r] + slot
+    el = slot if p.send_idx is None else np.asarray(p.send_idx)[sp]
+    off = np.asarray(p.send_base)[r] + el.astype(np.int64) * s
+    g = np.asarray(p.global_sidx, dtype=np.int64)[sp]
+    nn = (p.P + p.ppn - 1) // p.ppn
+    inter = (r // p.ppn) != (d // p.ppn)
+    gmax = int(g.max()) + 1 if V else 1
+    if nn * nn * gmax >= (1 << 62):
+        return None
+    key = ((r // p.ppn) * nn + d // p.ppn)[inter] * gmax + g[inter]
+    order = np.argsort(key, kind="stable")
+    k = key[order]
+    new = np.concatenate([[True], k[1:] != k[:-1]]) if len(k) else np.zeros(0, bool)
+    U = int(new.sum())
+
+    def lines(o):
+        return 128 * len(sorted_unique(np.concatenate([o >> 7, (o + s - 1) >> 7])))
+    st1 = lines(off[inter][order][new]) + 4 * U + s * U
+    st2 = 2 * s * U
+    st3 = lines(off[~inter]) + s * U + 4 * V + s * V
+    return {"U": U, "V_direct": int((~inter).sum()), "step1": st1, "step2": st2, "step3": st3,
+            "total": st1 + st2 + st3}
 
 
 def _match_edges(p):
