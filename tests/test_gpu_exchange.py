@@ -223,6 +223,39 @@ def test_startall_mixed_sizes_matches_individual():
             assert_bytes_equal(e.recv.cpu().numpy(), oracle.standard(p, x), f"batched {p.name}")
 
 
+@pytest.mark.parametrize("seed", range(4))
+def test_startall_random_forward_and_backward_batch(seed):
+    """One gbx_startall of random forward requests (both forms, fp32 and fp64, indexed and
+    packed sends) and the backward requests of the same patterns (accumulating on every other
+    one), started together twice: every receive buffer equals the oracle's exchange and every
+    gradient the oracle's reverse exchange in the order of its form, byte for byte."""
+    pats = [pt.random_pattern(1300 + 10 * seed + i, dtype="f64" if i % 2 else "f32", indexed=bool(i % 3))
+            for i in range(8)]
+    items = []
+    for i, q in enumerate(pats):
+        alg, form = ("locality", 1) if i % 2 == 0 else ("standard", 0)
+        x = payload(q, 50 + i)
+        g = grad_payload(q, 60 + i)
+        old = payload(q, 70 + i)
+        acc = i % 4 >= 2
+        send, recv = dev_bytes(x), torch.zeros(q.recvbuf_bytes, dtype=torch.uint8, device="cuda")
+        ex = gbx.Exchange(q, send, recv, algorithm=alg)
+        gr, gs = dev_bytes(g), dev_bytes(old)
+        b = gbx.backward_init(ex.request, gr, gs, accumulate=acc)
+        items.append((q, x, g, old, acc, form, recv, gs, ex, b))
+    reqs = [it[8].request for it in items] + [it[9] for it in items]
+    for rep in range(2):
+        for q, x, g, old, acc, form, recv, gs, ex, b in items:
+            recv.zero_()
+            gs.copy_(dev_bytes(old))
+        gbx.startall(reqs)
+        gbx.waitall(reqs)
+        for q, x, g, old, acc, form, recv, gs, ex, b in items:
+            assert_bytes_equal(recv.cpu().numpy(), oracle.standard(q, x), f"{q.name} forward #{rep}")
+            want = oracle.backward(q, g, old, form=form, accumulate=acc)
+            assert_bytes_equal(gs.cpu().numpy(), want, f"{q.name} backward acc={acc} #{rep}")
+
+
 def test_startall_rebind_moves_batch_to_new_buffers():
     """A batch keeps its launches across rebinds: every request of a started batch is rebound
     to new buffers, first as aligned as the old ones, then offset by half an element (accepted
