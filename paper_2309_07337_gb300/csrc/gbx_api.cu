@@ -222,7 +222,7 @@ int gbx_make_copy_op(gbx_request_s *req, int level, const char *src, int src_rol
     }
     if (req->piece > 0) {
         // pieces in ascending source address (same elements, same bytes)
-        const int64_t src_bytes = src_role == ROLE_SRC ? req->src_bytes : 2 * req->U * req->elem_size;
+        const int64_t src_bytes = src_role == ROLE_SRC ? req->src_bytes : 2 * req->Ur * req->elem_size;
         Seg *ord = nullptr;
         int64_t nord = 0;
         GBX_TRY(gbx_order_by_source(req, segs, nseg, idx, nelem, src_bytes, req->piece, &ord, &nord));
@@ -262,7 +262,8 @@ int gbx_make_copy_op(gbx_request_s *req, int level, const char *src, int src_rol
         op.stream_ok = op.flat_ok && stream_ok_for(req, op.d_flat_idx, nullptr, op.max_vec);
     }
     if (req->allow_bulk && !host_mem(src) && !host_mem(dst)) {
-        GBX_TRY(gbx_make_bulk(req, segs, nseg, nelem, &op.d_bulk, &op.nbulk, &op.bulk_ok));
+        GBX_TRY(gbx_make_bulk(req, segs, nseg, nelem, src_role == ROLE_AGG && dst_role == ROLE_AGG, &op.d_bulk,
+                              &op.nbulk, &op.bulk_ok));
         d.bulk = op.d_bulk;
         d.nbulk = op.nbulk;
         op.algo_bytes_bulk = 2 * nelem * req->elem_size + op.nbulk * (int64_t)sizeof(BulkTask);
@@ -593,7 +594,9 @@ static int tune_op(gbx_request_s *req, HostOp &op) {
     else forms.push_back(0);
     if (op.kind == 0 && op.stream_ok && (op.flat_only || (op.flat_ok && req->forced_flat != 0)))
         forms.push_back((op.cd.flat & 3) == 3 ? 11 : 10);
-    if (op.kind == 0 && op.bulk_ok && req->forced_flat != 1 && op.max_vec == 16) forms.push_back(8);
+    // (bulk_ok implies 16-byte aligned pieces; between the library's own aggregates the element
+    // size need not be a multiple of 16)
+    if (op.kind == 0 && op.bulk_ok && req->forced_flat != 1) forms.push_back(8);
     if (op.kind == 0 && op.scat_ok && op.max_vec == 16) forms.push_back(9);
     if (op.kind == 0 && op.stream_ok && req->allow_stream == 2) forms.assign(1, (op.cd.flat & 3) == 3 ? 11 : 10);
     if (op.kind == 0 && op.bulk_ok && req->allow_bulk == 2) forms.assign(1, 8);   // forced where it applies
@@ -607,7 +610,9 @@ static int tune_op(gbx_request_s *req, HostOp &op) {
         const bool pipe = op.kind == 0 && form >= 4 && form < 8, bulk = op.kind == 0 && (form == 8 || form == 9);
         const bool strm = op.kind == 0 ? form >= 10 : form == 1;
         // (the op's tile tables are sized for min_vec: no width below it)
-        for (int vec = op.max_vec; vec >= (bulk ? 16 : strm ? std::max(4, op.min_vec) : op.min_vec); vec >>= 1) {
+        // (the bulk and scatter kernels do not use the vector width: one pass, at max_vec)
+        for (int vec = op.max_vec; vec >= (bulk ? op.max_vec : strm ? std::max(4, op.min_vec) : op.min_vec);
+             vec >>= 1) {
             GBX_TRY(set_vec(req, op, vec));
             // stream forms: persistent grid only; block 256 and 512 select the two wide shapes,
             // block 128 the narrow one, offered only with one chunk per element (cpe == 1)
@@ -852,7 +857,7 @@ static void fill_info(gbx_request_s *req) {
 static int finalize(gbx_request_s *req) {
     {
         GbxRange r("gbx.setup.validate");
-        GBX_TRY(gbx_validate_program(req, req->agg ? 2 * req->U * req->elem_size : 0));
+        GBX_TRY(gbx_validate_program(req, req->agg ? 2 * req->Ur * req->elem_size : 0));
     }
     {
         GbxRange r("gbx.setup.tune");

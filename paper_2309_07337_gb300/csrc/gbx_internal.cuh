@@ -237,6 +237,8 @@ struct gbx_request_s {
     int64_t *val_pos;        // per element (standard numbering): aggregate slot, -1 if direct
     int64_t *agg_rep_off;    // per aggregate slot: byte offset of its representative source
     int32_t *agg_dst_node;   // per aggregate slot: destination node
+    int64_t Ur;              // first slot of the receive aggregate (U rounded up so that it starts
+                             // 16-byte aligned: both halves of `agg` hold Ur slots)
     Seg *segs_pair;          // per node pair: aggregate block (v0 = first slot, count by next)
     int64_t npairs;
     char *agg;               // locality scratch: send aggregate | receive aggregate
@@ -287,7 +289,8 @@ int gbx_split_single_rows(gbx_request_s *req, const int64_t *row_ptr, const int6
 int gbx_sort_pairs_by_source(gbx_request_s *req, int32_t *gs, int32_t *gd, int64_t n);
 int gbx_make_flat2_op(gbx_request_s *req, int level, const char *src, int src_role, const char *src2, int src2_role,
                       char *dst, int dst_role, const int32_t *gs, const int32_t *gd, int64_t nelem);
-int gbx_make_bulk(gbx_request_s *req, const Seg *segs, int64_t nseg, int64_t nelem, BulkTask **out, int64_t *n,
+int64_t agg_r_slot(int64_t U, int64_t s);
+int gbx_make_bulk(gbx_request_s *req, const Seg *segs, int64_t nseg, int64_t nelem, bool owned, BulkTask **out, int64_t *n,
                   int *ok);
 int gbx_bulk_prepare(void);
 int gbx_scatter_prepare(void);

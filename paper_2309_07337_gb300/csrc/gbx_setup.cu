@@ -522,6 +522,29 @@ __global__ void dup_check_kernel(const char *src, const int64_t *segv0, int64_t 
     }
 }
 
+// First slot of the receive aggregate: U rounded up to the next count of s-byte slots that
+// ends on a 16-byte boundary, so that both halves of the aggregate buffer (send aggregate at
+// slot 0, receive aggregate at this slot) start 16-byte aligned and hold the same number of
+// slots.  The padding slots are never read by the exchange.
+int64_t agg_r_slot(int64_t U, int64_t s) {
+    const int64_t m = 16 / std::max<int64_t>(1, std::min<int64_t>(16, s & -s));   // 16 / gcd(s, 16)
+    return (U + m - 1) / m * m;
+}
+
+// One contiguous segment (copy of the aggregate half at byte offset `from` to the one at
+// `to`, element space starting at 0), in device memory owned by `mem`.
+static int pair_block_seg(DevPool &mem, int64_t from, int64_t to, cudaStream_t st, Seg **out) {
+    Seg h;
+    h.v0 = 0;
+    h.dst_off = to;
+    h.src_off = from;
+    h.idx_off = -1;
+    GBX_TRY(mem.get(out, 1));
+    GBX_CUDA_TRY(cudaMemcpyAsync(*out, &h, sizeof(Seg), cudaMemcpyHostToDevice, st));
+    GBX_CUDA_TRY(cudaStreamSynchronize(st));
+    return GBX_SUCCESS;
+}
+
 int gbx_setup_forward(gbx_request_s *req, const int64_t *send_base, const int *sendcounts, const int *sdispls,
                       const int64_t *send_slot_ptr, const int *send_idx, const int64_t *recv_base,
                       const int *recvcounts, const int *rdispls, const int64_t *recv_slot_ptr,
@@ -764,7 +787,8 @@ int gbx_setup_forward(gbx_request_s *req, const int64_t *send_base, const int *s
         int64_t *dm1;
         GBX_TRY(ws.get(&dm1, 1));
         GBX_CUDA_TRY(cudaMemsetAsync(dm1, 0, 8, st));
-        seg12_kernel<<<grid_of(U), SETUP_T, 0, st>>>(a, key2, f1, p1, f2, p2, U, rb, U * s, seg1, seg2, dm1);
+        seg12_kernel<<<grid_of(U), SETUP_T, 0, st>>>(a, key2, f1, p1, f2, p2, U, rb, agg_r_slot(U, s) * s, seg1,
+                                                     seg2, dm1);
         GBX_CUDA_TRY(cudaGetLastError());
         GBX_TRY(gbx_read_i64(dm1, &m1, st));
         GBX_TRY(req->mem.get(&idx3, Vx));
@@ -790,7 +814,7 @@ int gbx_setup_forward(gbx_request_s *req, const int64_t *send_base, const int *s
     }
     if (nseg > 0) {
         seg03_kernel<<<grid_of(nseg), SETUP_T, 0, st>>>(req->segs_std, f_intra, v_intra, p_intra, v_inter, p_inter,
-                                                        nseg, U * s, seg0, seg3);
+                                                        nseg, agg_r_slot(U, s) * s, seg0, seg3);
         GBX_CUDA_TRY(cudaGetLastError());
     }
     if (req->check_dup && U > 0) {
@@ -801,12 +825,17 @@ int gbx_setup_forward(gbx_request_s *req, const int64_t *send_base, const int *s
         GBX_TRY(read_err_stage(err, st));
     }
     req->U = U;
+    const int64_t Ur = agg_r_slot(U, s);
+    req->Ur = Ur;
     req->npairs = npairs;
     req->info.U = U;
     req->info.node_pairs = npairs;
     req->info.msgs_step1 = m1;
     req->info.msgs_step3 = m3;
-    if (U > 0) GBX_TRY(req->mem.alloc((void **)&req->agg, (size_t)(2 * U * s)));
+    if (U > 0) {
+        GBX_TRY(req->mem.alloc((void **)&req->agg, (size_t)(2 * Ur * s)));
+        GBX_CUDA_TRY(cudaMemsetAsync(req->agg, 0, (size_t)(2 * Ur * s), st));   // (padding slots stay defined)
+    }
     // When the receive buffer is one contiguous run in receive order, the direct copies and
     // the redistribution become one receive-order flat op of the last level (each element
     // reads the send buffer or the receive aggregate); otherwise direct copies run in level 0
@@ -823,7 +852,7 @@ int gbx_setup_forward(gbx_request_s *req, const int64_t *send_base, const int *s
             GBX_TRY(ws.get(&bad, 1));
             GBX_CUDA_TRY(cudaMemsetAsync(bad, 0, sizeof(int), st));
             loc_final_index_kernel<<<grid_of(V), SETUP_T, 0, st>>>(segv0, nseg, seg_src, req->send_base_copy,
-                                                                   req->srcel, req->val_pos, V, s, U, gtmp, bad);
+                                                                   req->srcel, req->val_pos, V, s, Ur, gtmp, bad);
             GBX_CUDA_TRY(cudaGetLastError());
             int hb = 0;
             GBX_CUDA_TRY(cudaMemcpyAsync(&hb, bad, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -838,7 +867,11 @@ int gbx_setup_forward(gbx_request_s *req, const int64_t *send_base, const int *s
     if (U > 0) {
         GBX_TRY(gbx_make_copy_op(req, 0, req->src, ROLE_SRC, req->agg, ROLE_AGG, seg1, n1, idx1, U, U,
                                  2 * U * s + 4 * U));
-        GBX_TRY(gbx_make_copy_op(req, 1, req->agg, ROLE_AGG, req->agg, ROLE_AGG, seg2, npairs, nullptr, 0, U,
+        // step 2: the node pairs' blocks sit in the same order and at the same offsets in both
+        // aggregates, so together they are one contiguous block S -> R (padding slots included)
+        Seg *seg2m;
+        GBX_TRY(pair_block_seg(req->mem, 0, Ur * s, st, &seg2m));
+        GBX_TRY(gbx_make_copy_op(req, 1, req->agg, ROLE_AGG, req->agg, ROLE_AGG, seg2m, 1, nullptr, 0, Ur,
                                  2 * U * s + npairs * (int64_t)sizeof(Seg)));
         if (combined)
             GBX_TRY(gbx_make_flat_op(req, 2, req->src, ROLE_SRC, req->agg, ROLE_AGG, req->dst, ROLE_DST, gfin, V,
@@ -1009,7 +1042,12 @@ int gbx_setup_backward(gbx_request_s *bwd, int accumulate) {
     bwd->npairs = f->npairs;
     bwd->info.U = U;
     bwd->info.node_pairs = f->npairs;
-    if (U > 0) GBX_TRY(bwd->mem.alloc((void **)&bwd->agg, (size_t)(2 * U * s)));
+    const int64_t Ur = f->Ur;
+    bwd->Ur = Ur;
+    if (U > 0) {
+        GBX_TRY(bwd->mem.alloc((void **)&bwd->agg, (size_t)(2 * Ur * s)));
+        GBX_CUDA_TRY(cudaMemsetAsync(bwd->agg, 0, (size_t)(2 * Ur * s), st));
+    }
     int64_t total_terms = 0;
     if (U > 0) {
         // reverse step 3: rows = aggregate slots, terms = their receive slots in (rank, position)
@@ -1028,24 +1066,16 @@ int gbx_setup_backward(gbx_request_s *bwd, int accumulate) {
         GBX_TRY(bwd->mem.get(&row_out, U));
         GBX_TRY(bwd->mem.get(&terms, Vx + 2));
         // rows write the receive-aggregate half (gR) at U*s + slot*s
-        bwd_terms_kernel<<<grid_of(Vx), SETUP_T, 0, st>>>(k, v, flag, rowid, Vx, f->segs_std, segv0, nseg, s, U * s,
+        bwd_terms_kernel<<<grid_of(Vx), SETUP_T, 0, st>>>(k, v, flag, rowid, Vx, f->segs_std, segv0, nseg, s, Ur * s,
                                                           s, terms, row_ptr, row_out);
         GBX_CUDA_TRY(cudaGetLastError());
         GBX_TRY(finish_rows(row_ptr, U, Vx, st));
         GBX_TRY(gbx_make_fold_op(bwd, 0, bwd->agg, ROLE_AGG, bwd->src, ROLE_SRC, nullptr, ROLE_NONE, row_ptr, row_out,
                                  terms, U, Vx, 0));
-        // reverse step 2: gR -> gS per node pair
+        // reverse step 2: gR -> gS, the node pairs' blocks as one contiguous block
         Seg *rseg2;
-        GBX_TRY(bwd->mem.get(&rseg2, f->npairs));
-        {
-            std::vector<Seg> h(f->npairs);
-            GBX_CUDA_TRY(cudaMemcpyAsync(h.data(), f->segs_pair, sizeof(Seg) * f->npairs, cudaMemcpyDeviceToHost, st));
-            GBX_CUDA_TRY(cudaStreamSynchronize(st));
-            for (auto &sg : h) { std::swap(sg.dst_off, sg.src_off); }
-            GBX_CUDA_TRY(cudaMemcpyAsync(rseg2, h.data(), sizeof(Seg) * f->npairs, cudaMemcpyHostToDevice, st));
-            GBX_CUDA_TRY(cudaStreamSynchronize(st));
-        }
-        GBX_TRY(gbx_make_copy_op(bwd, 1, bwd->agg, ROLE_AGG, bwd->agg, ROLE_AGG, rseg2, f->npairs, nullptr, 0, U,
+        GBX_TRY(pair_block_seg(bwd->mem, Ur * s, 0, st, &rseg2));
+        GBX_TRY(gbx_make_copy_op(bwd, 1, bwd->agg, ROLE_AGG, bwd->agg, ROLE_AGG, rseg2, 1, nullptr, 0, Ur,
                                  2 * U * s + f->npairs * (int64_t)sizeof(Seg)));
         total_terms += Vx;
     }
@@ -1616,12 +1646,15 @@ __global__ void bulk_fill_kernel(const Seg *segs, int64_t nseg, int64_t nelem, i
     }
 }
 
-int gbx_make_bulk(gbx_request_s *req, const Seg *segs, int64_t nseg, int64_t nelem, BulkTask **out, int64_t *n,
-                  int *ok) {
+// owned: source and destination are the library's own aggregate buffers (256-byte aligned
+// allocations), so only the pieces' offsets and lengths decide; otherwise the caller's buffers'
+// alignment (and the element size) must be a multiple of 16 as well.
+int gbx_make_bulk(gbx_request_s *req, const Seg *segs, int64_t nseg, int64_t nelem, bool owned, BulkTask **out,
+                  int64_t *n, int *ok) {
     cudaStream_t st = req->stream;
     *ok = 0;
     *n = 0;
-    if (nseg <= 0 || nelem <= 0 || (req->align & 15)) return GBX_SUCCESS;
+    if (nseg <= 0 || nelem <= 0 || (!owned && (req->align & 15))) return GBX_SUCCESS;
     DevPool ws;
     int *bad;
     int64_t *np, *first;
