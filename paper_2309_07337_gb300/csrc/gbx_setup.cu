@@ -1212,7 +1212,7 @@ __global__ void scatter_start_kernel(const int64_t *flag, const int64_t *pid, in
 // Walks window w's pairs; counts its pieces (out == nullptr) or writes them from out[0].
 __device__ int64_t scatter_walk(const int32_t *gs, int64_t m0, int64_t m1, int64_t s, ScatterPiece *out) {
     int64_t np = 0;
-    ScatterPiece k;
+    ScatterPiece k = {};              // (every field is set at the window's first pair)
     int64_t run_lo = 0, run_hi = 0;   // current run, in source elements [lo, hi]
     auto close_run = [&]() {
         k.run_off[k.nrun] = (uint16_t)((run_lo * s) - k.src);
