@@ -498,6 +498,33 @@ def test_config5_full_512cube_backward():
         torch.cuda.empty_cache()
 
 
+def test_backward_bit_identical_over_100_starts_512cube():
+    """Determinism of the reverse exchange at full size, in the launch configuration the
+    benchmark times: 100 starts of each form's backward give the same field gradient, bit for
+    bit (fixed summation order, no atomics), and it is the oracle's."""
+    p = pt.config5()
+    x = torch.from_numpy(pt.stencil_field(p, pt.SEED + 5)).cuda()
+    halo = torch.zeros(p.recvbuf_bytes // 8, dtype=torch.float64, device="cuda")
+    g_np = grad_payload(p, 78)
+    g = torch.from_numpy(g_np).cuda()
+    dp = gbx.DevicePattern(p)
+    for alg, form in (("standard", 0), ("locality", 1)):
+        ex = gbx.Exchange(p, x, halo, alg, dp=dp)
+        gx = torch.zeros_like(x)
+        b = gbx.backward_init(ex.request, g, gx)
+        b.start()
+        b.wait()
+        first = gx.clone()
+        for _ in range(100):
+            gx.zero_()   # (source points no slot reads keep the initial zeros)
+            b.start()
+            b.wait()
+            assert torch.equal(gx.view(torch.uint8), first.view(torch.uint8)), f"{alg}: a start changed the gradient"
+        assert_bytes_equal(first.cpu().numpy(), oracle.backward(p, g_np, form=form), f"{alg} vs oracle")
+        del ex, b, gx, first
+        torch.cuda.empty_cache()
+
+
 def _explicit(P, ppn, out_lists, in_lists, s, send_base, recv_base, sendbuf_bytes, recvbuf_bytes, dtype="bytes"):
     """Pattern from per-rank lists: out_lists[r] = [(d, count, sdispl)], in_lists[d] = [(r, count, rdispl)]."""
     def csr(lists):
