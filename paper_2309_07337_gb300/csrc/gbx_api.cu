@@ -624,6 +624,10 @@ static int tune_op(gbx_request_s *req, HostOp &op) {
                     // a narrower vector must win clearly: it adds a kernel class to any batch
                     // the op joins, and small ops (under two waves of tiles) time within noise
                     const float margin = op_tiles(op) < 2 * 4 * gbx_num_sms() ? 0.85f : 0.97f;
+                    // the bulk form wins near-ties: it reads no per-element index and leaves the
+                    // SMs' load / store issue to the copy engine (repeated trials with a warm L2
+                    // time the index-driven forms within a few per cent of it)
+                    if (op.kind == 0 && form == 8) ms *= 0.97f;
                     if (ms < best.ms * (vec < best.vec ? margin : 1.0f)) best = {vec, blocks[bi], pers, form, ms};
                 }
             if (vec == 1) break;
