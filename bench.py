@@ -392,12 +392,21 @@ def run_ours(args):
     grad_halo = torch.randn(p.recvbuf_bytes // 8, dtype=torch.float64, device="cuda", generator=gen)
     grad_field = torch.zeros_like(field)
     dp = gbx.DevicePattern(p)
-    t_init = time.perf_counter()
-    ex_std = gbx.Exchange(p, field, halo_std, "standard", dp=dp, info=args.info)
-    ex_loc = gbx.Exchange(p, field, halo_loc, "locality", dp=dp, graph=ex_std.graph, info=args.info)
+    # set-up, timed by part: the graph (edge matching), then each request (device maps and
+    # descriptors, program validation, autotuning, graph capture)
+    tb = [time.perf_counter()]
+    graph = gbx.DistGraph(gbx.Comm(p.P, p.ppn), dp.in_ptr, dp.sources, dp.out_ptr, dp.dests)
+    torch.cuda.synchronize()
+    tb.append(time.perf_counter())
+    ex_std = gbx.Exchange(p, field, halo_std, "standard", dp=dp, graph=graph, info=args.info)
+    tb.append(time.perf_counter())
+    ex_loc = gbx.Exchange(p, field, halo_loc, "locality", dp=dp, graph=graph, info=args.info)
+    tb.append(time.perf_counter())
     bwd = gbx.backward_init(ex_std.request, grad_halo, grad_field, info=args.info)
     torch.cuda.synchronize()
-    t_init = time.perf_counter() - t_init
+    tb.append(time.perf_counter())
+    t_init = tb[-1] - tb[0]
+    init_parts = {k: tb[i + 1] - tb[i] for i, k in enumerate(("graph", "standard", "locality", "backward"))}
     reqs = [ex_std.request, ex_loc.request, bwd]
     infos = [r.info() for r in reqs]
 
@@ -483,7 +492,7 @@ def run_ours(args):
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": workload_config(p, args.edge, world, args.ranks),
             "roofline": roofline, "gpu_launches": launches, "clocks": clk, "forms": forms,
-            "init_s": t_init}
+            "init_s": t_init, "init_parts_s": init_parts}
 
     # ---------------------------------------------------------------- e2e
     # Steps end to end with the data on the host, through the library's C ABI, two ways.
